@@ -1,0 +1,606 @@
+/*
+ * lb_oracle.c -- plain FP64 CPU oracle of the two-phase lattice Boltzmann step.
+ *
+ * TEST INFRASTRUCTURE.  This is the slow, literal statement of what one time
+ * step computes, used to check the CUDA library.  Only the test suite, the
+ * smoke check and the benchmark's CPU-baseline leg may load it.  It shares no
+ * code, header, table or constant with the CUDA library.
+ *
+ * Method: accLB (arXiv 2505.01126), Sec. 2.
+ *   - phase field phi: conservative Allen-Cahn equation (Sec. 2.1.1, Eq. 4),
+ *     solved here with a D3Q7 BGK lattice Boltzmann model whose equilibrium
+ *     carries the sharpening flux (4M/W) phi(1-phi) n as its first moment;
+ *   - lattice gradient of Sec. 2.3 (d_a Psi = (1/cs^2) sum_i w_i c_ia Psi(x+c_i))
+ *     for grad(phi); the normal n = grad(phi)/|grad(phi)|; the curvature
+ *     kappa = div(n) with the same stencil;
+ *   - surface tension (Sec. 2.3, after Kim 2005): F^s = -(3W/2) sigma kappa
+ *     |grad phi| grad phi;
+ *   - hydrodynamics: D3Q27, pressure-based equilibrium (Sec. 2.2), Guo force
+ *     (Eq. 6), push form of the collision (Eq. 7) with the non-equilibrium part
+ *     rebuilt from the second-order Hermite coefficient (Eq. 8);
+ *   - FP64 diagnostics and the linear-forcing amplitude controller.
+ *
+ * Every stage is a separate loop over all sites writing a full field, in the
+ * order of the method.  Two copies of each population set are kept; streaming
+ * pushes f*_i(x) into f_new(x + c_i).  Per-site loops may run under OpenMP:
+ * every site writes only its own outputs (or its own streamed slots), so the
+ * result does not depend on the thread count.  Sums are serial, in site order.
+ *
+ * Readings of the paper taken here (the CUDA library takes the same ones):
+ *   - the equilibrium tanh profile is phi = 1/2 - 1/2 tanh(2(d-R)/W) in the
+ *     Euclidean distance d; it is the 1D steady state of Eq. 4 with kappa=4D/W;
+ *   - the surface-tension prefactor 3W/2 makes the Laplace jump 2 sigma/R;
+ *   - n uses the guard max(|grad phi|, 1e-10);
+ *   - the regularized non-equilibrium is w_i H_i:a2/(2 cs^4) (the printed form
+ *     omits w_i and the trace part of H_i);
+ *   - u = sum_i f_i c_i + F/2 (the printed sum of S_i vanishes identically);
+ *   - linear forcing F = A u, A_{t+1} = [eps_t + (K_target-K_t)/T_relax]/(2K_t).
+ */
+#include "lb_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---------------------------------------------------------------- lattices */
+
+/* D3Q27 in textbook order: rest, 6 faces, 12 edges, 8 corners; every direction
+ * is followed by its opposite, so (1,2), (3,4), ... (25,26) are opposite pairs. */
+static const int C27[27][3] = {
+    {0, 0, 0},
+    {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},  {0, 0, 1},   {0, 0, -1},
+    {1, 1, 0},   {-1, -1, 0}, {1, -1, 0},  {-1, 1, 0},  {1, 0, 1},   {-1, 0, -1},
+    {1, 0, -1},  {-1, 0, 1},  {0, 1, 1},   {0, -1, -1}, {0, 1, -1},  {0, -1, 1},
+    {1, 1, 1},   {-1, -1, -1}, {1, 1, -1}, {-1, -1, 1}, {1, -1, 1},  {-1, 1, -1},
+    {-1, 1, 1},  {1, -1, -1}};
+
+/* Weights by the number of non-zero components of c_i: 8/27, 2/27, 1/54, 1/216. */
+#define WR (8.0 / 27)
+#define WF (2.0 / 27)
+#define WE (1.0 / 54)
+#define WC (1.0 / 216)
+static const double W27[27] = {WR, WF, WF, WF, WF, WF, WF, WE, WE, WE, WE, WE, WE, WE,
+                               WE, WE, WE, WE, WE, WC, WC, WC, WC, WC, WC, WC, WC};
+static const double CS2 = 1.0 / 3.0; /* D3Q27 speed of sound squared */
+
+/* D3Q7: rest and the 6 faces, opposite pairs (1,2), (3,4), (5,6). */
+static const int C7[7][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0},
+                             {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+static const double W7[7] = {1.0 / 4, 1.0 / 8, 1.0 / 8, 1.0 / 8, 1.0 / 8, 1.0 / 8, 1.0 / 8};
+static const double CS2_7 = 1.0 / 4.0; /* D3Q7 speed of sound squared */
+
+static const double NORMAL_GUARD = 1e-10;
+
+void orc_lattice27(int c[27][3], double w[27]) {
+    for (int i = 0; i < 27; ++i) {
+        for (int a = 0; a < 3; ++a) c[i][a] = C27[i][a];
+        w[i] = W27[i];
+    }
+}
+
+void orc_lattice7(int c[7][3], double w[7]) {
+    for (int i = 0; i < 7; ++i) {
+        for (int a = 0; a < 3; ++a) c[i][a] = C7[i][a];
+        w[i] = W7[i];
+    }
+}
+
+/* ------------------------------------------------------------------- state */
+
+struct orc_state {
+    int nx, ny, nz;
+    long long N;
+    double tau, omega, nu, M, W, sigma, omega_phi, sharp, beta;
+    int force_kind;
+    double g_const[3], A_abc, kf, K_target, T_relax;
+    int regularize;
+    double A;       /* linear forcing amplitude used by the next step */
+    long long t;    /* steps taken */
+    double diag[5]; /* Phi, K, eps, max|u|, A_next of the last step */
+
+    double *f, *fn, *g, *gn;           /* populations, two copies each */
+    double *phi, *grad, *nrm, *kappa;  /* phase field and its derivatives */
+    double *Fs, *rho, *mom, *Pi;       /* surface force, hydrodynamic moments */
+    double *u, *F, *a2;                /* velocity, total force, Hermite coeff. */
+};
+
+static int g_threads = 0;
+
+void orc_set_threads(int n) { g_threads = n; }
+
+int orc_threads(void) {
+#ifdef _OPENMP
+    return g_threads > 0 ? g_threads : omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static inline int wrap(int v, int n) {
+    int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+static inline long long site(const orc_state* s, int x, int y, int z) {
+    return (long long)x + (long long)s->nx * ((long long)y + (long long)s->ny * z);
+}
+
+orc_state* orc_create(int nx, int ny, int nz, double tau, double M, double W, double sigma,
+                      int force_kind, const double g_const[3], double A_abc, double kf,
+                      double K_target, double T_relax, int regularize) {
+    if (nx < 1 || ny < 1 || nz < 1 || !(tau > 0.5) || !(M > 0) || !(W > 0) || !(sigma >= 0))
+        return NULL;
+    if (isinf(W) && sigma > 0) return NULL;
+    if (force_kind < ORC_FORCE_NONE || force_kind > ORC_FORCE_LINEAR) return NULL;
+    if (force_kind == ORC_FORCE_LINEAR && !(T_relax > 0)) return NULL;
+    orc_state* s = (orc_state*)calloc(1, sizeof(orc_state));
+    if (!s) return NULL;
+    s->nx = nx; s->ny = ny; s->nz = nz;
+    s->N = (long long)nx * ny * nz;
+    s->tau = tau;
+    s->omega = 1.0 / tau;
+    s->nu = CS2 * (tau - 0.5);                /* Sec. 2.2: nu = cs^2 (tau - 1/2) */
+    s->M = M; s->W = W; s->sigma = sigma;
+    s->omega_phi = 1.0 / (M / CS2_7 + 0.5);  /* M = cs7^2 (tau_phi - 1/2) */
+    s->sharp = isinf(W) ? 0.0 : (M / CS2_7) * (4.0 / W);
+    s->beta = sigma == 0 ? 0.0 : 1.5 * W * sigma;
+    s->force_kind = force_kind;
+    for (int a = 0; a < 3; ++a) s->g_const[a] = g_const ? g_const[a] : 0.0;
+    s->A_abc = A_abc; s->kf = kf; s->K_target = K_target; s->T_relax = T_relax;
+    s->regularize = regularize;
+    long long N = s->N;
+    s->f = (double*)calloc((size_t)(27 * N), sizeof(double));
+    s->fn = (double*)calloc((size_t)(27 * N), sizeof(double));
+    s->g = (double*)calloc((size_t)(7 * N), sizeof(double));
+    s->gn = (double*)calloc((size_t)(7 * N), sizeof(double));
+    s->phi = (double*)calloc((size_t)N, sizeof(double));
+    s->grad = (double*)calloc((size_t)(3 * N), sizeof(double));
+    s->nrm = (double*)calloc((size_t)(3 * N), sizeof(double));
+    s->kappa = (double*)calloc((size_t)N, sizeof(double));
+    s->Fs = (double*)calloc((size_t)(3 * N), sizeof(double));
+    s->rho = (double*)calloc((size_t)N, sizeof(double));
+    s->mom = (double*)calloc((size_t)(3 * N), sizeof(double));
+    s->Pi = (double*)calloc((size_t)(6 * N), sizeof(double));
+    s->u = (double*)calloc((size_t)(3 * N), sizeof(double));
+    s->F = (double*)calloc((size_t)(3 * N), sizeof(double));
+    s->a2 = (double*)calloc((size_t)(6 * N), sizeof(double));
+    if (!s->f || !s->fn || !s->g || !s->gn || !s->phi || !s->grad || !s->nrm || !s->kappa ||
+        !s->Fs || !s->rho || !s->mom || !s->Pi || !s->u || !s->F || !s->a2) {
+        orc_destroy(s);
+        return NULL;
+    }
+    return s;
+}
+
+void orc_destroy(orc_state* s) {
+    if (!s) return;
+    free(s->f); free(s->fn); free(s->g); free(s->gn);
+    free(s->phi); free(s->grad); free(s->nrm); free(s->kappa);
+    free(s->Fs); free(s->rho); free(s->mom); free(s->Pi);
+    free(s->u); free(s->F); free(s->a2);
+    free(s);
+}
+
+long long orc_time(const orc_state* s) { return s->t; }
+
+/* ------------------------------------------------- per-site building blocks */
+
+/* Pressure-based equilibrium (Sec. 2.2):
+ * f^eq_i = w_i (p* + c_i.u/cs^2 + (c_ia c_ib - cs^2 d_ab) u_a u_b / (2 cs^4)). */
+void orc_equilibrium(double p, const double u[3], double feq[27]) {
+    for (int i = 0; i < 27; ++i) {
+        double cu = 0, Huu = 0;
+        for (int a = 0; a < 3; ++a) cu += C27[i][a] * u[a];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                Huu += (C27[i][a] * C27[i][b] - (a == b ? CS2 : 0.0)) * u[a] * u[b];
+        feq[i] = W27[i] * (p + cu / CS2 + Huu / (2 * CS2 * CS2));
+    }
+}
+
+/* Guo forcing term, Eq. 6: S_i = w_i ((c_ia - u_a)/cs^2 + (c_ib u_b) c_ia / cs^4) F_a. */
+void orc_guo_source(const double u[3], const double F[3], double S[27]) {
+    for (int i = 0; i < 27; ++i) {
+        double cu = 0;
+        for (int b = 0; b < 3; ++b) cu += C27[i][b] * u[b];
+        double acc = 0;
+        for (int a = 0; a < 3; ++a)
+            acc += ((C27[i][a] - u[a]) / CS2 + cu * C27[i][a] / (CS2 * CS2)) * F[a];
+        S[i] = W27[i] * acc;
+    }
+}
+
+/* Symmetric tensor component (a,b) from storage order xx, yy, zz, xy, xz, yz. */
+static inline double sym(const double t[6], int a, int b) {
+    if (a == b) return t[a];
+    int k = a + b; /* xy -> 1, xz -> 2, yz -> 3 */
+    return t[2 + k];
+}
+
+/* Regularized non-equilibrium (Sec. 2.2, Hermite reconstruction):
+ * f^neq_i = w_i H_i : a2 / (2 cs^4), H_i = c_i c_i - cs^2 I. */
+void orc_regularized_neq(const double a2[6], double fneq[27]) {
+    for (int i = 0; i < 27; ++i) {
+        double Ha = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                Ha += (C27[i][a] * C27[i][b] - (a == b ? CS2 : 0.0)) * sym(a2, a, b);
+        fneq[i] = W27[i] * Ha / (2 * CS2 * CS2);
+    }
+}
+
+/* D3Q7 phase-field equilibrium: the zeroth moment is phi, the first moment is
+ * phi u + (4M/W) phi (1-phi) n, so the Chapman-Enskog limit is Eq. 4 with
+ * D = M = cs7^2 (tau_phi - 1/2).  sharp = (M/cs7^2)(4/W). */
+void orc_phase_equilibrium(double phi, const double u[3], const double n[3], double sharp,
+                           double geq[7]) {
+    for (int i = 0; i < 7; ++i) {
+        double cu = 0, cn = 0;
+        for (int a = 0; a < 3; ++a) {
+            cu += C7[i][a] * u[a];
+            cn += C7[i][a] * n[a];
+        }
+        geq[i] = W7[i] * phi * (1 + cu / CS2_7) + W7[i] * sharp * phi * (1 - phi) * cn;
+    }
+}
+
+/* Periodic neighbour coordinate tables: nb[c+1][x] = (x + c) mod n, c in {-1,0,1}. */
+static int* neighbour_table(int n) {
+    int* t = (int*)malloc((size_t)(3 * n) * sizeof(int));
+    for (int c = -1; c <= 1; ++c)
+        for (int x = 0; x < n; ++x) t[(c + 1) * n + x] = wrap(x + c, n);
+    return t;
+}
+
+/* Lattice gradient (Sec. 2.3): d_a Psi(x) = (1/cs^2) sum_i w_i c_ia Psi(x + c_i),
+ * summed over the 13 opposite pairs (the rest direction has c = 0), periodic. */
+void orc_gradient(int nx, int ny, int nz, const double* psi, double* grad) {
+    long long N = (long long)nx * ny * nz;
+    int* tx = neighbour_table(nx);
+    int* ty = neighbour_table(ny);
+    int* tz = neighbour_table(nz);
+#pragma omp parallel for schedule(static) num_threads(orc_threads())
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                long long s = (long long)x + (long long)nx * ((long long)y + (long long)ny * z);
+                double d[3] = {0, 0, 0};
+                for (int i = 1; i < 27; i += 2) {
+                    const int* c = C27[i];
+                    long long sp = tx[(1 + c[0]) * nx + x] +
+                                   (long long)nx * (ty[(1 + c[1]) * ny + y] + (long long)ny * tz[(1 + c[2]) * nz + z]);
+                    long long sm = tx[(1 - c[0]) * nx + x] +
+                                   (long long)nx * (ty[(1 - c[1]) * ny + y] + (long long)ny * tz[(1 - c[2]) * nz + z]);
+                    double diff = psi[sp] - psi[sm];
+                    for (int a = 0; a < 3; ++a) d[a] += W27[i] * c[a] * diff;
+                }
+                for (int a = 0; a < 3; ++a) grad[a * N + s] = d[a] / CS2;
+            }
+    free(tx); free(ty); free(tz);
+}
+
+/* ------------------------------------------------------------ step stages */
+
+/* phi = sum_i g_i (zeroth moment of the phase populations). */
+static void stage_phase_field(orc_state* s) {
+    long long N = s->N;
+#pragma omp parallel for schedule(static) num_threads(orc_threads())
+    for (long long x = 0; x < N; ++x) {
+        double p = 0;
+        for (int i = 0; i < 7; ++i) p += s->g[i * N + x];
+        s->phi[x] = p;
+    }
+}
+
+/* n = grad phi / max(|grad phi|, 1e-10). */
+static void stage_normal(orc_state* s) {
+    long long N = s->N;
+#pragma omp parallel for schedule(static) num_threads(orc_threads())
+    for (long long x = 0; x < N; ++x) {
+        double gx = s->grad[x], gy = s->grad[N + x], gz = s->grad[2 * N + x];
+        double m = sqrt(gx * gx + gy * gy + gz * gz);
+        double d = m > NORMAL_GUARD ? m : NORMAL_GUARD;
+        s->nrm[x] = gx / d;
+        s->nrm[N + x] = gy / d;
+        s->nrm[2 * N + x] = gz / d;
+    }
+}
+
+/* kappa = div n = d_x n_x + d_y n_y + d_z n_z, each with the lattice gradient. */
+static void stage_curvature(orc_state* s) {
+    long long N = s->N;
+    double* tmp = (double*)malloc((size_t)(3 * N) * sizeof(double));
+    for (long long x = 0; x < N; ++x) s->kappa[x] = 0;
+    for (int a = 0; a < 3; ++a) {
+        orc_gradient(s->nx, s->ny, s->nz, s->nrm + a * N, tmp);
+        for (long long x = 0; x < N; ++x) s->kappa[x] += tmp[a * N + x];
+    }
+    free(tmp);
+}
+
+/* Surface tension (Sec. 2.3): F^s = -(3W/2) sigma kappa |grad phi| grad phi. */
+static void stage_surface_force(orc_state* s) {
+    long long N = s->N;
+#pragma omp parallel for schedule(static) num_threads(orc_threads())
+    for (long long x = 0; x < N; ++x) {
+        double gx = s->grad[x], gy = s->grad[N + x], gz = s->grad[2 * N + x];
+        double m = sqrt(gx * gx + gy * gy + gz * gz);
+        double c = -s->beta * s->kappa[x] * m;
+        s->Fs[x] = c * gx;
+        s->Fs[N + x] = c * gy;
+        s->Fs[2 * N + x] = c * gz;
+    }
+}
+
+/* p* = sum_i f_i, m = sum_i f_i c_i, Pi = sum_i f_i c_i c_i (Sec. 2.2). */
+static void stage_hydro_moments(orc_state* s) {
+    long long N = s->N;
+#pragma omp parallel for schedule(static) num_threads(orc_threads())
+    for (long long x = 0; x < N; ++x) {
+        double p = 0, m[3] = {0, 0, 0}, P[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < 27; ++i) {
+            double fi = s->f[i * N + x];
+            const int* c = C27[i];
+            p += fi;
+            for (int a = 0; a < 3; ++a) m[a] += fi * c[a];
+            P[0] += fi * c[0] * c[0];
+            P[1] += fi * c[1] * c[1];
+            P[2] += fi * c[2] * c[2];
+            P[3] += fi * c[0] * c[1];
+            P[4] += fi * c[0] * c[2];
+            P[5] += fi * c[1] * c[2];
+        }
+        s->rho[x] = p;
+        for (int a = 0; a < 3; ++a) s->mom[a * N + x] = m[a];
+        for (int k = 0; k < 6; ++k) s->Pi[k * N + x] = P[k];
+    }
+}
+
+/* Velocity-independent part of the external force at site (x,y,z). */
+static void external_force(const orc_state* s, int x, int y, int z, double Fe[3]) {
+    Fe[0] = Fe[1] = Fe[2] = 0;
+    if (s->force_kind == ORC_FORCE_CONST) {
+        for (int a = 0; a < 3; ++a) Fe[a] = s->g_const[a];
+    } else if (s->force_kind == ORC_FORCE_ABC) {
+        /* ABC forcing (Sec. 5.1) */
+        double k = s->kf;
+        Fe[0] = s->A_abc * (sin(k * z) + cos(k * y));
+        Fe[1] = s->A_abc * (sin(k * x) + cos(k * z));
+        Fe[2] = s->A_abc * (sin(k * y) + cos(k * x));
+    }
+}
+
+/* u = sum f c + F/2 with F = F^s + F^ext + A u (linear forcing solved in closed
+ * form: u = (m + (F^s + F^ext)/2) / (1 - A/2)). */
+static void stage_velocity_force(orc_state* s) {
+    long long N = s->N;
+    double A = s->force_kind == ORC_FORCE_LINEAR ? s->A : 0.0;
+#pragma omp parallel for schedule(static) num_threads(orc_threads())
+    for (int z = 0; z < s->nz; ++z)
+        for (int y = 0; y < s->ny; ++y)
+            for (int x = 0; x < s->nx; ++x) {
+                long long i = site(s, x, y, z);
+                double Fe[3];
+                external_force(s, x, y, z, Fe);
+                for (int a = 0; a < 3; ++a) {
+                    double Fa = s->Fs[a * N + i] + Fe[a];
+                    double ua = (s->mom[a * N + i] + 0.5 * Fa) / (1 - 0.5 * A);
+                    s->u[a * N + i] = ua;
+                    s->F[a * N + i] = Fa + A * ua;
+                }
+            }
+}
+
+/* Eq. 8: a2_ab = sum_i f^neq_i (c_ia c_ib - cs^2 d_ab), f^neq_i = f_i - f^eq_i + S_i/2. */
+static void stage_hermite(orc_state* s) {
+    long long N = s->N;
+#pragma omp parallel for schedule(static) num_threads(orc_threads())
+    for (long long x = 0; x < N; ++x) {
+        double u[3] = {s->u[x], s->u[N + x], s->u[2 * N + x]};
+        double F[3] = {s->F[x], s->F[N + x], s->F[2 * N + x]};
+        double feq[27], S[27];
+        orc_equilibrium(s->rho[x], u, feq);
+        orc_guo_source(u, F, S);
+        double A[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < 27; ++i) {
+            const int* c = C27[i];
+            double fneq = s->f[i * N + x] - feq[i] + 0.5 * S[i];
+            A[0] += fneq * (c[0] * c[0] - CS2);
+            A[1] += fneq * (c[1] * c[1] - CS2);
+            A[2] += fneq * (c[2] * c[2] - CS2);
+            A[3] += fneq * c[0] * c[1];
+            A[4] += fneq * c[0] * c[2];
+            A[5] += fneq * c[1] * c[2];
+        }
+        for (int k = 0; k < 6; ++k) s->a2[k * N + x] = A[k];
+    }
+}
+
+/* Eq. 7 (push form): f_i(x + c_i, t+1) = f^eq_i + (1 - omega) f^neq_i + S_i/2. */
+static void stage_collide_stream_hydro(orc_state* s) {
+    long long N = s->N;
+#pragma omp parallel for schedule(static) num_threads(orc_threads())
+    for (int z = 0; z < s->nz; ++z)
+        for (int y = 0; y < s->ny; ++y)
+            for (int x = 0; x < s->nx; ++x) {
+                long long k = site(s, x, y, z);
+                double u[3] = {s->u[k], s->u[N + k], s->u[2 * N + k]};
+                double F[3] = {s->F[k], s->F[N + k], s->F[2 * N + k]};
+                double a2[6];
+                for (int q = 0; q < 6; ++q) a2[q] = s->a2[q * N + k];
+                double feq[27], S[27], fneq[27];
+                orc_equilibrium(s->rho[k], u, feq);
+                orc_guo_source(u, F, S);
+                if (s->regularize) {
+                    orc_regularized_neq(a2, fneq);
+                } else {
+                    for (int i = 0; i < 27; ++i) fneq[i] = s->f[i * N + k] - feq[i] + 0.5 * S[i];
+                }
+                for (int i = 0; i < 27; ++i) {
+                    const int* c = C27[i];
+                    long long dst = site(s, wrap(x + c[0], s->nx), wrap(y + c[1], s->ny),
+                                         wrap(z + c[2], s->nz));
+                    s->fn[i * N + dst] = feq[i] + (1 - s->omega) * fneq[i] + 0.5 * S[i];
+                }
+            }
+    double* t = s->f; s->f = s->fn; s->fn = t;
+}
+
+/* D3Q7 BGK: g_i(x + c_i, t+1) = g_i + omega_phi (g^eq_i - g_i). */
+static void stage_collide_stream_phase(orc_state* s) {
+    long long N = s->N;
+#pragma omp parallel for schedule(static) num_threads(orc_threads())
+    for (int z = 0; z < s->nz; ++z)
+        for (int y = 0; y < s->ny; ++y)
+            for (int x = 0; x < s->nx; ++x) {
+                long long k = site(s, x, y, z);
+                double u[3] = {s->u[k], s->u[N + k], s->u[2 * N + k]};
+                double n[3] = {s->nrm[k], s->nrm[N + k], s->nrm[2 * N + k]};
+                double geq[7];
+                orc_phase_equilibrium(s->phi[k], u, n, s->sharp, geq);
+                for (int i = 0; i < 7; ++i) {
+                    const int* c = C7[i];
+                    long long dst = site(s, wrap(x + c[0], s->nx), wrap(y + c[1], s->ny),
+                                         wrap(z + c[2], s->nz));
+                    double gi = s->g[i * N + k];
+                    s->gn[i * N + dst] = gi + s->omega_phi * (geq[i] - gi);
+                }
+            }
+    double* t = s->g; s->g = s->gn; s->gn = t;
+}
+
+/* FP64 reductions: Phi = sum phi, K = 1/2 sum |u|^2, eps = 2 nu sum S:S with
+ * S = -a2/(2 cs^2 tau) (the Chapman-Enskog estimate of Sec. 2.2), max|u|;
+ * then the linear-forcing amplitude for the next step. */
+static void stage_diagnostics(orc_state* s) {
+    long long N = s->N;
+    double Phi = 0, K = 0, SS = 0, umax = 0;
+    double scale = 1.0 / (2 * CS2 * s->tau);
+    for (long long x = 0; x < N; ++x) {
+        Phi += s->phi[x];
+        double u2 = s->u[x] * s->u[x] + s->u[N + x] * s->u[N + x] + s->u[2 * N + x] * s->u[2 * N + x];
+        K += 0.5 * u2;
+        double um = sqrt(u2);
+        if (um > umax || um != um) umax = um;
+        double ss = 0;
+        double A[6];
+        for (int q = 0; q < 6; ++q) A[q] = s->a2[q * N + x];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double Sab = -scale * sym(A, a, b);
+                ss += Sab * Sab;
+            }
+        SS += ss;
+    }
+    double eps = 2 * s->nu * SS;
+    double Anext = 0;
+    if (s->force_kind == ORC_FORCE_LINEAR && K > 0)
+        Anext = (eps + (s->K_target - K) / s->T_relax) / (2 * K);
+    s->diag[0] = Phi;
+    s->diag[1] = K;
+    s->diag[2] = eps;
+    s->diag[3] = umax;
+    s->diag[4] = Anext;
+    s->A = Anext;
+}
+
+/* Stages that need only the state at time t: phi, its derivatives, the forces,
+ * the moments and the velocity. */
+static void prepare(orc_state* s) {
+    stage_phase_field(s);
+    orc_gradient(s->nx, s->ny, s->nz, s->phi, s->grad);
+    stage_normal(s);
+    stage_curvature(s);
+    stage_surface_force(s);
+    stage_hydro_moments(s);
+    stage_velocity_force(s);
+}
+
+int orc_step(orc_state* s, int n) {
+    if (!s || n < 0) return -1;
+    for (int k = 0; k < n; ++k) {
+        prepare(s);
+        stage_hermite(s);
+        stage_diagnostics(s);
+        stage_collide_stream_hydro(s);
+        stage_collide_stream_phase(s);
+        s->t += 1;
+    }
+    return 0;
+}
+
+int orc_init(orc_state* s, const double* phi, const double* u) {
+    if (!s || !phi || !u) return -1;
+    long long N = s->N;
+    memcpy(s->phi, phi, (size_t)N * sizeof(double));
+    orc_gradient(s->nx, s->ny, s->nz, s->phi, s->grad);
+    stage_normal(s);
+    for (long long x = 0; x < N; ++x) {
+        double ux[3] = {u[x], u[N + x], u[2 * N + x]};
+        double n[3] = {s->nrm[x], s->nrm[N + x], s->nrm[2 * N + x]};
+        double feq[27], geq[7];
+        orc_equilibrium(1.0, ux, feq);
+        orc_phase_equilibrium(phi[x], ux, n, s->sharp, geq);
+        for (int i = 0; i < 27; ++i) s->f[i * N + x] = feq[i];
+        for (int i = 0; i < 7; ++i) s->g[i * N + x] = geq[i];
+    }
+    if (s->force_kind == ORC_FORCE_LINEAR && !(s->K_target > 0)) {
+        double K = 0;
+        for (long long x = 0; x < N; ++x)
+            K += 0.5 * (u[x] * u[x] + u[N + x] * u[N + x] + u[2 * N + x] * u[2 * N + x]);
+        s->K_target = K;
+    }
+    s->A = 0;
+    s->t = 0;
+    for (int q = 0; q < 5; ++q) s->diag[q] = 0;
+    return 0;
+}
+
+void orc_moments(orc_state* s, double* rho, double* u, double* phi) {
+    prepare(s);
+    long long N = s->N;
+    if (rho) memcpy(rho, s->rho, (size_t)N * sizeof(double));
+    if (u) memcpy(u, s->u, (size_t)(3 * N) * sizeof(double));
+    if (phi) memcpy(phi, s->phi, (size_t)N * sizeof(double));
+}
+
+/* phi -> grad phi, n, kappa and F^s (sigma, W as given), through the same stages as
+ * the step. */
+int orc_interface(int nx, int ny, int nz, double W, double sigma, const double* phi,
+                  double* grad, double* nrm, double* kappa, double* Fs) {
+    orc_state* s = orc_create(nx, ny, nz, 1.0, 0.1, W, sigma, ORC_FORCE_NONE, NULL, 0, 0, 0, 1, 1);
+    if (!s) return -1;
+    long long N = s->N;
+    memcpy(s->phi, phi, (size_t)N * sizeof(double));
+    orc_gradient(nx, ny, nz, s->phi, s->grad);
+    stage_normal(s);
+    stage_curvature(s);
+    stage_surface_force(s);
+    if (grad) memcpy(grad, s->grad, (size_t)(3 * N) * sizeof(double));
+    if (nrm) memcpy(nrm, s->nrm, (size_t)(3 * N) * sizeof(double));
+    if (kappa) memcpy(kappa, s->kappa, (size_t)N * sizeof(double));
+    if (Fs) memcpy(Fs, s->Fs, (size_t)(3 * N) * sizeof(double));
+    orc_destroy(s);
+    return 0;
+}
+
+void orc_diagnostics(const orc_state* s, double out[5]) {
+    for (int q = 0; q < 5; ++q) out[q] = s->diag[q];
+}
+
+void orc_get_populations(const orc_state* s, double* f, double* g) {
+    if (f) memcpy(f, s->f, (size_t)(27 * s->N) * sizeof(double));
+    if (g) memcpy(g, s->g, (size_t)(7 * s->N) * sizeof(double));
+}
+
+void orc_set_populations(orc_state* s, const double* f, const double* g) {
+    if (f) memcpy(s->f, f, (size_t)(27 * s->N) * sizeof(double));
+    if (g) memcpy(s->g, g, (size_t)(7 * s->N) * sizeof(double));
+}
+
+void orc_last_force(const orc_state* s, double* F) {
+    memcpy(F, s->F, (size_t)(3 * s->N) * sizeof(double));
+}

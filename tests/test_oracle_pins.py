@@ -1,0 +1,462 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a moment
+identity of the lattice, a closed form, a conservation law, a textbook scheme
+it must reduce to, or a physical law (viscous decay, tanh interface, Laplace
+pressure jump).  Section/equation numbers refer to accLB (arXiv 2505.01126).
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from paper_2505_01126_gb300 import inputs
+
+INF = float("inf")
+
+
+# ----------------------------------------------------------------- lattices
+def test_d3q27_moment_identities(orc):
+    """sum w = 1, sum w c = 0, sum w c c = cs^2 I, odd moments vanish, and the
+    fourth moment is isotropic: cs^4 (d_ab d_cd + d_ac d_bd + d_ad d_bc)."""
+    c, w = orc.lattice27()
+    c = c.astype(float)
+    cs2 = 1.0 / 3.0
+    assert len({tuple(v) for v in c.astype(int)}) == 27
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.abs(w @ c).max() < 1e-15
+    np.testing.assert_allclose(np.einsum("i,ia,ib->ab", w, c, c), cs2 * np.eye(3), atol=1e-15)
+    assert np.abs(np.einsum("i,ia,ib,ic->abc", w, c, c, c)).max() < 1e-15
+    m4 = np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c)
+    d = np.eye(3)
+    iso = cs2 ** 2 * (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+                      + np.einsum("ad,bc->abcd", d, d))
+    np.testing.assert_allclose(m4, iso, atol=1e-15)
+
+
+def test_d3q7_moment_identities(orc):
+    c, w = orc.lattice7()
+    c = c.astype(float)
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.abs(w @ c).max() < 1e-15
+    np.testing.assert_allclose(np.einsum("i,ia,ib->ab", w, c, c), 0.25 * np.eye(3), atol=1e-15)
+
+
+# ----------------------------------------------------------- lattice gradient
+def test_gradient_exact_for_quadratics(orc):
+    """The Sec. 2.3 stencil is exact for polynomials of degree <= 2 (checked away
+    from the periodic seam)."""
+    nz, ny, nx = 9, 10, 11
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    psi = 0.3 + 0.2 * x - 0.1 * y + 0.05 * z + 0.01 * x * x - 0.02 * x * y + 0.03 * y * z + 0.015 * z * z
+    g = orc.gradient(psi)
+    exact = np.stack([0.2 + 0.02 * x - 0.02 * y,
+                      -0.1 - 0.02 * x + 0.03 * z,
+                      0.05 + 0.03 * y + 0.03 * z])
+    inner = (slice(None), slice(1, -1), slice(1, -1), slice(1, -1))
+    np.testing.assert_allclose(g[inner], exact[inner], atol=1e-13)
+
+
+def test_gradient_of_periodic_wave_closed_form(orc):
+    """For psi = sin(kx x) cos(ky y): d_x psi = sin(kx) cos(kx x) cos(ky y) (2 + cos ky)/3,
+    d_y psi = -sin(kx x) sin(ky) sin(ky y) (2 + cos kx)/3, d_z psi = 0, on the periodic
+    lattice with non-cubic edges."""
+    nz, ny, nx = 5, 12, 16
+    kx, ky = 2 * math.pi * 3 / nx, 2 * math.pi * 2 / ny
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    psi = np.sin(kx * x) * np.cos(ky * y)
+    g = orc.gradient(psi)
+    gx = math.sin(kx) * np.cos(kx * x) * np.cos(ky * y) * (2 + math.cos(ky)) / 3
+    gy = -np.sin(kx * x) * math.sin(ky) * np.sin(ky * y) * (2 + math.cos(kx)) / 3
+    np.testing.assert_allclose(g[0], gx, atol=1e-14)
+    np.testing.assert_allclose(g[1], gy, atol=1e-14)
+    assert np.abs(g[2]).max() < 1e-14
+
+
+def test_gradient_of_constant_is_exactly_zero(orc):
+    g = orc.gradient(np.full((4, 5, 6), 0.3))
+    assert np.all(g == 0.0)
+
+
+# ---------------------------------------------------- equilibria and sources
+def test_equilibrium_moments(orc):
+    """Pressure-based equilibrium of Sec. 2.2: sum f^eq = p*, sum f^eq c = u,
+    sum f^eq c c = p* cs^2 I + u u."""
+    c, _ = orc.lattice27()
+    c = c.astype(float)
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        p = 1 + 0.1 * rng.standard_normal()
+        u = 0.05 * rng.standard_normal(3)
+        f = orc.equilibrium(p, u)
+        assert abs(f.sum() - p) < 1e-14
+        np.testing.assert_allclose(f @ c, u, atol=1e-15)
+        np.testing.assert_allclose(np.einsum("i,ia,ib->ab", f, c, c),
+                                   p / 3 * np.eye(3) + np.outer(u, u), atol=1e-15)
+
+
+def test_guo_source_moments(orc):
+    """Eq. 6 has moments sum S = 0, sum S c = F, sum S c c = u F + F u."""
+    c, _ = orc.lattice27()
+    c = c.astype(float)
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        u = 0.05 * rng.standard_normal(3)
+        F = 1e-3 * rng.standard_normal(3)
+        S = orc.guo_source(u, F)
+        assert abs(S.sum()) < 1e-17
+        np.testing.assert_allclose(S @ c, F, atol=1e-17)
+        np.testing.assert_allclose(np.einsum("i,ia,ib->ab", S, c, c),
+                                   np.outer(u, F) + np.outer(F, u), atol=1e-17)
+
+
+def test_hermite_regularization_is_a_projection(orc):
+    """Rebuilding f^neq from a2 and re-measuring Eq. 8 gives a2 back; the rebuilt
+    part carries no mass and no momentum."""
+    c, _ = orc.lattice27()
+    c = c.astype(float)
+    H = np.einsum("ia,ib->iab", c, c) - np.eye(3) / 3
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        a = rng.standard_normal(6) * 1e-3
+        fneq = orc.regularized_neq(a)
+        A = np.einsum("i,iab->ab", fneq, H)
+        full = np.array([[a[0], a[3], a[4]], [a[3], a[1], a[5]], [a[4], a[5], a[2]]])
+        np.testing.assert_allclose(A, full, atol=1e-17)
+        assert abs(fneq.sum()) < 1e-17
+        assert np.abs(fneq @ c).max() < 1e-17
+
+
+def test_phase_equilibrium_moments(orc):
+    """D3Q7 phase equilibrium: zeroth moment phi, first moment
+    phi u + (4M/W) phi (1 - phi) n, i.e. the advective plus sharpening flux of Eq. 4."""
+    c, _ = orc.lattice7()
+    c = c.astype(float)
+    M, W = 0.1, 3.0
+    sharp = (M / 0.25) * (4 / W)
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        phi = rng.uniform()
+        u = 0.05 * rng.standard_normal(3)
+        n = rng.standard_normal(3)
+        n /= np.linalg.norm(n)
+        geq = orc.phase_equilibrium(phi, u, n, sharp)
+        assert abs(geq.sum() - phi) < 1e-15
+        np.testing.assert_allclose(geq @ c, phi * u + 4 * M / W * phi * (1 - phi) * n, atol=1e-15)
+
+
+# ---------------------------------------- the step against a textbook scheme
+def _lattice_textbook():
+    """An independent enumeration of D3Q27 (itertools order) with product weights."""
+    w1 = {0: 2 / 3, 1: 1 / 6, -1: 1 / 6}
+    c = np.array(list(itertools.product((-1, 0, 1), repeat=3)))[:, ::-1]  # (cx, cy, cz)
+    w = np.array([w1[a] * w1[b] * w1[d] for a, b, d in c])
+    return c, w
+
+
+def _bgk_guo_step(f, c, w, omega, F):
+    """Textbook BGK with Guo forcing, Eq. 5, p*-form equilibrium, constant force F:
+    f_i(x + c_i, t+1) = f_i + omega (f^eq_i - f_i) + (1 - omega/2) S_i."""
+    p = f.sum(0)
+    u = np.einsum("i...,ia->a...", f, c.astype(float)) + 0.5 * F[:, None, None, None]
+    out = np.empty_like(f)
+    for i in range(len(w)):
+        ci = c[i].astype(float)
+        cu = np.einsum("a,a...->...", ci, u)
+        uu = np.einsum("a...,a...->...", u, u)
+        feq = w[i] * (p + 3 * cu + 4.5 * cu * cu - 1.5 * uu)
+        cF = ci @ F
+        uF = np.einsum("a,a...->...", F, u)
+        S = w[i] * (3 * (cF - uF) + 9 * cu * cF)
+        post = f[i] + omega * (feq - f[i]) + (1 - omega / 2) * S
+        out[i] = np.roll(post, shift=(c[i][2], c[i][1], c[i][0]), axis=(0, 1, 2))
+    return out
+
+
+def _reorder(f_orc, c_orc, c_ref):
+    idx = {tuple(v): k for k, v in enumerate(c_orc.astype(int))}
+    return np.stack([f_orc[idx[tuple(v)]] for v in c_ref.astype(int)])
+
+
+@pytest.mark.parametrize("tau,regularize", [(1.0, True), (0.8, False), (1.7, False)])
+def test_step_reduces_to_textbook_bgk_guo(orc, tau, regularize):
+    """Eq. 7 with the full non-equilibrium part is an algebraic rewrite of Eq. 5;
+    at tau = 1 the regularized term is multiplied by 1 - omega = 0, so the
+    regularized step is Eq. 5 as well.  Single phase (sigma = 0, no
+    sharpening), constant body force, non-equilibrium random start."""
+    nz, ny, nx = 4, 5, 6
+    Fc = np.array([1e-4, -2e-4, 5e-5])
+    o = orc.Oracle(nx, ny, nz, tau, 0.1, INF, 0.0, force_kind=orc.FORCE_CONST, g=Fc,
+                   regularize=regularize)
+    rng = np.random.default_rng(5)
+    u0 = 0.02 * rng.standard_normal((3, nz, ny, nx))
+    o.init(np.zeros((nz, ny, nx)), u0)
+    f0, g0 = o.populations()
+    f0 = f0 * (1 + 0.01 * rng.standard_normal(f0.shape))  # leave equilibrium
+    o.set_populations(f0, g0)
+    c_orc, _ = orc.lattice27()
+    c, w = _lattice_textbook()
+    f = _reorder(f0, c_orc, c)
+    for _ in range(3):
+        o.step(1)
+        f = _bgk_guo_step(f, c, w, 1 / tau, Fc)
+    fo, _ = o.populations()
+    np.testing.assert_allclose(_reorder(fo, c_orc, c), f, rtol=0, atol=2e-15)
+
+
+# ------------------------------------------------------------ invariants
+def test_rest_state_is_preserved(orc):
+    """Uniform phi, u = 0, p* = 1: f and g stay unchanged (200 steps, 1e-14)."""
+    n = 6
+    o = orc.Oracle(n, n, n, 0.8, 0.1, 3.0, 0.01)
+    o.init(np.full((n, n, n), 0.3), np.zeros((3, n, n, n)))
+    f0, g0 = o.populations()
+    o.step(200)
+    f1, g1 = o.populations()
+    assert np.abs(f1 - f0).max() <= 1e-14
+    assert np.abs(g1 - g0).max() <= 1e-14
+
+
+def _smooth_random_fields(shape, seed):
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    phi = np.zeros(shape)
+    for _ in range(3):
+        k = rng.integers(1, 3, size=3)
+        ph = rng.uniform(0, 2 * np.pi, size=3)
+        phi += np.sin(2 * np.pi * k[0] * x / nx + ph[0]) * np.cos(2 * np.pi * k[1] * y / ny + ph[1]) \
+            * np.cos(2 * np.pi * k[2] * z / nz + ph[2])
+    phi = 0.5 + 0.5 * np.tanh(2 * phi)
+    u = np.zeros((3,) + shape)
+    for a in range(3):
+        k = rng.integers(1, 3, size=3)
+        u[a] = 0.02 * np.sin(2 * np.pi * (k[0] * x / nx + k[1] * y / ny + k[2] * z / nz) + rng.uniform(0, 6))
+    return phi, u
+
+
+@pytest.mark.parametrize("force_kind", [0, 1, 2, 3])
+def test_mass_and_phase_conservation(orc, force_kind):
+    """sum p* and sum phi are conserved to round-off every step (sum of the
+    regularized part and of S vanish; sum_i w_i c_i.n = 0)."""
+    shape = (8, 10, 12)
+    phi, u = _smooth_random_fields(shape, 6)
+    o = orc.Oracle(12, 10, 8, 0.7, 0.1, 3.0, 0.02, force_kind=force_kind, g=(1e-5, 0, -1e-5),
+                   A_abc=1e-4, kf=2 * math.pi / 8, T_relax=50)
+    o.init(phi, u)
+    rho0, _, phi0 = o.moments()
+    m0, p0 = rho0.sum(), phi0.sum()
+    for _ in range(20):
+        o.step(1)
+        rho, _, ph = o.moments()
+        assert abs(rho.sum() - m0) <= 1e-12 * abs(m0)
+        assert abs(ph.sum() - p0) <= 1e-12 * abs(p0)
+
+
+@pytest.mark.parametrize("force_kind", [0, 1, 2, 3])
+def test_momentum_balance(orc, force_kind):
+    """P(t+1) - P(t) = sum_x F(x, t) with P = sum_x sum_i f_i c_i (Guo force, Eq. 6/7)."""
+    shape = (8, 10, 12)
+    phi, u = _smooth_random_fields(shape, 7)
+    o = orc.Oracle(12, 10, 8, 0.9, 0.1, 3.0, 0.02, force_kind=force_kind, g=(1e-5, 2e-5, -1e-5),
+                   A_abc=1e-4, kf=2 * math.pi / 8, T_relax=50)
+    o.init(phi, u)
+    c, _ = orc.lattice27()
+    c = c.astype(float)
+    for _ in range(5):
+        f, _ = o.populations()
+        P0 = f.reshape(27, -1).sum(1) @ c
+        o.step(1)
+        F = o.last_force()
+        f, _ = o.populations()
+        P1 = f.reshape(27, -1).sum(1) @ c
+        np.testing.assert_allclose(P1 - P0, F.reshape(3, -1).sum(1), atol=1e-13)
+
+
+def test_axis_permutation_equivariance(orc):
+    """Swapping the x and z axes of every input swaps them in every output
+    (catches stride and index mistakes in the stencils and streaming)."""
+    nz, ny, nx = 6, 7, 9
+    phi, u = _smooth_random_fields((nz, ny, nx), 8)
+    a = orc.Oracle(nx, ny, nz, 0.8, 0.1, 3.0, 0.02)
+    a.init(phi, u)
+    a.step(4)
+    ra, ua, pa = a.moments()
+    phiT = np.ascontiguousarray(phi.transpose(2, 1, 0))
+    uT = np.ascontiguousarray(u[::-1].transpose(0, 3, 2, 1))
+    b = orc.Oracle(nz, ny, nx, 0.8, 0.1, 3.0, 0.02)
+    b.init(phiT, uT)
+    b.step(4)
+    rb, ub, pb = b.moments()
+    np.testing.assert_allclose(rb.transpose(2, 1, 0), ra, atol=1e-14)
+    np.testing.assert_allclose(pb.transpose(2, 1, 0), pa, atol=1e-14)
+    np.testing.assert_allclose(ub[::-1].transpose(0, 3, 2, 1), ua, atol=1e-14)
+
+
+def test_abc_force_is_a_beltrami_field(orc):
+    """The ABC force of Sec. 5.1 (uniform phi, sigma = 0, u = 0 so F = F^ext) is
+    divergence-free with curl F = k_f F, checked with spectral derivatives."""
+    n = 16
+    kf = 2 * math.pi * 2 / n
+    o = orc.Oracle(n, n, n, 0.8, 0.1, INF, 0.0, force_kind=orc.FORCE_ABC, A_abc=1e-3, kf=kf)
+    o.init(np.zeros((n, n, n)), np.zeros((3, n, n, n)))
+    o.step(1)
+    F = o.last_force()
+    k = 2 * math.pi * np.fft.fftfreq(n, d=1.0)
+    KZ, KY, KX = np.meshgrid(k, k, k, indexing="ij")
+    Fh = [np.fft.fftn(F[a]) for a in range(3)]
+
+    def d(fh, K):
+        return np.real(np.fft.ifftn(1j * K * fh))
+
+    div = d(Fh[0], KX) + d(Fh[1], KY) + d(Fh[2], KZ)
+    curl = np.stack([d(Fh[2], KY) - d(Fh[1], KZ), d(Fh[0], KZ) - d(Fh[2], KX), d(Fh[1], KX) - d(Fh[0], KY)])
+    assert np.abs(div).max() < 1e-15
+    np.testing.assert_allclose(curl, kf * F, atol=1e-15)
+    assert np.abs(F).max() > 1e-3
+
+
+# ------------------------------------------------------------ physics laws
+@pytest.mark.parametrize("tau", [0.6, 1.0, 1.5])
+def test_taylor_green_viscosity(orc, tau):
+    """Sec. 2.2: nu = cs^2 (tau - 1/2).  A 2D Taylor-Green vortex in a 64 x 64 box
+    decays as K ~ exp(-4 nu k^2 t); the fitted rate is within 1% (after a
+    20-step transient from the zero non-equilibrium start)."""
+    n = 64
+    o = orc.Oracle(n, n, 1, tau, 0.1, INF, 0.0)
+    o.init(np.zeros((1, n, n)), inputs.taylor_green(n, n, 1, 0.01))
+    ts, Ks = [], []
+    for _ in range(220):
+        o.step(1)
+        ts.append(o.time - 1)
+        Ks.append(o.diagnostics()[1])
+    ts, Ks = np.array(ts), np.array(Ks)
+    sel = ts >= 20
+    rate = -np.polyfit(ts[sel], np.log(Ks[sel]), 1)[0]
+    k = 2 * math.pi / n
+    expected = 4 * (tau - 0.5) / 3 * k * k
+    assert abs(rate / expected - 1) < 0.01
+
+
+def test_allen_cahn_diffusion_rate(orc):
+    """Without sharpening (W = inf) and u = 0, Eq. 4 is diffusion with D = M:
+    a sine perturbation decays as exp(-M k^2 t) (within 1%)."""
+    n, M = 64, 0.05
+    k = 2 * math.pi / n
+    x = np.arange(n)
+    phi = np.broadcast_to(0.5 + 0.1 * np.sin(k * x), (1, 1, n)).copy()
+    o = orc.Oracle(n, 1, 1, 0.8, M, INF, 0.0)
+    o.init(phi, np.zeros((3, 1, 1, n)))
+    amps, ts = [], []
+    for _ in range(40):
+        o.step(25)
+        _, _, ph = o.moments()
+        amps.append(2 * np.abs(np.fft.rfft(ph[0, 0] - 0.5))[1] / n)
+        ts.append(o.time)
+    rate = -np.polyfit(ts, np.log(amps), 1)[0]
+    assert abs(rate / (M * k * k) - 1) < 0.01
+
+
+def test_tanh_interface_is_the_steady_state(orc):
+    """A planar slab started with twice the interface width relaxes to the
+    profile 1/2 +- 1/2 tanh(2 d / W) (the 1D steady state of Eq. 4 with
+    kappa = 4D/W); the error is below 2e-2 at W = 3 and decreases with W."""
+    n = 96
+    errs = []
+    for W in (3.0, 5.0, 8.0):
+        x0, x1 = 24.0, 72.0
+        phi = inputs.slab(n, 1, 1, 2 * W, x0, x1)
+        o = orc.Oracle(n, 1, 1, 0.8, 0.1, W, 0.0)
+        o.init(phi, np.zeros((3, 1, 1, n)))
+        o.step(2000)
+        _, _, ph = o.moments()
+        x = np.arange(n)
+        d = np.abs(x - 0.5 * (x0 + x1))
+        target = 0.5 - 0.5 * np.tanh(2 * (d - 0.5 * (x1 - x0)) / W)
+        errs.append(np.abs(ph[0, 0] - target).max())
+    assert errs[0] < 2e-2
+    assert errs[0] > errs[1] > errs[2]
+
+
+def test_curvature_of_a_sphere(orc):
+    """kappa = div n equals -2/R on the phi = 1/2 shell of a sphere (n points
+    into the phi = 1 phase), within 3% for R = 12, 16."""
+    n = 48
+    for R in (12.0, 16.0):
+        phi = inputs.droplet(n, n, n, R, 3.0)
+        _, nrm, kappa, _ = orc.interface(phi, 3.0, 0.01)
+        shell = np.abs(phi - 0.5) < 0.1
+        assert np.abs(kappa[shell] / (-2 / R) - 1).max() < 0.03
+        # unit normal where the gradient is resolved
+        norm = np.sqrt((nrm ** 2).sum(0))
+        assert np.abs(norm[shell] - 1).max() < 1e-12
+
+
+def test_surface_force_points_inward_and_sums_to_zero(orc):
+    """F^s = -(3W/2) sigma kappa |grad phi| grad phi pushes the interface of a
+    phi = 1 droplet inward and has zero net force on a centred droplet."""
+    n = 32
+    phi = inputs.droplet(n, n, n, 8.0, 3.0)
+    _, _, _, Fs = orc.interface(phi, 3.0, 0.01)
+    c = (n - 1) / 2
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r = np.stack([x - c, y - c, z - c])
+    radial = (Fs * r).sum(0)
+    shell = np.abs(phi - 0.5) < 0.4
+    assert np.all(radial[shell] < 0)
+    assert np.abs(Fs.reshape(3, -1).sum(1)).max() < 1e-14
+
+
+def _laplace_jump(orc, edge, R, steps=400, window=200, every=20):
+    """Time-averaged dp = cs^2 (<p*>_{r < R-2W} - <p*>_{r > R+2W}) of a static droplet
+    (tau = 1, M = 0.1, W = 3, sigma = 0.01) over the last `window` steps."""
+    w = inputs.static_droplet(edge=edge, R=R)
+    o = orc.Oracle(edge, edge, edge, w.tau, w.M, w.W, w.sigma)
+    o.init(w.phi, w.u)
+    c = (edge - 1) / 2
+    z, y, x = np.meshgrid(*[np.arange(edge)] * 3, indexing="ij")
+    d = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
+    o.step(steps - window)
+    dps, umax = [], 0.0
+    for _ in range(window // every):
+        o.step(every)
+        rho, u, _ = o.moments()
+        dps.append((rho[d < R - 2 * w.W].mean() - rho[d > R + 2 * w.W].mean()) / 3)
+        umax = max(umax, float(np.sqrt((u ** 2).sum(0)).max()))
+    return float(np.mean(dps)), umax, w.sigma
+
+
+def test_laplace_law(orc):
+    """A static droplet carries the pressure jump dp = 2 sigma/R (Laplace).  On a
+    W = 3 interface the lattice central difference resolves |grad phi|^2 about
+    10% low (transfer function sin(k)/k at k ~ 2/W), so dp is expected 5-15%
+    below 2 sigma/R; dp R must not depend on R (R = 8 and 10 agree within 4%),
+    and spurious currents stay below 1e-3."""
+    res = {}
+    for edge, R in ((32, 8.0), (40, 10.0)):
+        dp, umax, sigma = _laplace_jump(orc, edge, R)
+        ratio = dp / (2 * sigma / R)
+        assert 0.85 < ratio < 1.0, (R, ratio)
+        assert umax < 1e-3
+        res[R] = dp * R
+    assert abs(res[8.0] / res[10.0] - 1) < 0.04
+
+
+def test_linear_forcing_holds_kinetic_energy(orc):
+    """Linear forcing F = A u with A_{t+1} = [eps_t + (K_target - K_t)/T]/(2 K_t):
+    starting from A = 0, K settles within 2% of K_target after 5 T (sigma = 0)."""
+    n = 16
+    u = inputs.solenoidal_velocity(n, n, n, 0.02, seed=11)
+    T = 40.0
+    o = orc.Oracle(n, n, n, 0.6, 0.1, INF, 0.0, force_kind=orc.FORCE_LINEAR, T_relax=T)
+    o.init(np.zeros((n, n, n)), u)
+    K0 = 0.5 * (u ** 2).sum()
+    o.step(int(5 * T))
+    K = o.diagnostics()[1]
+    assert abs(K / K0 - 1) < 0.02
+    # without forcing the same flow loses a large share of its energy
+    f = orc.Oracle(n, n, n, 0.6, 0.1, INF, 0.0)
+    f.init(np.zeros((n, n, n)), u)
+    f.step(int(5 * T))
+    assert f.diagnostics()[1] < 0.7 * K0
