@@ -1,0 +1,310 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused two-phase lattice Boltzmann step on GB300.
+
+Workload (default): 256^3 periodic forced homogeneous isotropic turbulence
+with 64 bubbles of radius 10 (seeded, non-overlapping), interface width W = 3,
+sigma = 0.01, tau = 0.51, M = 0.1, solenoidal initial velocity from Fourier
+modes 1 <= |k| <= 4 with u_rms = 0.02, linear forcing holding the kinetic
+energy; FP32 population storage.  A "step" is one full time step of the box
+(the fused kernel plus the FP64 reduction).  The metric is MLUPS (million
+lattice-site updates per second, the paper's GLUPS x 1000) and the fraction of
+the measured HBM bandwidth reached by the fused kernel.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                       [--storage f32|f16|bf16] [--edge E]
+Under torchrun (N > 1) every rank advances its own replica box (weak scaling,
+no collective on the data path); value = sum of sites*steps over ranks divided
+by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2505_01126_gb300 import inputs  # noqa: E402
+
+METRIC = "two-phase MLUPS & % HBM roofline, FP32 vs 16-bit storage at stated error"
+UNIT = "MLUPS"
+# the oracle's sample for the CPU baseline: same recipe, 128^3 box with 8 bubbles
+# (the 256^3 box's 64 bubbles at the same volume fraction)
+SAMPLE_EDGE, SAMPLE_BUBBLES, SAMPLE_STEPS = 128, 8, 10
+# the reference arm's per-step sample: 64^3 box of the same recipe (1 bubble)
+REF_EDGE = 64
+
+
+def workload(edge: int):
+    nb = max(1, round(64 * (edge / 256) ** 3))
+    return inputs.bubbly_hit(edge, nb, 10.0, seed=2), nb
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline_sample():
+    """Time the oracle (as it stands) on a bounded sample of the workload."""
+    import oracle
+
+    oracle.build()
+    w, _ = workload(SAMPLE_EDGE)
+    n = SAMPLE_EDGE
+    o = oracle.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma, force_kind=oracle.FORCE_LINEAR, T_relax=w.T_relax)
+    o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
+    o.step(1)  # first touch of the arrays
+    t0 = time.perf_counter()
+    o.step(SAMPLE_STEPS)
+    dt = time.perf_counter() - t0
+    o.close()
+    value = n ** 3 * SAMPLE_STEPS / dt / 1e6
+    return {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{n}^3 box of the same recipe ({SAMPLE_BUBBLES} bubbles R=10, u_rms 0.02, tau 0.51, "
+                      f"linear forcing), {SAMPLE_STEPS} FP64 oracle steps after 1 untimed step, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, each step one oracle step of
+    the 128^3 sample of the workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    w, nb = workload(REF_EDGE)
+    n = REF_EDGE
+    o = oracle.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma, force_kind=oracle.FORCE_LINEAR, T_relax=w.T_relax)
+    o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = n ** 3 * args.steps / dt / 1e6
+    sample = (f"{n}^3 box of the same recipe ({nb} bubble R=10, u_rms 0.02, tau 0.51, linear forcing), "
+              f"one FP64 oracle step per bench step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{n}^3 sample of the 256^3 periodic bubbly forced HIT workload "
+                                   f"(bubbles R=10, W=3, sigma=0.01, tau=0.51, M=0.1, u_rms=0.02, linear forcing)",
+                       "edge": n, "bubbles": nb, "storage": "f64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--edge", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank, world, local = dist_env()
+    import torch
+
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    from paper_2505_01126_gb300 import build
+
+    if rank == 0:
+        build.build()
+    barrier()
+    from paper_2505_01126_gb300 import lbgb
+
+    w, nb = workload(args.edge)
+    n = args.edge
+    N = n ** 3
+    force = lbgb.Force(kind=lbgb.LB_FORCE_LINEAR, T_relax=w.T_relax)
+    stream = torch.cuda.Stream()
+    box = lbgb.Box(n, n, n, w.tau, w.M, w.W, w.sigma, force=force, storage=args.storage, stream=stream)
+    if not args.no_tune:
+        os.environ.setdefault("LBGB_TUNE_CACHE", os.path.join(ROOT, "paper_2505_01126_gb300", "tune_cache.txt"))
+        box.tune(3)
+    ty, zc = box.tile()
+    phi_d = torch.from_numpy(w.phi).cuda()
+    u_d = torch.from_numpy(w.u).cuda()
+    box.init(phi_d, u_d)
+    box.step(args.warmup)
+    box.sync()
+
+    # ---- device-resident timed region (kernel events on the library's stream)
+    box.set_timing(True)
+    launches0 = box.launches
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    box.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop() if clocks else None
+    ms = e0.elapsed_time(e1)
+    kern_ms, kern_n = box.kernel_time()
+    launches = box.launches - launches0
+    box.set_timing(False)
+    diag = box.diagnostics(allow_nonfinite=True)
+
+    # max over ranks
+    t_max = ms
+    if pg is not None:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = N * args.steps * world / (t_max * 1e-3) / 1e6
+
+    # ---- end to end through the public API with pinned host buffers
+    phi_h = torch.from_numpy(w.phi).pin_memory()
+    u_h = torch.from_numpy(w.u).pin_memory()
+    rho_o = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
+    u_o = torch.empty((3, n, n, n), dtype=torch.float32).pin_memory()
+    phi_o = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
+    e2e_steps = args.steps
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    box.init(phi_h.numpy(), u_h.numpy())
+    for _ in range(e2e_steps):
+        box.step(1)
+        box.diagnostics(allow_nonfinite=True)  # per-step result read back (40 bytes)
+    box.moments(rho_o.numpy(), u_o.numpy(), phi_o.numpy())
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if pg is not None:
+        t = torch.tensor([t_e2e], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e_value = N * e2e_steps * world / t_e2e / 1e6
+    h2d = 4 * N * 4 / e2e_steps
+    d2h = 40 + 5 * N * 4 / e2e_steps
+
+    if rank == 0:
+        peak, peak_kind = peaks()
+        bps = box.bytes_per_site
+        kern_avg_s = kern_ms / max(kern_n, 1) * 1e-3
+        achieved = bps * N / kern_avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "fused_step_kernel", "bytes_per_site": bps,
+                "kernel_ms_avg": kern_avg_s * 1e3, "peak_source": peak_kind}
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            try:
+                cpu = cpu_baseline_sample()
+            except Exception as ex:  # report, do not fail the benchmark line
+                cpu = {"error": str(ex)}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+                "config": {"workload": f"{n}^3 periodic bubbly forced HIT, {nb} bubbles R=10, W=3, sigma=0.01, "
+                                       f"tau={w.tau}, M=0.1, u_rms=0.02, linear forcing",
+                           "edge": n, "storage": args.storage, "tile": [32, ty, zc],
+                           "l2": "inputs larger than L2 (populations %.2f GB), no flush" % (bps * N / 2 / 1e9),
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "note": "lb_init from pinned host fields, K x (lb_step(1) + lb_diagnostics), "
+                                "lb_moments to pinned host"},
+                "clocks": clk, "gpu_launches": launches,
+                "diagnostics": {"Phi": diag[0], "K": diag[1], "eps": diag[2], "umax": diag[3], "A": diag[4]}}
+        print(json.dumps(line), flush=True)
+    box.close()
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

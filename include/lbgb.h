@@ -1,0 +1,173 @@
+/*
+ * lbgb.h -- C ABI of the GB300 (sm_103a) two-phase lattice Boltzmann library.
+ *
+ * The library advances one periodic box (or a batch of independent boxes) by
+ * the fused per-site time step of accLB (arXiv 2505.01126, Sec. 2):
+ *   1. phi = sum_q g_q                  (D3Q7 phase populations)
+ *   2. grad phi with the lattice stencil of Sec. 2.3
+ *   3. n = grad phi / max(|grad phi|, 1e-10)
+ *   4. kappa = div n (same stencil, so phi is read within radius 2)
+ *   5. surface tension F^s = -(3W/2) sigma kappa |grad phi| grad phi (Sec. 2.3)
+ *   6. external force: none, constant, ABC (Sec. 5.1) or linear A_t u
+ *   7. hydrodynamic moments p* = sum f, m = sum f c, Pi = sum f c c (Sec. 2.2)
+ *   8. u = (m + (F^s + F^ext)/2) / (1 - A_t/2), F = F^s + F^ext + A_t u
+ *   9. a2 = Pi - cs^2 p* I - u u + (u F + F u)/2   (Eq. 8 in closed form)
+ *  10. f*_i = w_i [p* + c_i.u/cs^2 + H_i:(u u + (1-omega) a2)/(2 cs^4)] + S_i/2
+ *      (Eq. 7 with the Hermite-regularized non-equilibrium; S_i is Eq. 6)
+ *  11. g*_q = g_q + omega_phi (g^eq_q - g_q),
+ *      g^eq_q = w_q phi (1 + c_q.u/cs7^2) + w_q (M/cs7^2)(4/W) phi (1-phi) c_q.n
+ *      (D3Q7 BGK whose Chapman-Enskog limit is the Allen-Cahn Eq. 4, D = M)
+ *  12. streaming f_i(x + c_i) <- f*_i, g_q(x + c_q) <- g*_q, periodic
+ *  13. FP64 reductions Phi = sum phi, K = 1/2 sum |u|^2,
+ *      eps = 2 nu sum S:S with S = -a2/(2 cs^2 tau), max|u|, and the next
+ *      linear-forcing amplitude A_{t+1} = [eps + (K_target - K)/T_relax]/(2K).
+ * D3Q27: cs^2 = 1/3, weights 8/27, 2/27, 1/54, 1/216.  D3Q7: cs7^2 = 1/4,
+ * weights 1/4 (rest), 1/8.  nu = cs^2 (tau - 1/2) (Sec. 2.2).
+ *
+ * Conventions for every call:
+ *  - Fields are FP32 structure-of-arrays over the site index
+ *    s = x + nx*(y + ny*z) (x fastest); a vector field is three consecutive
+ *    planes (ux | uy | uz), 3*N floats.
+ *  - Field pointers may be host or device memory (the library asks the CUDA
+ *    runtime which); they are borrowed for the duration of the call only and
+ *    never freed by the library.  Device pointers must belong to the current
+ *    device.  Host pointers make the call synchronous.
+ *  - Every call that can fail returns LB_OK (0) or a negative LB_E* code and
+ *    records a message for lb_last_error().  No exception, trap or device
+ *    assert crosses the ABI.
+ *  - Work is queued on the context's stream (default: the legacy default
+ *    stream; see lb_set_stream).  lb_step is asynchronous.
+ */
+#ifndef LBGB_H
+#define LBGB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ return codes */
+#define LB_OK 0
+#define LB_EINVAL (-1)     /* invalid argument (sizes, parameters, NULL, state) */
+#define LB_ENOMEM (-2)     /* device allocation failed */
+#define LB_ECUDA (-3)      /* a CUDA runtime call or kernel launch failed */
+#define LB_ENONFINITE (-4) /* a NaN/Inf was seen by the step's reductions */
+#define LB_ESTATE (-5)     /* call out of order (e.g. lb_step before lb_init) */
+
+/* ---------------------------------------------------- population storage */
+#define LB_F32 0          /* f and g stored as FP32 */
+#define LB_F16_SHIFTED 1  /* f stored as FP16 (f_i - w_i)/w_i, g FP32; FP32 math */
+#define LB_BF16_SHIFTED 2 /* f stored as BF16 (f_i - w_i)/w_i, g FP32; FP32 math */
+
+/* ------------------------------------------------------------ forcing */
+#define LB_FORCE_NONE 0
+#define LB_FORCE_CONST 1  /* F^ext = g (uniform body force) */
+#define LB_FORCE_ABC 2    /* F^ext = A (sin kz + cos ky, sin kx + cos kz, sin ky + cos kx), Sec. 5.1 */
+#define LB_FORCE_LINEAR 3 /* F^ext = A_t u with the kinetic-energy controller of step 13 */
+
+typedef struct lb_force {
+    int kind;        /* LB_FORCE_* */
+    double g[3];     /* LB_FORCE_CONST: force per site, lattice units */
+    double A;        /* LB_FORCE_ABC: amplitude */
+    double kf;       /* LB_FORCE_ABC: wavenumber in radians per lattice spacing */
+    double K_target; /* LB_FORCE_LINEAR: target K = 1/2 sum |u|^2; <= 0 takes the K of lb_init's u */
+    double T_relax;  /* LB_FORCE_LINEAR: relaxation time of the controller in steps (> 0) */
+} lb_force;
+
+typedef struct lb_ctx lb_ctx;
+
+/*
+ * lb_create -- allocate a periodic nx*ny*nz box on the current CUDA device.
+ *   tau    hydrodynamic relaxation time, > 1/2 (Sec. 2.2: nu = (tau - 1/2)/3)
+ *   M      phase-field mobility D = M of Eq. 4, > 0 (omega_phi = 1/(4M + 1/2))
+ *   W      interface width delta of Eq. 4, > 0; +INFINITY switches the
+ *          sharpening flux off (then sigma must be 0)
+ *   sigma  surface tension, >= 0
+ *   force  NULL for no external force
+ *   storage  LB_F32, LB_F16_SHIFTED or LB_BF16_SHIFTED
+ * The context owns the populations (f: 27 planes, in place with the AA access
+ * pattern; g: two buffers of 7 planes), the reduction scratch and the device
+ * state.  Sizes: 1 <= nx, ny, nz and nx*ny*nz*27 < 2^63.
+ * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA; *out is set to NULL on error.
+ */
+int lb_create(int nx, int ny, int nz, double tau, double M, double W, double sigma,
+              const lb_force* force, int storage, lb_ctx** out);
+
+/* Use `stream` (a cudaStream_t, e.g. torch.cuda.Stream.cuda_stream) for all
+ * later work of this context; NULL selects the legacy default stream. */
+int lb_set_stream(lb_ctx* ctx, void* stream);
+
+/*
+ * lb_init -- set the state at t = 0 from phi (N floats) and u (3N floats):
+ * n from phi (steps 2-3), f_i = f^eq_i(p* = 1, u), g_q = g^eq_q(phi, u, n).
+ * u is the physical velocity.  Resets t, the forcing amplitude (A_0 = 0) and,
+ * for LB_FORCE_LINEAR with K_target <= 0, sets K_target = 1/2 sum |u|^2 (FP64).
+ */
+int lb_init(lb_ctx* ctx, const float* phi, const float* u);
+
+/* lb_step -- advance n >= 0 full time steps (steps 1-13), asynchronously.
+ * Runs of two or more steps replay a captured CUDA graph. */
+int lb_step(lb_ctx* ctx, int n);
+
+/*
+ * lb_moments -- fields at the current time t: rho = p* = sum f (N floats),
+ * u = the forced velocity of step 8 (3N floats), phi = sum g (N floats).
+ * Any output may be NULL.  Waits for completion when an output is host memory.
+ */
+int lb_moments(lb_ctx* ctx, float* rho, float* u, float* phi);
+
+/*
+ * lb_diagnostics -- FP64 reductions of the most recent step (of lb_init's
+ * fields before the first step): out = {Phi, K, eps, max|u|, A_next}.
+ * Synchronises the context's stream.  Returns LB_ENONFINITE (out still
+ * filled) if any step since lb_init met a NaN or Inf.
+ */
+int lb_diagnostics(lb_ctx* ctx, double out[5]);
+
+/* Wait for the context's queued work; LB_ECUDA if a kernel failed. */
+int lb_sync(lb_ctx* ctx);
+
+/* Steps taken since lb_init. */
+long long lb_time(const lb_ctx* ctx);
+
+/* Launch shape of the fused step kernel: tile height ty (x tile is 32 sites)
+ * in {4, 8, 16} and z-chunk zc >= 1 planes per block.  Takes effect at the
+ * next lb_step; lb_tune picks it by measurement. */
+int lb_set_tile(lb_ctx* ctx, int ty, int zc);
+int lb_get_tile(const lb_ctx* ctx, int* ty, int* zc);
+
+/*
+ * lb_tune -- time every supported (ty, zc) on a scratch box with this box's
+ * nx, ny, storage and min(nz, 128) planes, for `steps` steps each, and keep
+ * the fastest.  Allocates and frees its scratch; the context's state is not
+ * touched.  Results are cached per (device name, nx, ny, nz, storage) in the
+ * file named by LBGB_TUNE_CACHE, if set.
+ */
+int lb_tune(lb_ctx* ctx, int steps);
+
+/* Algorithmic bytes moved per site per step by the fused kernel (population
+ * reads and writes): 27*2*sizeof(f) + 7*2*sizeof(g). */
+double lb_bytes_per_site(const lb_ctx* ctx);
+
+/* Free everything the context owns.  NULL is ignored. */
+void lb_destroy(lb_ctx* ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* lb_last_error(void);
+
+/* Kernel launches queued by the library since the context was created. */
+long long lb_launch_count(const lb_ctx* ctx);
+
+/*
+ * Kernel timing.  While on (on != 0), lb_step launches step by step (no
+ * graph) and records a CUDA event pair on the context's stream around every
+ * fused step kernel.  lb_kernel_time waits for the stream, returns the summed
+ * kernel time in milliseconds and the number of timed launches since timing
+ * was switched on, and keeps timing on.  Turning timing on again resets both.
+ */
+int lb_set_timing(lb_ctx* ctx, int on);
+int lb_kernel_time(lb_ctx* ctx, double* ms, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBGB_H */

@@ -1,0 +1,605 @@
+// lbgb_api.cu -- C ABI of the fused two-phase lattice Boltzmann library (see
+// include/lbgb.h for the contract of each call).
+//
+// A context owns, on one device: f (27 planes, in place, AA pattern), g (two
+// buffers of 7 planes), the per-block FP64 partial sums, a small DevState
+// (forcing amplitude, K_target, last diagnostics, non-finite flag), the ABC
+// sin/cos tables and, on demand, staging buffers for host-pointer I/O.
+// A step is two launches on the context's stream: the fused step kernel and a
+// one-block FP64 reduction that also updates the forcing amplitude on the
+// device, so consecutive steps need no host synchronisation and can be
+// captured in a CUDA graph (two steps, one of each AA parity).
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lbgb.h"
+#include "lbgb_kernels.cuh"
+
+using namespace lbgb;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define LB_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA, "%s: %s", \
+                        #call, cudaGetErrorString(e_));                                   \
+    } while (0)
+
+struct FinalizeArgs {
+    int mode;        // MODE_STEP or MODE_INIT
+    int force_kind;
+    double nu, tau, T_relax, K_target_param;
+};
+
+// One block: deterministic FP64 sum of the per-block partials, then the
+// diagnostics (step 13) and the next linear-forcing amplitude.
+__global__ void __launch_bounds__(256) finalize_kernel(const double* __restrict__ part, int nblk,
+                                                       DevState* st, FinalizeArgs fa) {
+    double v0 = 0, v1 = 0, v2 = 0, v3 = 0, v4 = 0;
+    for (int b = threadIdx.x; b < nblk; b += 256) {
+        const double* p = part + (long long)b * NPART;
+        v0 += p[0];
+        v1 += p[1];
+        v2 += p[2];
+        v3 = fmax(v3, p[3]);
+        v4 = fmax(v4, p[4]);
+    }
+    block_reduce5<256>(v0, v1, v2, v3, v4);
+    if (threadIdx.x == 0) {
+        const double Phi = v0, K = v1;
+        if (fa.mode == MODE_INIT) {
+            st->K_target = fa.K_target_param > 0 ? fa.K_target_param : K;
+            st->A = 0.0;
+            st->diag[0] = Phi; st->diag[1] = K; st->diag[2] = 0.0; st->diag[3] = v3; st->diag[4] = 0.0;
+            st->flags = v4 > 0 ? 1 : 0;
+        } else {
+            // eps = 2 nu sum S:S, S = -a2/(2 cs^2 tau) = -(3/(2 tau)) a2
+            const double s = 1.5 / fa.tau;
+            const double eps = 2.0 * fa.nu * s * s * v2;
+            double An = 0.0;
+            if (fa.force_kind == FK_LINEAR && K > 0) An = (eps + (st->K_target - K) / fa.T_relax) / (2.0 * K);
+            st->diag[0] = Phi; st->diag[1] = K; st->diag[2] = eps; st->diag[3] = v3; st->diag[4] = An;
+            st->A = An;
+            if (v4 > 0) st->flags |= 1;
+        }
+    }
+}
+
+bool is_device_pointer(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct lb_ctx {
+    int nx, ny, nz;
+    long long N;
+    double tau, M, W, sigma;
+    lb_force force;
+    int storage;
+    size_t fsize;  // bytes per stored f value
+    int device;
+
+    void* f = nullptr;
+    float* g[2] = {nullptr, nullptr};
+    double* partials = nullptr;
+    long long npart_cap = 0;
+    DevState* st = nullptr;
+    float* abc = nullptr;
+    float* stage = nullptr;  // 5N floats for host I/O, allocated on demand
+    cudaStream_t stream = nullptr;
+
+    long long t = 0;
+    bool initialized = false;
+    int ty = 8, zc = 32;
+    long long launches = 0;
+
+    cudaGraphExec_t graph = nullptr;  // two steps starting at even parity
+    int graph_ty = 0, graph_zc = 0;
+
+    bool timing = false;                       // event pairs around fused launches
+    std::vector<cudaEvent_t> ev_start, ev_stop;
+    size_t ev_used = 0;
+};
+
+namespace {
+
+dim3 grid_for(const lb_ctx* c, int ty, int zc) {
+    return dim3((unsigned)((c->nx + 31) / 32), (unsigned)((c->ny + ty - 1) / ty),
+                (unsigned)((c->nz + zc - 1) / zc));
+}
+
+StepArgs base_args(const lb_ctx* c) {
+    StepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.zc = c->zc;
+    a.N = c->N;
+    a.f = c->f;
+    a.force_kind = c->force.kind;
+    a.omega = (float)(1.0 / c->tau);
+    a.omega_phi = (float)(1.0 / (c->M / 0.25 + 0.5));
+    a.sharp = isinf(c->W) ? 0.f : (float)((c->M / 0.25) * (4.0 / c->W));
+    a.beta = c->sigma == 0 ? 0.f : (float)(1.5 * c->W * c->sigma);
+    a.gc0 = (float)c->force.g[0]; a.gc1 = (float)c->force.g[1]; a.gc2 = (float)c->force.g[2];
+    a.A_abc = (float)c->force.A;
+    a.abc = c->abc;
+    a.st = c->st;
+    a.partials = c->partials;
+    return a;
+}
+
+cudaError_t launch_any(const lb_ctx* c, int mode, int parity, int ty, dim3 grid, const StepArgs& a,
+                       cudaStream_t s) {
+    switch (c->storage) {
+        case LB_F32: return launch_fused<float>(mode, parity, ty, grid, a, s);
+        case LB_F16_SHIFTED: return launch_fused<__half>(mode, parity, ty, grid, a, s);
+        case LB_BF16_SHIFTED: return launch_fused<__nv_bfloat16>(mode, parity, ty, grid, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+FinalizeArgs fin_args(const lb_ctx* c, int mode) {
+    FinalizeArgs fa;
+    fa.mode = mode;
+    fa.force_kind = c->force.kind;
+    fa.tau = c->tau;
+    fa.nu = (c->tau - 0.5) / 3.0;
+    fa.T_relax = c->force.T_relax;
+    fa.K_target_param = c->force.K_target;
+    return fa;
+}
+
+// One time step at parity `par` on stream s (2 launches).
+int enqueue_step(lb_ctx* c, int par, cudaStream_t s) {
+    StepArgs a = base_args(c);
+    a.zc = c->zc;
+    a.g_in = c->g[par];
+    a.g_out = c->g[par ^ 1];
+    const dim3 grid = grid_for(c, c->ty, c->zc);
+    const long long nblk = (long long)grid.x * grid.y * grid.z;
+    if (nblk > c->npart_cap) return fail(LB_EINVAL, "tile (%d,%d) needs %lld partials > %lld", c->ty, c->zc, nblk, c->npart_cap);
+    const bool timed = c->timing && s == c->stream;
+    if (timed) {
+        if (c->ev_used == c->ev_start.size()) {
+            cudaEvent_t e0, e1;
+            LB_CUDA(cudaEventCreate(&e0));
+            LB_CUDA(cudaEventCreate(&e1));
+            c->ev_start.push_back(e0);
+            c->ev_stop.push_back(e1);
+        }
+        LB_CUDA(cudaEventRecord(c->ev_start[c->ev_used], s));
+    }
+    LB_CUDA(launch_any(c, MODE_STEP, par, c->ty, grid, a, s));
+    if (timed) {
+        LB_CUDA(cudaEventRecord(c->ev_stop[c->ev_used], s));
+        c->ev_used += 1;
+    }
+    finalize_kernel<<<1, 256, 0, s>>>(c->partials, (int)nblk, c->st, fin_args(c, MODE_STEP));
+    LB_CUDA(cudaGetLastError());
+    c->launches += 2;
+    return LB_OK;
+}
+
+void drop_graph(lb_ctx* c) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+}
+
+int capture_graph(lb_ctx* c) {
+    drop_graph(c);
+    cudaStream_t cs;
+    LB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return fail(LB_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+    }
+    long long before = c->launches;
+    int rc = enqueue_step(c, 0, cs);
+    if (rc == LB_OK) rc = enqueue_step(c, 1, cs);
+    c->launches = before;  // captured launches are counted when replayed
+    e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (rc != LB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(LB_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph = nullptr;
+        return fail(LB_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    }
+    c->graph_ty = c->ty;
+    c->graph_zc = c->zc;
+    return LB_OK;
+}
+
+int ensure_stage(lb_ctx* c) {
+    if (!c->stage) LB_CUDA(cudaMalloc(&c->stage, (size_t)c->N * 5 * sizeof(float)));
+    return LB_OK;
+}
+
+int check_tile(int ty, int zc) {
+    if (ty != 4 && ty != 8 && ty != 16) return fail(LB_EINVAL, "tile height %d not in {4, 8, 16}", ty);
+    if (zc < 1) return fail(LB_EINVAL, "z chunk %d < 1", zc);
+    return LB_OK;
+}
+
+long long max_blocks(const lb_ctx* c) {
+    // the smallest tile (ty = 4) with zc = 1 bounds every configuration
+    return (long long)((c->nx + 31) / 32) * ((c->ny + 3) / 4) * c->nz;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lb_last_error(void) { return g_err; }
+
+void lb_destroy(lb_ctx* c) {
+    if (!c) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    drop_graph(c);
+    for (auto e : c->ev_start) cudaEventDestroy(e);
+    for (auto e : c->ev_stop) cudaEventDestroy(e);
+    cudaFree(c->f);
+    cudaFree(c->g[0]);
+    cudaFree(c->g[1]);
+    cudaFree(c->partials);
+    cudaFree(c->st);
+    cudaFree(c->abc);
+    cudaFree(c->stage);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete c;
+}
+
+int lb_create(int nx, int ny, int nz, double tau, double M, double W, double sigma, const lb_force* force,
+              int storage, lb_ctx** out) {
+    if (!out) return fail(LB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(LB_EINVAL, "box %d x %d x %d: every edge must be >= 1", nx, ny, nz);
+    if ((long long)nx * ny >= (1LL << 31)) return fail(LB_EINVAL, "nx*ny must be < 2^31");
+    if (!(tau > 0.5) || !isfinite(tau)) return fail(LB_EINVAL, "tau = %g must be > 1/2", tau);
+    if (!(M > 0) || !isfinite(M)) return fail(LB_EINVAL, "M = %g must be > 0", M);
+    if (!(W > 0)) return fail(LB_EINVAL, "W = %g must be > 0 (or +inf)", W);
+    if (!(sigma >= 0) || !isfinite(sigma)) return fail(LB_EINVAL, "sigma = %g must be >= 0", sigma);
+    if (isinf(W) && sigma > 0) return fail(LB_EINVAL, "sigma > 0 needs a finite W");
+    if (storage != LB_F32 && storage != LB_F16_SHIFTED && storage != LB_BF16_SHIFTED)
+        return fail(LB_EINVAL, "unknown storage %d", storage);
+    lb_force fz;
+    memset(&fz, 0, sizeof(fz));
+    if (force) fz = *force;
+    if (fz.kind < LB_FORCE_NONE || fz.kind > LB_FORCE_LINEAR) return fail(LB_EINVAL, "unknown force kind %d", fz.kind);
+    if (fz.kind == LB_FORCE_LINEAR && !(fz.T_relax > 0)) return fail(LB_EINVAL, "linear forcing needs T_relax > 0");
+
+    lb_ctx* c = new lb_ctx();
+    c->nx = nx; c->ny = ny; c->nz = nz;
+    c->N = (long long)nx * ny * nz;
+    c->tau = tau; c->M = M; c->W = W; c->sigma = sigma;
+    c->force = fz;
+    c->storage = storage;
+    c->fsize = storage == LB_F32 ? 4 : 2;
+    cudaGetDevice(&c->device);
+    if (c->N > (1LL << 62) / 27) {
+        delete c;
+        return fail(LB_EINVAL, "box too large");
+    }
+    // default launch shape: z chunk of 32 planes, smaller for thin boxes
+    c->ty = 8;
+    c->zc = nz < 32 ? nz : 32;
+
+    int rc = LB_OK;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (rc != LB_OK) return;
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA, "cudaMalloc(%zu bytes): %s", bytes,
+                      cudaGetErrorString(e));
+        }
+    };
+    alloc(&c->f, (size_t)c->N * 27 * c->fsize);
+    alloc((void**)&c->g[0], (size_t)c->N * 7 * sizeof(float));
+    alloc((void**)&c->g[1], (size_t)c->N * 7 * sizeof(float));
+    c->npart_cap = max_blocks(c);
+    alloc((void**)&c->partials, (size_t)c->npart_cap * NPART * sizeof(double));
+    alloc((void**)&c->st, sizeof(DevState));
+    if (rc == LB_OK && fz.kind == LB_FORCE_ABC) {
+        const int L = 2 * (nx + ny + nz);
+        float* h = (float*)malloc((size_t)L * sizeof(float));
+        int o = 0;
+        const int ns[3] = {nx, ny, nz};
+        for (int ax = 0; ax < 3; ++ax) {
+            for (int k = 0; k < ns[ax]; ++k) h[o + k] = (float)sin(fz.kf * k);
+            for (int k = 0; k < ns[ax]; ++k) h[o + ns[ax] + k] = (float)cos(fz.kf * k);
+            o += 2 * ns[ax];
+        }
+        alloc((void**)&c->abc, (size_t)L * sizeof(float));
+        if (rc == LB_OK) {
+            cudaError_t e = cudaMemcpy(c->abc, h, (size_t)L * sizeof(float), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) rc = fail(LB_ECUDA, "ABC table upload: %s", cudaGetErrorString(e));
+        }
+        free(h);
+    }
+    if (rc == LB_OK) {
+        cudaError_t e = cudaMemset(c->st, 0, sizeof(DevState));
+        if (e != cudaSuccess) rc = fail(LB_ECUDA, "cudaMemset: %s", cudaGetErrorString(e));
+    }
+    if (rc != LB_OK) {
+        lb_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return LB_OK;
+}
+
+int lb_set_stream(lb_ctx* c, void* stream) {
+    if (!c) return fail(LB_EINVAL, "ctx is NULL");
+    c->stream = (cudaStream_t)stream;
+    return LB_OK;
+}
+
+int lb_init(lb_ctx* c, const float* phi, const float* u) {
+    if (!c || !phi || !u) return fail(LB_EINVAL, "lb_init: NULL argument");
+    const long long N = c->N;
+    const float* dphi = phi;
+    const float* du = u;
+    if (!is_device_pointer(phi) || !is_device_pointer(u)) {
+        int rc = ensure_stage(c);
+        if (rc) return rc;
+        if (!is_device_pointer(phi)) {
+            LB_CUDA(cudaMemcpyAsync(c->stage, phi, (size_t)N * sizeof(float), cudaMemcpyDefault, c->stream));
+            dphi = c->stage;
+        }
+        if (!is_device_pointer(u)) {
+            LB_CUDA(cudaMemcpyAsync(c->stage + N, u, (size_t)N * 3 * sizeof(float), cudaMemcpyDefault, c->stream));
+            du = c->stage + N;
+        }
+    }
+    StepArgs a = base_args(c);
+    a.zc = c->nz < 32 ? c->nz : 32;
+    a.g_out = c->g[0];
+    a.in_phi = dphi;
+    a.in_u = du;
+    const dim3 grid = grid_for(c, 8, a.zc);
+    const long long nblk = (long long)grid.x * grid.y * grid.z;
+    LB_CUDA(launch_any(c, MODE_INIT, 0, 8, grid, a, c->stream));
+    finalize_kernel<<<1, 256, 0, c->stream>>>(c->partials, (int)nblk, c->st, fin_args(c, MODE_INIT));
+    LB_CUDA(cudaGetLastError());
+    c->launches += 2;
+    c->t = 0;
+    c->initialized = true;
+    if (dphi != phi || du != u) LB_CUDA(cudaStreamSynchronize(c->stream));  // staging is reused
+    return LB_OK;
+}
+
+int lb_step(lb_ctx* c, int n) {
+    if (!c) return fail(LB_EINVAL, "ctx is NULL");
+    if (n < 0) return fail(LB_EINVAL, "n = %d < 0", n);
+    if (!c->initialized) return fail(LB_ESTATE, "lb_step before lb_init");
+    int rc = check_tile(c->ty, c->zc);
+    if (rc) return rc;
+    while (n > 0) {
+        const int par = (int)(c->t & 1);
+        if (par == 0 && n >= 2 && !c->timing) {
+            if (!c->graph || c->graph_ty != c->ty || c->graph_zc != c->zc) {
+                rc = capture_graph(c);
+                if (rc) return rc;
+            }
+            LB_CUDA(cudaGraphLaunch(c->graph, c->stream));
+            c->launches += 4;
+            c->t += 2;
+            n -= 2;
+        } else {
+            rc = enqueue_step(c, par, c->stream);
+            if (rc) return rc;
+            c->t += 1;
+            n -= 1;
+        }
+    }
+    return LB_OK;
+}
+
+int lb_moments(lb_ctx* c, float* rho, float* u, float* phi) {
+    if (!c) return fail(LB_EINVAL, "ctx is NULL");
+    if (!c->initialized) return fail(LB_ESTATE, "lb_moments before lb_init");
+    const long long N = c->N;
+    const bool hr = rho && !is_device_pointer(rho);
+    const bool hu = u && !is_device_pointer(u);
+    const bool hp = phi && !is_device_pointer(phi);
+    if (hr || hu || hp) {
+        int rc = ensure_stage(c);
+        if (rc) return rc;
+    }
+    StepArgs a = base_args(c);
+    a.zc = c->nz < 32 ? c->nz : 32;
+    const int par = (int)(c->t & 1);
+    a.g_in = c->g[par];
+    a.out_rho = hr ? c->stage : rho;
+    a.out_u = hu ? c->stage + N : u;
+    a.out_phi = hp ? c->stage + 4 * N : phi;
+    LB_CUDA(launch_any(c, MODE_MOMENTS, par, 8, grid_for(c, 8, a.zc), a, c->stream));
+    c->launches += 1;
+    if (hr) LB_CUDA(cudaMemcpyAsync(rho, c->stage, (size_t)N * sizeof(float), cudaMemcpyDefault, c->stream));
+    if (hu) LB_CUDA(cudaMemcpyAsync(u, c->stage + N, (size_t)N * 3 * sizeof(float), cudaMemcpyDefault, c->stream));
+    if (hp) LB_CUDA(cudaMemcpyAsync(phi, c->stage + 4 * N, (size_t)N * sizeof(float), cudaMemcpyDefault, c->stream));
+    if (hr || hu || hp) LB_CUDA(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+int lb_diagnostics(lb_ctx* c, double out[5]) {
+    if (!c || !out) return fail(LB_EINVAL, "lb_diagnostics: NULL argument");
+    if (!c->initialized) return fail(LB_ESTATE, "lb_diagnostics before lb_init");
+    DevState h;
+    LB_CUDA(cudaMemcpyAsync(&h, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 5; ++k) out[k] = h.diag[k];
+    if (h.flags & 1) return fail(LB_ENONFINITE, "a NaN or Inf was met since lb_init");
+    return LB_OK;
+}
+
+int lb_sync(lb_ctx* c) {
+    if (!c) return fail(LB_EINVAL, "ctx is NULL");
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+long long lb_time(const lb_ctx* c) { return c ? c->t : -1; }
+
+long long lb_launch_count(const lb_ctx* c) { return c ? c->launches : -1; }
+
+int lb_set_timing(lb_ctx* c, int on) {
+    if (!c) return fail(LB_EINVAL, "ctx is NULL");
+    c->timing = on != 0;
+    c->ev_used = 0;
+    return LB_OK;
+}
+
+int lb_kernel_time(lb_ctx* c, double* ms, long long* launches) {
+    if (!c || !ms || !launches) return fail(LB_EINVAL, "lb_kernel_time: NULL argument");
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    double total = 0.0;
+    for (size_t k = 0; k < c->ev_used; ++k) {
+        float m = 0.f;
+        LB_CUDA(cudaEventElapsedTime(&m, c->ev_start[k], c->ev_stop[k]));
+        total += m;
+    }
+    *ms = total;
+    *launches = (long long)c->ev_used;
+    return LB_OK;
+}
+
+int lb_set_tile(lb_ctx* c, int ty, int zc) {
+    if (!c) return fail(LB_EINVAL, "ctx is NULL");
+    int rc = check_tile(ty, zc);
+    if (rc) return rc;
+    c->ty = ty;
+    c->zc = zc > c->nz ? c->nz : zc;
+    return LB_OK;
+}
+
+int lb_get_tile(const lb_ctx* c, int* ty, int* zc) {
+    if (!c || !ty || !zc) return fail(LB_EINVAL, "lb_get_tile: NULL argument");
+    *ty = c->ty;
+    *zc = c->zc;
+    return LB_OK;
+}
+
+double lb_bytes_per_site(const lb_ctx* c) {
+    if (!c) return 0.0;
+    return 27.0 * 2.0 * (double)c->fsize + 7.0 * 2.0 * 4.0;
+}
+
+int lb_tune(lb_ctx* c, int steps) {
+    if (!c) return fail(LB_EINVAL, "ctx is NULL");
+    if (steps < 1) return fail(LB_EINVAL, "steps = %d < 1", steps);
+    char dev_name[256] = "";
+    {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, c->device) == cudaSuccess) snprintf(dev_name, sizeof(dev_name), "%s", prop.name);
+    }
+    for (char* p = dev_name; *p; ++p)
+        if (*p == ' ') *p = '_';
+    const char* cache = getenv("LBGB_TUNE_CACHE");
+    char key[512];
+    snprintf(key, sizeof(key), "%s %d %d %d %d", dev_name, c->nx, c->ny, c->nz, c->storage);
+    if (cache) {
+        FILE* fp = fopen(cache, "r");
+        if (fp) {
+            char line[640];
+            while (fgets(line, sizeof(line), fp)) {
+                int ty, zc;
+                size_t kl = strlen(key);
+                if (strncmp(line, key, kl) == 0 && sscanf(line + kl, " %d %d", &ty, &zc) == 2 &&
+                    check_tile(ty, zc) == LB_OK) {
+                    fclose(fp);
+                    return lb_set_tile(c, ty, zc);
+                }
+            }
+            fclose(fp);
+        }
+    }
+    const int nzt = c->nz < 128 ? c->nz : 128;
+    lb_ctx* s = nullptr;
+    int rc = lb_create(c->nx, c->ny, nzt, c->tau, c->M, c->W, c->sigma, &c->force, c->storage, &s);
+    if (rc) return rc;
+    lb_set_stream(s, c->stream);
+    // scratch state: phi = 0, u = 0 (the kernel's cost does not depend on the values)
+    float* z = nullptr;
+    cudaError_t e = cudaMalloc(&z, (size_t)s->N * 4 * sizeof(float));
+    if (e != cudaSuccess) {
+        lb_destroy(s);
+        return fail(LB_ENOMEM, "tune scratch: %s", cudaGetErrorString(e));
+    }
+    cudaMemsetAsync(z, 0, (size_t)s->N * 4 * sizeof(float), c->stream);
+    rc = lb_init(s, z, z + s->N);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int tys[3] = {4, 8, 16};
+    const int zcs[5] = {8, 16, 32, 64, 128};
+    float best = 1e30f;
+    int bty = c->ty, bzc = c->zc;
+    for (int a = 0; a < 3 && rc == LB_OK; ++a)
+        for (int b = 0; b < 5 && rc == LB_OK; ++b) {
+            if (zcs[b] > nzt && b > 0 && zcs[b - 1] >= nzt) continue;
+            rc = lb_set_tile(s, tys[a], zcs[b]);
+            if (rc == LB_OK) rc = lb_step(s, 2);  // warm-up and graph capture
+            cudaEventRecord(e0, c->stream);
+            if (rc == LB_OK) rc = lb_step(s, 2 * steps);
+            cudaEventRecord(e1, c->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rc == LB_OK && ms < best) {
+                best = ms;
+                bty = tys[a];
+                bzc = zcs[b];
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(z);
+    lb_destroy(s);
+    if (rc) return rc;
+    if (cache) {
+        FILE* fp = fopen(cache, "a");
+        if (fp) {
+            fprintf(fp, "%s %d %d\n", key, bty, bzc);
+            fclose(fp);
+        }
+    }
+    return lb_set_tile(c, bty, bzc);
+}
+
+}  // extern "C"

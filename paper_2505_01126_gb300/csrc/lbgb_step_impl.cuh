@@ -1,0 +1,43 @@
+// lbgb_step_impl.cuh -- host launcher of the fused kernel for one storage type.
+// Included once per storage type by lbgb_step_{f32,f16,bf16}.cu so the three
+// sets of kernel instances compile in parallel.
+#pragma once
+#include "lbgb_kernels.cuh"
+
+namespace lbgb {
+
+template <class FT, int TY>
+static cudaError_t launch_ty(int mode, int parity, dim3 grid, const StepArgs& a, cudaStream_t st) {
+    const dim3 block(32 * TY);
+    if (mode == MODE_STEP) {
+        if (parity == 0) fused_step_kernel<FT, TY, MODE_STEP, 0><<<grid, block, 0, st>>>(a);
+        else fused_step_kernel<FT, TY, MODE_STEP, 1><<<grid, block, 0, st>>>(a);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_fused<LBGB_FT>(int mode, int parity, int ty, dim3 grid, const StepArgs& a,
+                                  cudaStream_t st) {
+    if (mode == MODE_MOMENTS) {
+        if (ty != 8) return cudaErrorInvalidValue;
+        if (parity == 0) fused_step_kernel<LBGB_FT, 8, MODE_MOMENTS, 0><<<grid, 256, 0, st>>>(a);
+        else fused_step_kernel<LBGB_FT, 8, MODE_MOMENTS, 1><<<grid, 256, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    if (mode == MODE_INIT) {
+        if (ty != 8) return cudaErrorInvalidValue;
+        fused_step_kernel<LBGB_FT, 8, MODE_INIT, 0><<<grid, 256, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    switch (ty) {
+        case 4: return launch_ty<LBGB_FT, 4>(mode, parity, grid, a, st);
+        case 8: return launch_ty<LBGB_FT, 8>(mode, parity, grid, a, st);
+        case 16: return launch_ty<LBGB_FT, 16>(mode, parity, grid, a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace lbgb

@@ -1,0 +1,234 @@
+"""Thin ctypes binding of the CUDA library (C ABI in include/lbgb.h).
+
+Argument marshalling only: every step of the time step runs in the library's
+kernels.  Fields may be torch CUDA tensors (passed by device pointer), CPU
+torch tensors or numpy arrays (passed by host pointer); scalar fields have
+shape (nz, ny, nx) and vector fields (3, nz, ny, nx), float32, contiguous.
+Importing this module loads csrc/liblbgb.so and raises if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "csrc", "liblbgb.so")
+
+LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENONFINITE, LB_ESTATE = 0, -1, -2, -3, -4, -5
+LB_F32, LB_F16_SHIFTED, LB_BF16_SHIFTED = 0, 1, 2
+LB_FORCE_NONE, LB_FORCE_CONST, LB_FORCE_ABC, LB_FORCE_LINEAR = 0, 1, 2, 3
+
+STORAGE = {"f32": LB_F32, "f16": LB_F16_SHIFTED, "bf16": LB_BF16_SHIFTED}
+
+
+class LBError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class lb_force(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("g", ctypes.c_double * 3), ("A", ctypes.c_double),
+                ("kf", ctypes.c_double), ("K_target", ctypes.c_double), ("T_relax", ctypes.c_double)]
+
+
+EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_step", "lb_moments", "lb_diagnostics",
+           "lb_sync", "lb_time", "lb_set_tile", "lb_get_tile", "lb_tune", "lb_bytes_per_site",
+           "lb_destroy", "lb_last_error", "lb_launch_count", "lb_set_timing", "lb_kernel_time"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_2505_01126_gb300.build.build() first")
+    try:  # make the CUDA runtime that torch loaded visible first (same soname)
+        import torch  # noqa: F401
+    except Exception:
+        pass
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.lb_create.argtypes = [i, i, i, d, d, d, d, ctypes.POINTER(lb_force), i, ctypes.POINTER(vp)]
+    lib.lb_set_stream.argtypes = [vp, vp]
+    lib.lb_init.argtypes = [vp, vp, vp]
+    lib.lb_step.argtypes = [vp, i]
+    lib.lb_moments.argtypes = [vp, vp, vp, vp]
+    lib.lb_diagnostics.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    lib.lb_sync.argtypes = [vp]
+    lib.lb_time.argtypes = [vp]
+    lib.lb_time.restype = ctypes.c_longlong
+    lib.lb_set_tile.argtypes = [vp, i, i]
+    lib.lb_get_tile.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.lb_tune.argtypes = [vp, i]
+    lib.lb_bytes_per_site.argtypes = [vp]
+    lib.lb_bytes_per_site.restype = d
+    lib.lb_destroy.argtypes = [vp]
+    lib.lb_destroy.restype = None
+    lib.lb_last_error.restype = ctypes.c_char_p
+    lib.lb_launch_count.argtypes = [vp]
+    lib.lb_launch_count.restype = ctypes.c_longlong
+    lib.lb_set_timing.argtypes = [vp, i]
+    lib.lb_kernel_time.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(rc: int):
+    if rc != LB_OK:
+        raise LBError(rc, _lib.lb_last_error().decode())
+
+
+def _ptr(a, n_expected: int, writable: bool = False):
+    """Pointer of a contiguous float32 torch tensor (CUDA or CPU) or numpy array."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags.c_contiguous:
+            if writable:
+                raise ValueError("output arrays must be contiguous float32")
+            a = np.ascontiguousarray(a, dtype=np.float32)
+        if a.size != n_expected:
+            raise ValueError(f"expected {n_expected} floats, got {a.size}")
+        return ctypes.c_void_p(a.ctypes.data), a
+    import torch
+
+    if not isinstance(a, torch.Tensor):
+        raise TypeError("fields must be torch tensors or numpy arrays")
+    if a.dtype != torch.float32 or not a.is_contiguous():
+        if writable:
+            raise ValueError("output tensors must be contiguous float32")
+        a = a.contiguous().float()
+    if a.numel() != n_expected:
+        raise ValueError(f"expected {n_expected} floats, got {a.numel()}")
+    return ctypes.c_void_p(a.data_ptr()), a
+
+
+@dataclass
+class Force:
+    kind: int = LB_FORCE_NONE
+    g: tuple = (0.0, 0.0, 0.0)
+    A: float = 0.0
+    kf: float = 0.0
+    K_target: float = 0.0
+    T_relax: float = 100.0
+
+    def to_c(self) -> lb_force:
+        f = lb_force()
+        f.kind = int(self.kind)
+        for k in range(3):
+            f.g[k] = float(self.g[k])
+        f.A, f.kf = float(self.A), float(self.kf)
+        f.K_target, f.T_relax = float(self.K_target), float(self.T_relax)
+        return f
+
+
+class Box:
+    """One periodic box: lb_create / lb_init / lb_step / lb_moments / lb_diagnostics."""
+
+    def __init__(self, nx, ny, nz, tau, M, W, sigma, force: Force | None = None, storage="f32",
+                 stream=None):
+        self._h = None
+        self.shape = (int(nz), int(ny), int(nx))
+        self.N = int(nx) * int(ny) * int(nz)
+        st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        h = ctypes.c_void_p()
+        fc = (force or Force()).to_c()
+        _check(_lib.lb_create(int(nx), int(ny), int(nz), float(tau), float(M), float(W), float(sigma),
+                              ctypes.byref(fc), st, ctypes.byref(h)))
+        self._h = h
+        if stream is not None:
+            self.set_stream(stream)
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an integer cudaStream_t or None."""
+        handle = getattr(stream, "cuda_stream", stream)
+        _check(_lib.lb_set_stream(self._h, ctypes.c_void_p(int(handle) if handle else 0)))
+
+    def init(self, phi, u):
+        p, _k1 = _ptr(phi, self.N)
+        q, _k2 = _ptr(u, 3 * self.N)
+        _check(_lib.lb_init(self._h, p, q))
+
+    def step(self, n: int = 1):
+        _check(_lib.lb_step(self._h, int(n)))
+
+    def moments(self, rho=None, u=None, phi=None):
+        """Fill caller buffers (any may be None) with p*, u (forced velocity) and phi."""
+        r, _a = _ptr(rho, self.N, True)
+        v, _b = _ptr(u, 3 * self.N, True)
+        p, _c = _ptr(phi, self.N, True)
+        _check(_lib.lb_moments(self._h, r, v, p))
+
+    def moments_numpy(self):
+        rho = np.zeros(self.shape, np.float32)
+        u = np.zeros((3,) + self.shape, np.float32)
+        phi = np.zeros(self.shape, np.float32)
+        self.moments(rho, u, phi)
+        return rho, u, phi
+
+    def diagnostics(self, allow_nonfinite: bool = False) -> np.ndarray:
+        out = (ctypes.c_double * 5)()
+        rc = _lib.lb_diagnostics(self._h, out)
+        if rc != LB_OK and not (allow_nonfinite and rc == LB_ENONFINITE):
+            _check(rc)
+        return np.array(list(out))
+
+    def sync(self):
+        _check(_lib.lb_sync(self._h))
+
+    @property
+    def time(self) -> int:
+        return int(_lib.lb_time(self._h))
+
+    def set_tile(self, ty: int, zc: int):
+        _check(_lib.lb_set_tile(self._h, int(ty), int(zc)))
+
+    def tile(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.lb_get_tile(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def tune(self, steps: int = 3):
+        _check(_lib.lb_tune(self._h, int(steps)))
+        return self.tile()
+
+    @property
+    def bytes_per_site(self) -> float:
+        return float(_lib.lb_bytes_per_site(self._h))
+
+    @property
+    def launches(self) -> int:
+        return int(_lib.lb_launch_count(self._h))
+
+    def set_timing(self, on: bool = True):
+        _check(_lib.lb_set_timing(self._h, 1 if on else 0))
+
+    def kernel_time(self):
+        """(summed fused-kernel milliseconds, timed launches) since timing was switched on."""
+        ms, n = ctypes.c_double(), ctypes.c_longlong()
+        _check(_lib.lb_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.lb_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

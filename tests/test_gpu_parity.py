@@ -1,0 +1,290 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Both sides take the same FP32-rounded inputs from the seeded generators.  The
+bar for FP32 storage is max|delta| <= 1e-5 in p* (rho), u and phi after 50
+steps; 16-bit storage states its error instead (see test_gpu_precision.py).
+Sizes span several tiles in x (32 sites) and y (8 sites) with ragged tails,
+z-chunking, and degenerate edges (boxes of 1 or 2 sites along an axis).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2505_01126_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lbgb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_01126_gb300 import build
+
+    build.build()
+    from paper_2505_01126_gb300 import lbgb as mod
+
+    return mod
+
+
+def smooth_fields(shape, seed, bubbles=0, R=3.0, W=3.0):
+    """Random smooth phase field in [0, 1] and velocity of amplitude 0.02."""
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    s = np.zeros(shape)
+    for _ in range(3):
+        k = rng.integers(1, 3, size=3)
+        ph = rng.uniform(0, 2 * np.pi, size=3)
+        s += np.sin(2 * np.pi * k[0] * x / nx + ph[0]) * np.cos(2 * np.pi * k[1] * y / ny + ph[1]) \
+            * np.cos(2 * np.pi * k[2] * z / nz + ph[2])
+    phi = 0.5 + 0.5 * np.tanh(1.5 * s)
+    u = np.zeros((3,) + shape)
+    for a in range(3):
+        k = rng.integers(1, 3, size=3)
+        u[a] = 0.02 * np.sin(2 * np.pi * (k[0] * x / nx + k[1] * y / ny + k[2] * z / nz) + rng.uniform(0, 6))
+    return inputs.to_f32(phi), inputs.to_f32(u)
+
+
+def run_pair(lbgb, orc, shape, tau, M, W, sigma, phi, u, steps, force=None, storage="f32", tile=None,
+             orc_force=None):
+    nz, ny, nx = shape
+    force = force or {}
+    o = orc.Oracle(nx, ny, nz, tau, M, W, sigma, **force)
+    o.init(phi.astype(np.float64), u.astype(np.float64))
+    o.step(steps)
+    fk = lbgb.Force(kind=force.get("force_kind", 0), g=force.get("g", (0, 0, 0)), A=force.get("A_abc", 0.0),
+                    kf=force.get("kf", 0.0), K_target=force.get("K_target", 0.0),
+                    T_relax=force.get("T_relax", 100.0))
+    b = lbgb.Box(nx, ny, nz, tau, M, W, sigma, force=fk, storage=storage)
+    if tile is not None:
+        b.set_tile(*tile)
+    b.init(phi, u)
+    b.step(steps)
+    got = b.moments_numpy()
+    want = o.moments()
+    return b, o, got, want
+
+
+def max_err(got, want):
+    return [float(np.abs(g.astype(np.float64) - w).max()) for g, w in zip(got, want)]
+
+
+def check_diagnostics(dg, do, N, delta=TOL):
+    """GPU FP64 reductions against the oracle's, with bounds that follow from
+    fields agreeing to `delta` per component: Phi within N delta; K within
+    sqrt(2 K 3N) delta + 1.5 N delta^2 (Cauchy-Schwarz on sum u.du); max|u| within
+    sqrt(3) delta; eps (a sum of squared Hermite coefficients) within 2%."""
+    assert abs(dg[0] - do[0]) <= N * delta
+    assert abs(dg[1] - do[1]) <= math.sqrt(2 * do[1] * 3 * N) * delta + 1.5 * N * delta ** 2
+    assert abs(dg[3] - do[3]) <= math.sqrt(3) * delta
+    assert abs(dg[2] - do[2]) <= 0.02 * abs(do[2]) + 1e-12
+
+
+def test_static_droplet_32_50_steps(lbgb, orc):
+    """32^3 droplet R = 8, W = 3, sigma = 0.01, tau = 1, M = 0.1: 50 steps."""
+    w = inputs.static_droplet()
+    b, o, got, want = run_pair(lbgb, orc, (32, 32, 32), w.tau, w.M, w.W, w.sigma, w.phi, w.u, 50)
+    e = max_err(got, want)
+    assert max(e) <= TOL, e
+    check_diagnostics(b.diagnostics(), o.diagnostics(), 32 ** 3)
+
+
+def test_init_state_moments(lbgb, orc):
+    """t = 0: p* = 1, u = physical velocity + F^s/2, phi as given (rounded identically)."""
+    phi, u = smooth_fields((9, 17, 40), 1)
+    b, o, got, want = run_pair(lbgb, orc, (9, 17, 40), 0.8, 0.1, 3.0, 0.01, phi, u, 0)
+    assert max(max_err(got, want)) <= 1e-6
+
+
+@pytest.mark.parametrize("shape", [(11, 13, 37), (5, 9, 70), (40, 3, 33), (2, 2, 2), (1, 1, 1),
+                                   (3, 1, 5), (1, 6, 1)])
+def test_ragged_and_degenerate_boxes(lbgb, orc, shape):
+    """Ragged tiles in x and y, a z extent that is not a multiple of the z chunk,
+    and boxes with edges of 1 or 2 sites (the periodic stencils wrap onto
+    themselves)."""
+    phi, u = smooth_fields(shape, sum(shape))
+    b, o, got, want = run_pair(lbgb, orc, shape, 0.7, 0.1, 3.0, 0.02, phi, u, 50)
+    e = max_err(got, want)
+    assert max(e) <= TOL, e
+
+
+@pytest.mark.parametrize("kind", ["const", "abc", "linear"])
+def test_forcing_kinds(lbgb, orc, kind):
+    shape = (12, 20, 36)
+    phi, u = smooth_fields(shape, 3)
+    force = {"const": dict(force_kind=1, g=(1e-5, -2e-5, 5e-6)),
+             "abc": dict(force_kind=2, A_abc=2e-5, kf=2 * math.pi / 12),
+             "linear": dict(force_kind=3, T_relax=20.0)}[kind]
+    b, o, got, want = run_pair(lbgb, orc, shape, 0.6, 0.1, 3.0, 0.01, phi, u, 50, force=force)
+    e = max_err(got, want)
+    assert max(e) <= TOL, e
+    dg, do = b.diagnostics(), o.diagnostics()
+    check_diagnostics(dg, do, int(np.prod(shape)))
+    if kind == "linear":
+        assert abs(dg[4] - do[4]) <= 1e-5 * abs(do[4]) + 1e-9
+
+
+def test_hit_64_two_bubbles(lbgb, orc):
+    """64^3 forced HIT surrogate: solenoidal u (|k| in [1,4], u_rms 0.02), two bubbles
+    R = 10, tau = 0.51, linear forcing; 50 steps."""
+    w = inputs.bubbly_hit(64, 2, 10.0, seed=2)
+    force = dict(force_kind=3, T_relax=w.T_relax)
+    b, o, got, want = run_pair(lbgb, orc, (64, 64, 64), w.tau, w.M, w.W, w.sigma, w.phi, w.u, 50, force=force)
+    e = max_err(got, want)
+    assert max(e) <= TOL, e
+
+
+@pytest.mark.parametrize("tile", [(4, 8), (8, 16), (16, 64), (8, 5), (4, 1)])
+def test_tile_shapes_give_identical_fields(lbgb, tile):
+    """Every launch shape computes each site with the same arithmetic, so the
+    fields are bitwise identical across tile shapes (no forcing controller)."""
+    shape = (21, 19, 45)
+    phi, u = smooth_fields(shape, 4)
+    nz, ny, nx = shape
+    ref = lbgb.Box(nx, ny, nz, 0.8, 0.1, 3.0, 0.01)
+    ref.init(phi, u)
+    ref.step(7)
+    r0 = ref.moments_numpy()
+    b = lbgb.Box(nx, ny, nz, 0.8, 0.1, 3.0, 0.01)
+    b.set_tile(*tile)
+    b.init(phi, u)
+    b.step(7)
+    r1 = b.moments_numpy()
+    for x, y in zip(r0, r1):
+        assert np.array_equal(x, y)
+
+
+def test_graph_replay_equals_single_steps(lbgb):
+    shape = (16, 16, 40)
+    phi, u = smooth_fields(shape, 5)
+    nz, ny, nx = shape
+    a = lbgb.Box(nx, ny, nz, 0.8, 0.1, 3.0, 0.01, force=lbgb.Force(kind=3, T_relax=30.0))
+    a.init(phi, u)
+    a.step(9)  # graph for pairs + one single step
+    b = lbgb.Box(nx, ny, nz, 0.8, 0.1, 3.0, 0.01, force=lbgb.Force(kind=3, T_relax=30.0))
+    b.init(phi, u)
+    for _ in range(9):
+        b.step(1)
+    assert a.time == b.time == 9
+    for x, y in zip(a.moments_numpy(), b.moments_numpy()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.diagnostics(), b.diagnostics())
+
+
+def test_device_and_host_pointers_agree(lbgb):
+    import torch
+
+    shape = (8, 12, 34)
+    phi, u = smooth_fields(shape, 6)
+    nz, ny, nx = shape
+    a = lbgb.Box(nx, ny, nz, 0.8, 0.1, 3.0, 0.01)
+    a.init(torch.from_numpy(phi).cuda(), torch.from_numpy(u).cuda())
+    a.step(5)
+    rho = torch.zeros(shape, device="cuda")
+    uu = torch.zeros((3,) + shape, device="cuda")
+    ph = torch.zeros(shape, device="cuda")
+    a.moments(rho, uu, ph)
+    torch.cuda.synchronize()
+    b = lbgb.Box(nx, ny, nz, 0.8, 0.1, 3.0, 0.01)
+    b.init(phi, u)
+    b.step(5)
+    r = b.moments_numpy()
+    assert np.array_equal(rho.cpu().numpy(), r[0])
+    assert np.array_equal(uu.cpu().numpy(), r[1])
+    assert np.array_equal(ph.cpu().numpy(), r[2])
+
+
+def test_torch_stream_is_used(lbgb):
+    import torch
+
+    shape = (8, 8, 32)
+    phi, u = smooth_fields(shape, 7)
+    nz, ny, nx = shape
+    s = torch.cuda.Stream()
+    b = lbgb.Box(nx, ny, nz, 0.8, 0.1, 3.0, 0.01, stream=s)
+    b.init(phi, u)
+    b.step(4)
+    rho = torch.zeros(shape, device="cuda")
+    b.moments(rho=rho)
+    s.synchronize()
+    assert abs(float(rho.sum()) - nx * ny * nz) < 1e-2
+
+
+def test_mass_and_phase_conservation_fp32(lbgb):
+    """sum p* and sum phi stay at their initial values up to FP32 rounding."""
+    w = inputs.bubbly_hit(48, 3, 8.0, seed=9)
+    b = lbgb.Box(48, 48, 48, w.tau, w.M, w.W, w.sigma, force=lbgb.Force(kind=3, T_relax=100.0))
+    b.init(w.phi, w.u)
+    d0 = b.diagnostics()
+    b.step(200)
+    d1 = b.diagnostics()
+    rho, u, phi = b.moments_numpy()
+    N = 48 ** 3
+    assert abs(rho.astype(np.float64).sum() / N - 1) < 1e-5
+    assert abs(d1[0] / d0[0] - 1) < 1e-5
+    assert abs(phi.astype(np.float64).sum() / d0[0] - 1) < 1e-5
+
+
+def test_rest_state_fp32(lbgb):
+    n = 16
+    b = lbgb.Box(n, n, n, 0.8, 0.1, 3.0, 0.01)
+    b.init(np.full((n, n, n), 0.3, np.float32), np.zeros((3, n, n, n), np.float32))
+    b.step(100)
+    rho, u, phi = b.moments_numpy()
+    assert np.abs(rho - 1).max() < 1e-6
+    assert np.abs(u).max() < 1e-7
+    assert np.abs(phi - 0.3).max() < 1e-6
+
+
+def test_state_errors(lbgb):
+    b = lbgb.Box(8, 8, 8, 0.8, 0.1, 3.0, 0.01)
+    with pytest.raises(lbgb.LBError) as e:
+        b.step(1)
+    assert e.value.code == lbgb.LB_ESTATE
+    with pytest.raises(lbgb.LBError) as e:
+        b.set_tile(5, 8)
+    assert e.value.code == lbgb.LB_EINVAL
+
+
+def test_nonfinite_input_is_reported(lbgb):
+    """A NaN planted in the host input is reported by lb_diagnostics (no fault)."""
+    n = 8
+    phi = np.full((n, n, n), 0.5, np.float32)
+    phi[3, 4, 5] = np.nan
+    b = lbgb.Box(n, n, n, 0.8, 0.1, 3.0, 0.01)
+    b.init(phi, np.zeros((3, n, n, n), np.float32))
+    b.step(2)
+    with pytest.raises(lbgb.LBError) as e:
+        b.diagnostics()
+    assert e.value.code == lbgb.LB_ENONFINITE
+    d = b.diagnostics(allow_nonfinite=True)
+    assert d.shape == (5,)
+
+
+def test_full_size_256_one_step_each_parity(lbgb, orc):
+    """The benchmark workload (256^3 forced HIT, 64 bubbles R = 10, tau = 0.51) in the
+    benchmark's launch shape: 2 steps (one of each AA parity), every site
+    compared with the oracle."""
+    w = inputs.bubbly_hit(256, 64, 10.0, seed=2)
+    n = 256
+    b = lbgb.Box(n, n, n, w.tau, w.M, w.W, w.sigma, force=lbgb.Force(kind=3, T_relax=w.T_relax))
+    b.init(w.phi, w.u)
+    b.step(2)
+    got = b.moments_numpy()
+    dg = b.diagnostics()
+    b.close()
+    o = orc.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma, force_kind=3, T_relax=w.T_relax)
+    o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
+    o.step(2)
+    want = o.moments()
+    do = o.diagnostics()
+    o.close()
+    e = max_err(got, want)
+    assert max(e) <= TOL, e
+    check_diagnostics(dg, do, n ** 3)
