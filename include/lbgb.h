@@ -15,8 +15,9 @@
  *  10. f*_i = w_i [p* + c_i.u/cs^2 + H_i:(u u + (1-omega) a2)/(2 cs^4)] + S_i/2
  *      (Eq. 7 with the Hermite-regularized non-equilibrium; S_i is Eq. 6)
  *  11. g*_q = g_q + omega_phi (g^eq_q - g_q),
- *      g^eq_q = w_q phi (1 + c_q.u/cs7^2) + w_q (M/cs7^2)(4/W) phi (1-phi) c_q.n
- *      (D3Q7 BGK whose Chapman-Enskog limit is the Allen-Cahn Eq. 4, D = M)
+ *      g^eq_q = w_q phi (1 + c_q.u/cs7^2) + w_q (M/cs7^2)(4/W) max(phi (1-phi), 0) c_q.n
+ *      (D3Q7 BGK whose Chapman-Enskog limit is the Allen-Cahn Eq. 4, D = M;
+ *      the interface indicator phi (1-phi) is taken as 0 where phi overshoots [0, 1])
  *  12. streaming f_i(x + c_i) <- f*_i, g_q(x + c_q) <- g*_q, periodic
  *  13. FP64 reductions Phi = sum phi, K = 1/2 sum |u|^2,
  *      eps = 2 nu sum S:S with S = -a2/(2 cs^2 tau), max|u|, and the next
@@ -27,7 +28,7 @@
  * Conventions for every call:
  *  - Fields are FP32 structure-of-arrays over the site index
  *    s = x + nx*(y + ny*z) (x fastest); a vector field is three consecutive
- *    planes (ux | uy | uz), 3*N floats.
+ *    planes (ux | uy | uz), 3*N floats.  N = nx*ny*nz < 2^31 - 1.
  *  - Field pointers may be host or device memory (the library asks the CUDA
  *    runtime which); they are borrowed for the duration of the call only and
  *    never freed by the library.  Device pointers must belong to the current
@@ -54,9 +55,11 @@ extern "C" {
 #define LB_ESTATE (-5)     /* call out of order (e.g. lb_step before lb_init) */
 
 /* ---------------------------------------------------- population storage */
-#define LB_F32 0          /* f and g stored as FP32 */
-#define LB_F16_SHIFTED 1  /* f stored as FP16 (f_i - w_i)/w_i, g FP32; FP32 math */
-#define LB_BF16_SHIFTED 2 /* f stored as BF16 (f_i - w_i)/w_i, g FP32; FP32 math */
+/* Every storage holds the shifted population delta_i = (f_i - w_i)/w_i; the
+ * arithmetic is FP32 and the D3Q7 populations g are FP32 in all three. */
+#define LB_F32 0          /* delta_i stored as FP32 */
+#define LB_F16_SHIFTED 1  /* delta_i stored as FP16 */
+#define LB_BF16_SHIFTED 2 /* delta_i stored as BF16 */
 
 /* ------------------------------------------------------------ forcing */
 #define LB_FORCE_NONE 0
@@ -86,7 +89,7 @@ typedef struct lb_ctx lb_ctx;
  *   storage  LB_F32, LB_F16_SHIFTED or LB_BF16_SHIFTED
  * The context owns the populations (f: 27 planes, in place with the AA access
  * pattern; g: two buffers of 7 planes), the reduction scratch and the device
- * state.  Sizes: 1 <= nx, ny, nz and nx*ny*nz*27 < 2^63.
+ * state.  Sizes: 1 <= nx, ny, nz and nx*ny*nz < 2^31 - 1 (1024^3 fits).
  * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA; *out is set to NULL on error.
  */
 int lb_create(int nx, int ny, int nz, double tau, double M, double W, double sigma,
@@ -130,7 +133,7 @@ int lb_sync(lb_ctx* ctx);
 long long lb_time(const lb_ctx* ctx);
 
 /* Launch shape of the fused step kernel: tile height ty (x tile is 32 sites)
- * in {4, 8, 16} and z-chunk zc >= 1 planes per block.  Takes effect at the
+ * in {4, 8} and z-chunk zc >= 1 planes per block.  Takes effect at the
  * next lb_step; lb_tune picks it by measurement. */
 int lb_set_tile(lb_ctx* ctx, int ty, int zc);
 int lb_get_tile(const lb_ctx* ctx, int* ty, int* zc);

@@ -31,6 +31,8 @@
  *     Euclidean distance d; it is the 1D steady state of Eq. 4 with kappa=4D/W;
  *   - the surface-tension prefactor 3W/2 makes the Laplace jump 2 sigma/R;
  *   - n uses the guard max(|grad phi|, 1e-10);
+ *   - the sharpening flux uses max(phi (1-phi), 0) (no flux where phi
+ *     overshoots [0, 1]);
  *   - the regularized non-equilibrium is w_i H_i:a2/(2 cs^4) (the printed form
  *     omits w_i and the trace part of H_i);
  *   - u = sum_i f_i c_i + F/2 (the printed sum of S_i vanishes identically);
@@ -233,17 +235,23 @@ void orc_regularized_neq(const double a2[6], double fneq[27]) {
 }
 
 /* D3Q7 phase-field equilibrium: the zeroth moment is phi, the first moment is
- * phi u + (4M/W) phi (1-phi) n, so the Chapman-Enskog limit is Eq. 4 with
- * D = M = cs7^2 (tau_phi - 1/2).  sharp = (M/cs7^2)(4/W). */
+ * phi u + (4M/W) max(phi (1-phi), 0) n, so the Chapman-Enskog limit is Eq. 4
+ * with D = M = cs7^2 (tau_phi - 1/2).  sharp = (M/cs7^2)(4/W).
+ * phi (1-phi) is Eq. 4's interface indicator, zero in both bulk phases; where
+ * numerical overshoot puts phi outside [0, 1] it is taken as 0 (bulk), since
+ * the unclamped flux there reverses into -c grad phi/|grad phi|, a normalised
+ * diffusion that is ill-conditioned where |grad phi| is small. */
 void orc_phase_equilibrium(double phi, const double u[3], const double n[3], double sharp,
                            double geq[7]) {
+    double ind = phi * (1 - phi);
+    if (ind < 0) ind = 0;
     for (int i = 0; i < 7; ++i) {
         double cu = 0, cn = 0;
         for (int a = 0; a < 3; ++a) {
             cu += C7[i][a] * u[a];
             cn += C7[i][a] * n[a];
         }
-        geq[i] = W7[i] * phi * (1 + cu / CS2_7) + W7[i] * sharp * phi * (1 - phi) * cn;
+        geq[i] = W7[i] * phi * (1 + cu / CS2_7) + W7[i] * sharp * ind * cn;
     }
 }
 

@@ -146,6 +146,19 @@ def test_phase_equilibrium_moments(orc):
         np.testing.assert_allclose(geq @ c, phi * u + 4 * M / W * phi * (1 - phi) * n, atol=1e-15)
 
 
+def test_phase_equilibrium_has_no_sharpening_outside_the_interface(orc):
+    """Outside [0, 1] (numerical overshoot) the interface indicator phi (1 - phi) is
+    taken as 0: the first moment is the advective flux phi u alone."""
+    c, _ = orc.lattice7()
+    c = c.astype(float)
+    u = np.array([0.01, -0.02, 0.005])
+    n = np.array([0.6, 0.0, 0.8])
+    for phi in (1.004, -0.002):
+        geq = orc.phase_equilibrium(phi, u, n, 0.5)
+        assert abs(geq.sum() - phi) < 1e-15
+        np.testing.assert_allclose(geq @ c, phi * u, atol=1e-16)
+
+
 # ---------------------------------------- the step against a textbook scheme
 def _lattice_textbook():
     """An independent enumeration of D3Q27 (itertools order) with product weights."""
