@@ -172,6 +172,7 @@ def main():
     ap.add_argument("--edge", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--tile", type=int, nargs=2, metavar=("TY", "ZC"), help="fixed launch shape (skips tuning)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -209,7 +210,9 @@ def main():
     force = lbgb.Force(kind=lbgb.LB_FORCE_LINEAR, T_relax=w.T_relax)
     stream = torch.cuda.Stream()
     box = lbgb.Box(n, n, n, w.tau, w.M, w.W, w.sigma, force=force, storage=args.storage, stream=stream)
-    if not args.no_tune:
+    if args.tile:
+        box.set_tile(*args.tile)
+    elif not args.no_tune:
         os.environ.setdefault("LBGB_TUNE_CACHE", os.path.join(ROOT, "paper_2505_01126_gb300", "tune_cache.txt"))
         box.tune(3)
     ty, zc = box.tile()

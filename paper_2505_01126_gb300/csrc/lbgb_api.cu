@@ -61,26 +61,30 @@ __global__ void __launch_bounds__(256) finalize_kernel(const double* __restrict_
         v0 += p[0];
         v1 += p[1];
         v2 += p[2];
-        v3 = fmax(v3, p[3]);
+        v3 += p[3];
         v4 = fmax(v4, p[4]);
     }
     block_reduce5<256>(v0, v1, v2, v3, v4);
     if (threadIdx.x == 0) {
-        const double Phi = v0, K = v1;
+        const double Phi = v0, K = v1, umax = sqrt(v4);
+        // a NaN or Inf anywhere reaches the sums (max ignores NaN, the sums do not)
+        const bool bad = !isfinite(v0 + v1 + v2 + v3);
         if (fa.mode == MODE_INIT) {
             st->K_target = fa.K_target_param > 0 ? fa.K_target_param : K;
             st->A = 0.0;
-            st->diag[0] = Phi; st->diag[1] = K; st->diag[2] = 0.0; st->diag[3] = v3; st->diag[4] = 0.0;
-            st->flags = v4 > 0 ? 1 : 0;
+            st->diag[0] = Phi; st->diag[1] = K; st->diag[2] = 0.0; st->diag[3] = umax; st->diag[4] = 0.0;
+            st->mass = 0.0;
+            st->flags = bad ? 1 : 0;
         } else {
             // eps = 2 nu sum S:S, S = -a2/(2 cs^2 tau) = -(3/(2 tau)) a2
             const double s = 1.5 / fa.tau;
             const double eps = 2.0 * fa.nu * s * s * v2;
             double An = 0.0;
             if (fa.force_kind == FK_LINEAR && K > 0) An = (eps + (st->K_target - K) / fa.T_relax) / (2.0 * K);
-            st->diag[0] = Phi; st->diag[1] = K; st->diag[2] = eps; st->diag[3] = v3; st->diag[4] = An;
+            st->diag[0] = Phi; st->diag[1] = K; st->diag[2] = eps; st->diag[3] = umax; st->diag[4] = An;
+            st->mass = v3;
             st->A = An;
-            if (v4 > 0) st->flags |= 1;
+            if (bad) st->flags |= 1;
         }
     }
 }
@@ -138,8 +142,8 @@ StepArgs base_args(const lb_ctx* c) {
     StepArgs a;
     memset(&a, 0, sizeof(a));
     a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.zc = c->zc;
-    a.N = c->N;
-    a.f = c->f;
+    a.N = (int)c->N;
+    for (int i = 0; i < 27; ++i) a.fk[i] = (char*)c->f + (size_t)i * (size_t)c->N * c->fsize;
     a.force_kind = c->force.kind;
     a.omega = (float)(1.0 / c->tau);
     a.omega_phi = (float)(1.0 / (c->M / 0.25 + 0.5));
@@ -151,6 +155,14 @@ StepArgs base_args(const lb_ctx* c) {
     a.st = c->st;
     a.partials = c->partials;
     return a;
+}
+
+// D3Q7 plane pointers: read buffer `par`, write buffer par ^ 1.
+void set_g(StepArgs& a, const lb_ctx* c, int par) {
+    for (int q = 0; q < 7; ++q) {
+        a.gin[q] = c->g[par] + (size_t)q * (size_t)c->N;
+        a.gout[q] = c->g[par ^ 1] + (size_t)q * (size_t)c->N;
+    }
 }
 
 cudaError_t launch_any(const lb_ctx* c, int mode, int parity, int ty, dim3 grid, const StepArgs& a,
@@ -178,8 +190,7 @@ FinalizeArgs fin_args(const lb_ctx* c, int mode) {
 int enqueue_step(lb_ctx* c, int par, cudaStream_t s) {
     StepArgs a = base_args(c);
     a.zc = c->zc;
-    a.g_in = c->g[par];
-    a.g_out = c->g[par ^ 1];
+    set_g(a, c, par);
     const dim3 grid = grid_for(c, c->ty, c->zc);
     const long long nblk = (long long)grid.x * grid.y * grid.z;
     if (nblk > c->npart_cap) return fail(LB_EINVAL, "tile (%d,%d) needs %lld partials > %lld", c->ty, c->zc, nblk, c->npart_cap);
@@ -248,7 +259,7 @@ int ensure_stage(lb_ctx* c) {
 }
 
 int check_tile(int ty, int zc) {
-    if (ty != 4 && ty != 8 && ty != 16) return fail(LB_EINVAL, "tile height %d not in {4, 8, 16}", ty);
+    if (ty != 4 && ty != 8) return fail(LB_EINVAL, "tile height %d not in {4, 8}", ty);
     if (zc < 1) return fail(LB_EINVAL, "z chunk %d < 1", zc);
     return LB_OK;
 }
@@ -288,7 +299,8 @@ int lb_create(int nx, int ny, int nz, double tau, double M, double W, double sig
     if (!out) return fail(LB_EINVAL, "out is NULL");
     *out = nullptr;
     if (nx < 1 || ny < 1 || nz < 1) return fail(LB_EINVAL, "box %d x %d x %d: every edge must be >= 1", nx, ny, nz);
-    if ((long long)nx * ny >= (1LL << 31)) return fail(LB_EINVAL, "nx*ny must be < 2^31");
+    if ((long long)nx * ny * nz >= (1LL << 31) - 1)
+        return fail(LB_EINVAL, "nx*ny*nz must be < 2^31 - 1 (32-bit site indices)");
     if (!(tau > 0.5) || !isfinite(tau)) return fail(LB_EINVAL, "tau = %g must be > 1/2", tau);
     if (!(M > 0) || !isfinite(M)) return fail(LB_EINVAL, "M = %g must be > 0", M);
     if (!(W > 0)) return fail(LB_EINVAL, "W = %g must be > 0 (or +inf)", W);
@@ -310,10 +322,6 @@ int lb_create(int nx, int ny, int nz, double tau, double M, double W, double sig
     c->storage = storage;
     c->fsize = storage == LB_F32 ? 4 : 2;
     cudaGetDevice(&c->device);
-    if (c->N > (1LL << 62) / 27) {
-        delete c;
-        return fail(LB_EINVAL, "box too large");
-    }
     // default launch shape: z chunk of 32 planes, smaller for thin boxes
     c->ty = 8;
     c->zc = nz < 32 ? nz : 32;
@@ -388,7 +396,7 @@ int lb_init(lb_ctx* c, const float* phi, const float* u) {
     }
     StepArgs a = base_args(c);
     a.zc = c->nz < 32 ? c->nz : 32;
-    a.g_out = c->g[0];
+    set_g(a, c, 1);  // writes buffer 0
     a.in_phi = dphi;
     a.in_u = du;
     const dim3 grid = grid_for(c, 8, a.zc);
@@ -444,7 +452,7 @@ int lb_moments(lb_ctx* c, float* rho, float* u, float* phi) {
     StepArgs a = base_args(c);
     a.zc = c->nz < 32 ? c->nz : 32;
     const int par = (int)(c->t & 1);
-    a.g_in = c->g[par];
+    set_g(a, c, par);
     a.out_rho = hr ? c->stage : rho;
     a.out_u = hu ? c->stage + N : u;
     a.out_phi = hp ? c->stage + 4 * N : phi;
@@ -566,22 +574,25 @@ int lb_tune(lb_ctx* c, int steps) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int tys[3] = {4, 8, 16};
+    const int tys[2] = {4, 8};
     const int zcs[5] = {8, 16, 32, 64, 128};
     float best = 1e30f;
     int bty = c->ty, bzc = c->zc;
-    for (int a = 0; a < 3 && rc == LB_OK; ++a)
+    for (int a = 0; a < 2 && rc == LB_OK; ++a)
         for (int b = 0; b < 5 && rc == LB_OK; ++b) {
-            if (zcs[b] > nzt && b > 0 && zcs[b - 1] >= nzt) continue;
-            rc = lb_set_tile(s, tys[a], zcs[b]);
-            if (rc == LB_OK) rc = lb_step(s, 2);  // warm-up and graph capture
+            if (b > 0 && zcs[b - 1] >= nzt) continue;  // larger chunks clamp to the same launch
+            if (lb_set_tile(s, tys[a], zcs[b]) != LB_OK) continue;
+            if (lb_step(s, 2) != LB_OK) {  // warm-up and graph capture; skip shapes that fail
+                cudaGetLastError();
+                continue;
+            }
             cudaEventRecord(e0, c->stream);
-            if (rc == LB_OK) rc = lb_step(s, 2 * steps);
+            int r2 = lb_step(s, 2 * steps);
             cudaEventRecord(e1, c->stream);
             cudaEventSynchronize(e1);
             float ms = 0;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (rc == LB_OK && ms < best) {
+            if (r2 == LB_OK && ms < best) {
                 best = ms;
                 bty = tys[a];
                 bzc = zcs[b];

@@ -16,8 +16,10 @@
 // The 27 f and 7 g loads of plane z are issued at the top of the iteration,
 // before phase A, so their latency overlaps phases A and B.
 //
-// Layout in HBM (structure of arrays, site s = x + nx*(y + ny*z)):
-//   f: 27 planes of N, in place with the AA access pattern.  Even parity
+// Layout in HBM (structure of arrays, site s = x + nx*(y + ny*z), 32-bit):
+//   f: 27 planes of N holding delta_i = f_i/w_i - 1, in place with the AA
+//      access pattern; each plane has its own base pointer in the kernel
+//      arguments, so an access is one 32-bit index add and one wide multiply-add.  Even parity
 //      (t even) reads f_i(x) from slot (x, i) and writes f*_i to slot (x, -i);
 //      odd parity reads f_i(x) from slot (x - c_i, -i) and writes f*_i to slot
 //      (x + c_i, i).  Each slot is read and then written by the same site, so
@@ -39,17 +41,6 @@ namespace lbgb {
 __host__ __device__ constexpr int CX(int i) { return i % 3 - 1; }
 __host__ __device__ constexpr int CY(int i) { return (i / 3) % 3 - 1; }
 __host__ __device__ constexpr int CZ(int i) { return i / 9 - 1; }
-__host__ __device__ constexpr int NNZ(int i) {
-    return (CX(i) != 0) + (CY(i) != 0) + (CZ(i) != 0);
-}
-// D3Q27 weights by the number of non-zero components: 8/27, 2/27, 1/54, 1/216.
-__host__ __device__ constexpr float W27(int i) {
-    return NNZ(i) == 0 ? 8.f / 27.f : NNZ(i) == 1 ? 2.f / 27.f : NNZ(i) == 2 ? 1.f / 54.f : 1.f / 216.f;
-}
-__host__ __device__ constexpr float INVW27(int i) {
-    return NNZ(i) == 0 ? 27.f / 8.f : NNZ(i) == 1 ? 13.5f : NNZ(i) == 2 ? 54.f : 216.f;
-}
-
 enum Mode { MODE_STEP = 0, MODE_MOMENTS = 1, MODE_INIT = 2 };
 enum ForceKind { FK_NONE = 0, FK_CONST = 1, FK_ABC = 2, FK_LINEAR = 3 };
 
@@ -58,62 +49,58 @@ struct DevState {
     double A;        // linear-forcing amplitude used by the next step
     double K_target; // kinetic-energy target of the controller
     double diag[5];  // Phi, K, eps, max|u|, A_next of the last reduction
+    double mass;     // sum of p* - 1 of the last reduction
     int flags;       // bit 0: a non-finite value was seen
     int pad;
 };
 
-constexpr int NPART = 5;  // per-block partials: Phi, K, a2:a2, max|u|, non-finite
+// per-block partials: Phi, K, a2:a2, sum(p* - 1), max|u|^2
+constexpr int NPART = 5;
 
 struct StepArgs {
     int nx, ny, nz, zc;
-    long long N;
-    void* f;             // 27 planes of the storage type
-    const float* g_in;   // 7 planes, state at t
-    float* g_out;        // 7 planes, state at t+1 (INIT: state at 0)
+    int N;                  // sites, < 2^31 (32-bit site indices)
+    void* fk[27];           // population plane i (storage type), holding delta_i = f_i/w_i - 1
+    const float* gin[7];    // D3Q7 planes at t
+    float* gout[7];         // D3Q7 planes at t+1 (INIT: at 0)
     int force_kind;
     float omega, omega_phi, sharp, beta;  // sharp = (M/cs7^2)(4/W), beta = 3W sigma/2
-    float gc0, gc1, gc2; // constant force
+    float gc0, gc1, gc2;    // constant force
     float A_abc;
-    const float* abc;    // sin/cos tables: sin(kx) [nx], cos(kx) [nx], sin(ky), cos(ky), sin(kz), cos(kz)
+    const float* abc;       // sin(kx)[nx], cos(kx)[nx], sin(ky)[ny], cos(ky)[ny], sin(kz)[nz], cos(kz)[nz]
     const DevState* st;
-    double* partials;    // NPART per block
-    float* out_rho;      // MOMENTS outputs (any may be null)
+    double* partials;       // NPART per block
+    float* out_rho;         // MOMENTS outputs (any may be null)
     float* out_u;
     float* out_phi;
-    const float* in_phi; // INIT inputs
+    const float* in_phi;    // INIT inputs
     const float* in_u;
 };
 
 // ---------------------------------------------------------- storage codecs
+// Every storage type holds the shifted, scaled population delta_i = f_i/w_i - 1
+// (zero at rest, O(Ma) in a flow, never subnormal in 16 bits); all arithmetic
+// is FP32.  The moments and the collision below work on delta directly, so no
+// codec multiplies by w_i.
 template <class T>
 struct Codec;
 
 template <>
 struct Codec<float> {
-    static __device__ __forceinline__ float dec(float v, int) { return v; }
-    static __device__ __forceinline__ float enc(float f, int) { return f; }
+    static __device__ __forceinline__ float ld(const float* p) { return *p; }
+    static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 };
 
-// 16-bit storage holds the shifted, scaled deviation (f_i - w_i)/w_i, so the
-// stored number is O(Ma) and never subnormal; arithmetic stays FP32.
 template <>
 struct Codec<__half> {
-    static __device__ __forceinline__ float dec(__half v, int i) {
-        return fmaf(W27(i), __half2float(v), W27(i));
-    }
-    static __device__ __forceinline__ __half enc(float f, int i) {
-        return __float2half_rn((f - W27(i)) * INVW27(i));
-    }
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 };
 
 template <>
 struct Codec<__nv_bfloat16> {
-    static __device__ __forceinline__ float dec(__nv_bfloat16 v, int i) {
-        return fmaf(W27(i), __bfloat162float(v), W27(i));
-    }
-    static __device__ __forceinline__ __nv_bfloat16 enc(float f, int i) {
-        return __float2bfloat16_rn((f - W27(i)) * INVW27(i));
-    }
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
 __device__ __forceinline__ int wrap_mod(int v, int n) {
@@ -121,8 +108,10 @@ __device__ __forceinline__ int wrap_mod(int v, int n) {
     return r < 0 ? r + n : r;
 }
 
+__host__ __device__ constexpr int IDX(int cx, int cy, int cz) { return (cx + 1) + 3 * (cy + 1) + 9 * (cz + 1); }
+
 // ------------------------------------------------------- block reduction
-// Sums v0..v2 and maxes v3, v4 over the block; thread 0 gets the result.
+// Sums v0..v3 and maxes v4 over the block; thread 0 gets the result.
 template <int NT>
 __device__ __forceinline__ void block_reduce5(double& v0, double& v1, double& v2, double& v3,
                                               double& v4) {
@@ -133,7 +122,7 @@ __device__ __forceinline__ void block_reduce5(double& v0, double& v1, double& v2
         v0 += __shfl_down_sync(0xffffffffu, v0, off);
         v1 += __shfl_down_sync(0xffffffffu, v1, off);
         v2 += __shfl_down_sync(0xffffffffu, v2, off);
-        v3 = fmax(v3, __shfl_down_sync(0xffffffffu, v3, off));
+        v3 += __shfl_down_sync(0xffffffffu, v3, off);
         v4 = fmax(v4, __shfl_down_sync(0xffffffffu, v4, off));
     }
     if (lane == 0) {
@@ -152,13 +141,145 @@ __device__ __forceinline__ void block_reduce5(double& v0, double& v1, double& v2
             v0 += __shfl_down_sync(0xffffffffu, v0, off);
             v1 += __shfl_down_sync(0xffffffffu, v1, off);
             v2 += __shfl_down_sync(0xffffffffu, v2, off);
-            v3 = fmax(v3, __shfl_down_sync(0xffffffffu, v3, off));
+            v3 += __shfl_down_sync(0xffffffffu, v3, off);
             v4 = fmax(v4, __shfl_down_sync(0xffffffffu, v4, off));
         }
     }
 }
 
+// --------------------------------------------------- per-site arithmetic
+// Moments of h_i = w_i delta_i (delta_i = f_i/w_i - 1), using that the D3Q27
+// weights factor as w1(cx) w1(cy) w1(cz) with w1 = (1/6, 2/3, 1/6): sums are
+// taken along z, then y, then x with integer weights (1, 4, 1) and scaled by
+// 1/216 at the end.  Returns p' = p* - 1, m = sum f c, P' = sum f c c - I/3.
+__host__ __device__ __forceinline__ void shifted_moments(const float (&d)[27], float& pp, float& m0, float& m1,
+                                                float& m2, float& P00, float& P11, float& P22, float& P01,
+                                                float& P02, float& P12) {
+    float A0[3][3], A1[3][3], A2[3][3];  // [cy+1][cx+1]: z-weighted sums of cz^0, cz^1, cz^2 terms
+#pragma unroll
+    for (int cy = 0; cy < 3; ++cy)
+#pragma unroll
+        for (int cx = 0; cx < 3; ++cx) {
+            const int b = cx + 3 * cy;
+            const float em = d[b], e0 = d[b + 9], ep = d[b + 18];
+            const float s = em + ep;
+            A2[cy][cx] = s;
+            A0[cy][cx] = fmaf(4.f, e0, s);
+            A1[cy][cx] = ep - em;
+        }
+    float B00[3], B01[3], B02[3], B10[3], B11[3], B20[3];
+#pragma unroll
+    for (int cx = 0; cx < 3; ++cx) {
+        const float s0 = A0[0][cx] + A0[2][cx];
+        B00[cx] = fmaf(4.f, A0[1][cx], s0);
+        B02[cx] = s0;
+        B01[cx] = A0[2][cx] - A0[0][cx];
+        B10[cx] = fmaf(4.f, A1[1][cx], A1[0][cx] + A1[2][cx]);
+        B11[cx] = A1[2][cx] - A1[0][cx];
+        B20[cx] = fmaf(4.f, A2[1][cx], A2[0][cx] + A2[2][cx]);
+    }
+    constexpr float k = 1.f / 216.f;
+    const float t = B00[0] + B00[2];
+    pp = fmaf(4.f, B00[1], t) * k;
+    m0 = (B00[2] - B00[0]) * k;
+    P00 = t * k;
+    m1 = fmaf(4.f, B01[1], B01[0] + B01[2]) * k;
+    P01 = (B01[2] - B01[0]) * k;
+    P11 = fmaf(4.f, B02[1], B02[0] + B02[2]) * k;
+    m2 = fmaf(4.f, B10[1], B10[0] + B10[2]) * k;
+    P02 = (B10[2] - B10[0]) * k;
+    P12 = fmaf(4.f, B11[1], B11[0] + B11[2]) * k;
+    P22 = fmaf(4.f, B20[1], B20[0] + B20[2]) * k;
+}
+
+// f*_i/w_i - 1 is a quadratic polynomial in c_i:
+//   e0 + sum_a P^{sign c_a}_a [c_a != 0] + sum_{a<b} c_a c_b X_ab,
+// evaluated for all 27 directions reusing face and xy-edge partial sums.
+__host__ __device__ __forceinline__ void quad_poly27(float e0, const float (&Pp)[3], const float (&Pm)[3], float Xxy,
+                                            float Xxz, float Xyz, float (&v)[27]) {
+    v[IDX(0, 0, 0)] = e0;
+    const float fxp = e0 + Pp[0], fxm = e0 + Pm[0];
+    const float fyp = e0 + Pp[1], fym = e0 + Pm[1];
+    v[IDX(1, 0, 0)] = fxp;
+    v[IDX(-1, 0, 0)] = fxm;
+    v[IDX(0, 1, 0)] = fyp;
+    v[IDX(0, -1, 0)] = fym;
+    v[IDX(0, 0, 1)] = e0 + Pp[2];
+    v[IDX(0, 0, -1)] = e0 + Pm[2];
+    const float epp = fxp + (Pp[1] + Xxy), epm = fxp + (Pm[1] - Xxy);
+    const float emp = fxm + (Pp[1] - Xxy), emm = fxm + (Pm[1] + Xxy);
+    v[IDX(1, 1, 0)] = epp;
+    v[IDX(1, -1, 0)] = epm;
+    v[IDX(-1, 1, 0)] = emp;
+    v[IDX(-1, -1, 0)] = emm;
+    v[IDX(1, 0, 1)] = fxp + (Pp[2] + Xxz);
+    v[IDX(1, 0, -1)] = fxp + (Pm[2] - Xxz);
+    v[IDX(-1, 0, 1)] = fxm + (Pp[2] - Xxz);
+    v[IDX(-1, 0, -1)] = fxm + (Pm[2] + Xxz);
+    v[IDX(0, 1, 1)] = fyp + (Pp[2] + Xyz);
+    v[IDX(0, 1, -1)] = fyp + (Pm[2] - Xyz);
+    v[IDX(0, -1, 1)] = fym + (Pp[2] - Xyz);
+    v[IDX(0, -1, -1)] = fym + (Pm[2] + Xyz);
+    const float Vpp = Xxz + Xyz, Vpm = Xxz - Xyz;  // (sx Xxz + sy Xyz) for (+,+) and (+,-)
+    v[IDX(1, 1, 1)] = epp + (Pp[2] + Vpp);
+    v[IDX(1, 1, -1)] = epp + (Pm[2] - Vpp);
+    v[IDX(1, -1, 1)] = epm + (Pp[2] + Vpm);
+    v[IDX(1, -1, -1)] = epm + (Pm[2] - Vpm);
+    v[IDX(-1, 1, 1)] = emp + (Pp[2] - Vpm);
+    v[IDX(-1, 1, -1)] = emp + (Pm[2] + Vpm);
+    v[IDX(-1, -1, 1)] = emm + (Pp[2] - Vpp);
+    v[IDX(-1, -1, -1)] = emm + (Pm[2] + Vpp);
+}
+
+// Steps 8-10 for one site from its shifted moments: forced velocity u, total
+// force F = Fe + A u, Hermite coefficient a2 (Eq. 8 in closed form), and the
+// post-collision shifted populations v_i = f*_i/w_i - 1 of Eq. 7 with the
+// regularized non-equilibrium part and the Guo source (Eq. 6):
+//   f*_i/w_i = p* + 3 c.u + 4.5 (c.B.c - tr B/3) + 1.5 c.F - 1.5 u.F + 4.5 (c.u)(c.F),
+//   B = u u + (1 - omega) a2.
+// Also returns a2:a2 for the dissipation estimate.
+__host__ __device__ __forceinline__ void collide_site(float pp, float m0, float m1, float m2, float P00, float P11,
+                                                      float P22, float P01, float P02, float P12, float Fe0,
+                                                      float Fe1, float Fe2, float A_lin, float omega, float& u0,
+                                                      float& u1, float& u2, float& aa, float (&v)[27]) {
+    const float inv = 1.f / (1.f - 0.5f * A_lin);
+    u0 = fmaf(0.5f, Fe0, m0) * inv;
+    u1 = fmaf(0.5f, Fe1, m1) * inv;
+    u2 = fmaf(0.5f, Fe2, m2) * inv;
+    const float F0 = fmaf(A_lin, u0, Fe0), F1 = fmaf(A_lin, u1, Fe1), F2 = fmaf(A_lin, u2, Fe2);
+    // a2 = Pi - p*/3 I - u u + (u F + F u)/2, with Pi - p*/3 I = P' - p'/3 I
+    const float p3 = pp * (1.f / 3.f);
+    const float a00 = P00 - p3 - u0 * u0 + u0 * F0;
+    const float a11 = P11 - p3 - u1 * u1 + u1 * F1;
+    const float a22 = P22 - p3 - u2 * u2 + u2 * F2;
+    const float a01 = P01 - u0 * u1 + 0.5f * (u0 * F1 + F0 * u1);
+    const float a02 = P02 - u0 * u2 + 0.5f * (u0 * F2 + F0 * u2);
+    const float a12 = P12 - u1 * u2 + 0.5f * (u1 * F2 + F1 * u2);
+    aa = a00 * a00 + a11 * a11 + a22 * a22 + 2.f * (a01 * a01 + a02 * a02 + a12 * a12);
+    const float om1 = 1.f - omega;
+    const float B00 = fmaf(om1, a00, u0 * u0), B11 = fmaf(om1, a11, u1 * u1);
+    const float B22 = fmaf(om1, a22, u2 * u2), B01 = fmaf(om1, a01, u0 * u1);
+    const float B02 = fmaf(om1, a02, u0 * u2), B12 = fmaf(om1, a12, u1 * u2);
+    const float uF = u0 * F0 + u1 * F1 + u2 * F2;
+    const float e0 = pp - 1.5f * (B00 + B11 + B22 + uF);
+    const float L0 = fmaf(1.5f, F0, 3.f * u0), L1 = fmaf(1.5f, F1, 3.f * u1), L2 = fmaf(1.5f, F2, 3.f * u2);
+    const float Q0 = 4.5f * fmaf(u0, F0, B00), Q1 = 4.5f * fmaf(u1, F1, B11), Q2 = 4.5f * fmaf(u2, F2, B22);
+    const float Pp[3] = {Q0 + L0, Q1 + L1, Q2 + L2};
+    const float Pm[3] = {Q0 - L0, Q1 - L1, Q2 - L2};
+    const float Xxy = fmaf(9.f, B01, 4.5f * (u0 * F1 + u1 * F0));
+    const float Xxz = fmaf(9.f, B02, 4.5f * (u0 * F2 + u2 * F0));
+    const float Xyz = fmaf(9.f, B12, 4.5f * (u1 * F2 + u2 * F1));
+    quad_poly27(e0, Pp, Pm, Xxy, Xxz, Xyz, v);
+}
+
 // ------------------------------------------------------------ fused kernel
+// Shared-memory planes: Z6 = 6 Sz(phi) and D2 = 2 Dz(phi) on the halo-2 plane
+// (Sz = (1,4,1)/6 smoothing, Dz = central difference along z), so that the
+// lattice gradient of Sec. 2.3 becomes grad phi = G/72 with
+//   Gx = sum_y k (Z6(x+1) - Z6(x-1)), Gy = sum_x k (Z6(y+1) - Z6(y-1)),
+//   Gz = sum_x sum_y k k D2,  k = (1, 4, 1),
+// the same sum as the 26-neighbour stencil, regrouped.  The curvature uses the
+// same factorisation on n (planes 6 Sz n_x, 6 Sz n_y, 2 Dz n_z).
 template <class FT, int TY, int MODE, int PAR>
 __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 512 / (32 * TY)))
 fused_step_kernel(const StepArgs a) {
@@ -169,110 +290,143 @@ fused_step_kernel(const StepArgs a) {
     constexpr int NA = (NHA + NT - 1) / NT;
     constexpr int NB = (NHB + NT - 1) / NT;
 
-    __shared__ float s_phi[4][HY][HX];
-    __shared__ float s_n[4][3][BY][BX];
-    __shared__ float s_g[2][4][TY][TX];  // grad phi and |grad phi| of the interior
+    __shared__ float s_Z[2][NHA];        // 6 Sz phi, planes by parity
+    __shared__ float s_D[2][NHA];        // 2 Dz phi
+    __shared__ float s_phi[4][NT];       // phi of the interior, 4-plane ring
+    __shared__ float s_n[4][3][NHB];     // unit normal, 4-plane ring
+    __shared__ float s_k[3][NHB];        // 6 Sz n_x, 6 Sz n_y, 2 Dz n_z of one plane
+    __shared__ float s_grad[2][4][NT];   // grad phi and |grad phi| of the interior
 
     using C = Codec<FT>;
-    FT* __restrict__ F = static_cast<FT*>(a.f);
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const long long N = a.N;
-    const long long plane = (long long)nx * ny;
+    const int N = a.N;
+    const int plane = nx * ny;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * a.zc;
     const int z1 = min(z0 + a.zc, nz);
 
-    // phase-A sites (halo-2 plane), fixed for the whole march
-    int a_row[NA], a_idx[NA];
+    // phase-A slots (halo-2 plane), fixed for the whole march
+    int a_row[NA], a_idx[NA], a_int[NA];
+    float ph1[NA], ph2[NA];  // phi one and two planes below, per slot
 #pragma unroll
     for (int k = 0; k < NA; ++k) {
         const int idx = tid + k * NT;
         a_idx[k] = idx < NHA ? idx : -1;
         const int ly = idx / HX, lx = idx - (idx / HX) * HX;
         a_row[k] = wrap_mod(y0 + ly - 2, ny) * nx + wrap_mod(x0 + lx - 2, nx);
+        a_int[k] = (idx < NHA && lx >= 2 && lx < TX + 2 && ly >= 2 && ly < TY + 2) ? (ly - 2) * TX + (lx - 2) : -1;
+        ph1[k] = 0.f;
+        ph2[k] = 0.f;
     }
 
-    // phase-C site
+    // phase-C site and its periodic neighbour offsets (32-bit site indices)
     const int lx = tid % TX, ly = tid / TX;
     const int gx = x0 + lx, gy = y0 + ly;
     const bool active = gx < nx && gy < ny;
     const int cxs = active ? gx : nx - 1, cys = active ? gy : ny - 1;
-    const int Xo[3] = {cxs == 0 ? nx - 1 : cxs - 1, cxs, cxs == nx - 1 ? 0 : cxs + 1};
-    const int Yo[3] = {(cys == 0 ? ny - 1 : cys - 1) * nx, cys * nx, (cys == ny - 1 ? 0 : cys + 1) * nx};
+    const int row_s = cys * nx + cxs;
+    const int DX0 = cxs == 0 ? nx - 1 : -1, DX2 = cxs == nx - 1 ? 1 - nx : 1;
+    const int DY0 = cys == 0 ? (ny - 1) * nx : -nx, DY2 = cys == ny - 1 ? (1 - ny) * nx : nx;
+    const int DX[3] = {DX0, 0, DX2};
+    const int DY[3] = {DY0, 0, DY2};
+    const int c1 = (ly + 1) * BX + (lx + 1);  // own site in the halo-1 plane
 
     float A_lin = 0.f;
     if (MODE != MODE_INIT && a.force_kind == FK_LINEAR) A_lin = (float)a.st->A;
 
-    double d_phi = 0.0, d_K = 0.0, d_aa = 0.0, d_umax = 0.0, d_bad = 0.0;
+    // FP32 per-thread partial sums over this thread's <= zc sites; FP64 beyond
+    float s_phi_acc = 0.f, s_K = 0.f, s_aa = 0.f, s_mass = 0.f, s_umax2 = 0.f;
 
-    auto phaseA = [&](int zp) {
-        const long long zb = (long long)wrap_mod(zp, nz) * plane;
-        float* ring = &s_phi[zp & 3][0][0];
+    auto phaseA = [&](int zp, bool make_zd) {
+        const int zb = wrap_mod(zp, nz) * plane;
 #pragma unroll
         for (int k = 0; k < NA; ++k) {
             if (a_idx[k] >= 0) {
-                const long long s = zb + a_row[k];
+                const int s = zb + a_row[k];
                 float p;
                 if (MODE == MODE_INIT) {
                     p = a.in_phi[s];
                 } else {
-                    p = 0.f;
+                    p = __ldg(a.gin[0] + s);
 #pragma unroll
-                    for (int q = 0; q < 7; ++q) p += __ldg(a.g_in + q * N + s);
+                    for (int q = 1; q < 7; ++q) p += __ldg(a.gin[q] + s);
                 }
-                ring[a_idx[k]] = p;
+                if (make_zd) {
+                    s_Z[(zp - 1) & 1][a_idx[k]] = fmaf(4.f, ph1[k], ph2[k] + p);
+                    s_D[(zp - 1) & 1][a_idx[k]] = p - ph2[k];
+                }
+                if (a_int[k] >= 0) s_phi[zp & 3][a_int[k]] = p;
+                ph2[k] = ph1[k];
+                ph1[k] = p;
             }
         }
     };
 
-    auto phaseB = [&](int zp) {
+    // n at plane zp on the halo-1 plane; with make_k also the curvature
+    // ingredients of plane zp-1 (needs n at zp-2, zp-1, zp of the same site,
+    // which this thread wrote itself).
+    auto phaseB = [&](int zp, bool make_k) {
+        const float* Z = s_Z[zp & 1];
+        const float* D = s_D[zp & 1];
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
             const int idx = tid + k * NT;
             if (idx < NHB) {
                 const int by = idx / BX, bx = idx - (idx / BX) * BX;
-                float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-#pragma unroll
-                for (int i = 14; i < 27; ++i) {
-                    const int cx = CX(i), cy = CY(i), cz = CZ(i);
-                    const float d = s_phi[(zp + cz) & 3][by + 1 + cy][bx + 1 + cx] -
-                                    s_phi[(zp - cz) & 3][by + 1 - cy][bx + 1 - cx];
-                    const float wd = W27(i) * d;
-                    if (cx > 0) g0 += wd; else if (cx < 0) g0 -= wd;
-                    if (cy > 0) g1 += wd; else if (cy < 0) g1 -= wd;
-                    if (cz > 0) g2 += wd; else if (cz < 0) g2 -= wd;
-                }
-                g0 *= 3.f; g1 *= 3.f; g2 *= 3.f;
-                const float m = sqrtf(g0 * g0 + g1 * g1 + g2 * g2);
-                const float den = fmaxf(m, 1e-10f);
-                s_n[zp & 3][0][by][bx] = g0 / den;
-                s_n[zp & 3][1][by][bx] = g1 / den;
-                s_n[zp & 3][2][by][bx] = g2 / den;
+                const int c = (by + 1) * HX + (bx + 1);
+                const float zmm = Z[c - HX - 1], zm0 = Z[c - HX], zmp = Z[c - HX + 1];
+                const float z0m = Z[c - 1], z0p = Z[c + 1];
+                const float zpm = Z[c + HX - 1], zp0 = Z[c + HX], zpp = Z[c + HX + 1];
+                // differences before sums keep the small gradients of a nearly uniform phi accurate
+                const float Gx = fmaf(4.f, z0p - z0m, (zmp - zmm) + (zpp - zpm));
+                const float Gy = fmaf(4.f, zp0 - zm0, (zpm - zmm) + (zpp - zmp));
+                const float rm = fmaf(4.f, D[c - 1], D[c - HX - 1] + D[c + HX - 1]);
+                const float r0 = fmaf(4.f, D[c], D[c - HX] + D[c + HX]);
+                const float rp = fmaf(4.f, D[c + 1], D[c - HX + 1] + D[c + HX + 1]);
+                const float Gz = fmaf(4.f, r0, rm + rp);
+                constexpr float k72 = 1.f / 72.f;
+                const float g0 = Gx * k72, g1 = Gy * k72, g2 = Gz * k72;
+                const float gg = g0 * g0 + g1 * g1 + g2 * g2;
+                const float r = rsqrtf(fmaxf(gg, 1e-20f));  // 1 / max(|grad phi|, 1e-10)
+                const float n0 = g0 * r, n1 = g1 * r, n2 = g2 * r;
+                s_n[zp & 3][0][idx] = n0;
+                s_n[zp & 3][1][idx] = n1;
+                s_n[zp & 3][2][idx] = n2;
                 if (bx >= 1 && bx <= TX && by >= 1 && by <= TY) {
-                    s_g[zp & 1][0][by - 1][bx - 1] = g0;
-                    s_g[zp & 1][1][by - 1][bx - 1] = g1;
-                    s_g[zp & 1][2][by - 1][bx - 1] = g2;
-                    s_g[zp & 1][3][by - 1][bx - 1] = m;
+                    const int e = (by - 1) * TX + (bx - 1);
+                    s_grad[zp & 1][0][e] = g0;
+                    s_grad[zp & 1][1][e] = g1;
+                    s_grad[zp & 1][2][e] = g2;
+                    s_grad[zp & 1][3][e] = gg * r;  // |grad phi|
+                }
+                if (make_k) {
+                    s_k[0][idx] = fmaf(4.f, s_n[(zp - 1) & 3][0][idx], s_n[(zp - 2) & 3][0][idx] + n0);
+                    s_k[1][idx] = fmaf(4.f, s_n[(zp - 1) & 3][1][idx], s_n[(zp - 2) & 3][1][idx] + n1);
+                    s_k[2][idx] = n2 - s_n[(zp - 2) & 3][2][idx];
                 }
             }
         }
     };
 
-    // prologue: phi on planes z0-2 .. z0+1, n on z0-1 and z0
-    for (int zp = z0 - 2; zp <= z0 + 1; ++zp) phaseA(zp);
+    // prologue: phi history from z0-2, gradient planes and n at z0-1, z0
+    phaseA(z0 - 2, false);
+    phaseA(z0 - 1, false);
+    phaseA(z0, true);
     __syncthreads();
-    phaseB(z0 - 1);
-    phaseB(z0);
+    phaseB(z0 - 1, false);
+    phaseA(z0 + 1, true);
     __syncthreads();
+    phaseB(z0, false);
 
     for (int z = z0; z < z1; ++z) {
-        const long long Zo[3] = {(long long)(z == 0 ? nz - 1 : z - 1) * plane, (long long)z * plane,
-                                 (long long)(z == nz - 1 ? 0 : z + 1) * plane};
-        const long long s = Zo[1] + Yo[1] + Xo[1];
+        const int DZ0 = z == 0 ? (nz - 1) * plane : -plane;
+        const int DZ2 = z == nz - 1 ? (1 - nz) * plane : plane;
+        const int DZ[3] = {DZ0, 0, DZ2};
+        const int s = z * plane + row_s;
 
         // ---- issue this plane's population loads first
-        float fl[27];
+        float dl[27];
         float gl[7];
         float uin0 = 0.f, uin1 = 0.f, uin2 = 0.f;
         if (active) {
@@ -283,81 +437,74 @@ fused_step_kernel(const StepArgs a) {
             } else {
 #pragma unroll
                 for (int i = 0; i < 27; ++i) {
-                    long long src;
                     if (PAR == 0) {
-                        src = (long long)i * N + s;
+                        dl[i] = C::ld(static_cast<const FT*>(a.fk[i]) + s);
                     } else {  // f_i(x) sits in slot (x - c_i, opposite of i)
-                        src = (long long)(26 - i) * N + Zo[1 - CZ(i)] + Yo[1 - CY(i)] + Xo[1 - CX(i)];
+                        const int src = s + DZ[1 - CZ(i)] + DY[1 - CY(i)] + DX[1 - CX(i)];
+                        dl[i] = C::ld(static_cast<const FT*>(a.fk[26 - i]) + src);
                     }
-                    fl[i] = C::dec(F[src], i);
                 }
                 if (MODE == MODE_STEP) {
 #pragma unroll
-                    for (int q = 0; q < 7; ++q) gl[q] = __ldg(a.g_in + q * N + s);
+                    for (int q = 0; q < 7; ++q) gl[q] = __ldg(a.gin[q] + s);
                 }
             }
         }
 
-        phaseA(z + 2);
+        phaseA(z + 2, true);
         __syncthreads();
-        phaseB(z + 1);
+        phaseB(z + 1, true);
         __syncthreads();
 
         if (active) {
-            const float phi = s_phi[z & 3][ly + 2][lx + 2];
-            const float n0 = s_n[z & 3][0][ly + 1][lx + 1];
-            const float n1 = s_n[z & 3][1][ly + 1][lx + 1];
-            const float n2 = s_n[z & 3][2][ly + 1][lx + 1];
+            const int e = ly * TX + lx;
+            const float phi = s_phi[z & 3][e];
+            const float n0 = s_n[z & 3][0][c1], n1 = s_n[z & 3][1][c1], n2 = s_n[z & 3][2][c1];
 
             if (MODE == MODE_INIT) {
-                // f = f^eq(p* = 1, u) in the even-parity layout, g = g^eq(phi, u, n)
+                // f = f^eq(p* = 1, u): delta_i = 3 c.u + 4.5 (c.u)^2 - 1.5 u^2 (even layout)
                 const float u0 = uin0, u1 = uin1, u2 = uin2;
                 const float uu = u0 * u0 + u1 * u1 + u2 * u2;
-                const float E0 = 1.f - 1.5f * uu;
-                F[13 * N + s] = C::enc(W27(13) * E0, 13);
+                const float Pp[3] = {fmaf(4.5f * u0, u0, 3.f * u0), fmaf(4.5f * u1, u1, 3.f * u1),
+                                     fmaf(4.5f * u2, u2, 3.f * u2)};
+                const float Pm[3] = {fmaf(4.5f * u0, u0, -3.f * u0), fmaf(4.5f * u1, u1, -3.f * u1),
+                                     fmaf(4.5f * u2, u2, -3.f * u2)};
+                float v[27];
+                quad_poly27(-1.5f * uu, Pp, Pm, 9.f * u0 * u1, 9.f * u0 * u2, 9.f * u1 * u2, v);
 #pragma unroll
-                for (int i = 14; i < 27; ++i) {
-                    const int cx = CX(i), cy = CY(i), cz = CZ(i);
-                    const float cu = cx * u0 + cy * u1 + cz * u2;
-                    const float E = E0 + 4.5f * cu * cu;
-                    const float O = 3.f * cu;
-                    F[(long long)i * N + s] = C::enc(W27(i) * (E + O), i);
-                    F[(long long)(26 - i) * N + s] = C::enc(W27(26 - i) * (E - O), 26 - i);
-                }
-                const float phs = a.sharp * phi * (1.f - phi);
-                float* G = a.g_out;
-                G[s] = 0.25f * phi;
-                G[N + s] = 0.125f * (phi + (4.f * phi * u0 + phs * n0));
-                G[2 * N + s] = 0.125f * (phi - (4.f * phi * u0 + phs * n0));
-                G[3 * N + s] = 0.125f * (phi + (4.f * phi * u1 + phs * n1));
-                G[4 * N + s] = 0.125f * (phi - (4.f * phi * u1 + phs * n1));
-                G[5 * N + s] = 0.125f * (phi + (4.f * phi * u2 + phs * n2));
-                G[6 * N + s] = 0.125f * (phi - (4.f * phi * u2 + phs * n2));
-                d_phi += (double)phi;
-                d_K += 0.5 * (double)uu;
-                d_umax = fmax(d_umax, (double)sqrtf(uu));
-                if (!isfinite(phi + uu)) d_bad = 1.0;
+                for (int i = 0; i < 27; ++i) C::st(static_cast<FT*>(a.fk[i]) + s, v[i]);
+                const float phs = a.sharp * fmaxf(phi * (1.f - phi), 0.f);  // interface indicator, 0 outside [0, 1]
+                const float j0 = fmaf(4.f * phi, u0, phs * n0);
+                const float j1 = fmaf(4.f * phi, u1, phs * n1);
+                const float j2 = fmaf(4.f * phi, u2, phs * n2);
+                a.gout[0][s] = 0.25f * phi;
+                a.gout[1][s] = 0.125f * (phi + j0);
+                a.gout[2][s] = 0.125f * (phi - j0);
+                a.gout[3][s] = 0.125f * (phi + j1);
+                a.gout[4][s] = 0.125f * (phi - j1);
+                a.gout[5][s] = 0.125f * (phi + j2);
+                a.gout[6][s] = 0.125f * (phi - j2);
+                s_phi_acc += phi;
+                s_K = fmaf(0.5f, uu, s_K);
+                s_umax2 = fmaxf(s_umax2, uu);
             } else {
-                // ---- step 4: kappa = div n (lattice stencil over the n ring)
-                float kap = 0.f;
-#pragma unroll
-                for (int i = 14; i < 27; ++i) {
-                    const int cx = CX(i), cy = CY(i), cz = CZ(i);
-                    const int zpl = (z + cz) & 3, zmi = (z - cz) & 3;
-                    float acc = 0.f;
-                    if (cx != 0)
-                        acc += cx * (s_n[zpl][0][ly + 1 + cy][lx + 1 + cx] - s_n[zmi][0][ly + 1 - cy][lx + 1 - cx]);
-                    if (cy != 0)
-                        acc += cy * (s_n[zpl][1][ly + 1 + cy][lx + 1 + cx] - s_n[zmi][1][ly + 1 - cy][lx + 1 - cx]);
-                    if (cz != 0)
-                        acc += cz * (s_n[zpl][2][ly + 1 + cy][lx + 1 + cx] - s_n[zmi][2][ly + 1 - cy][lx + 1 - cx]);
-                    kap += W27(i) * acc;
-                }
-                kap *= 3.f;
+                // ---- step 4: kappa = div n from the factorised planes (sum / 72)
+                const float* K0 = s_k[0];
+                const float* K1 = s_k[1];
+                const float* K2 = s_k[2];
+                const float kx = fmaf(4.f, K0[c1 + 1] - K0[c1 - 1],
+                                      (K0[c1 - BX + 1] - K0[c1 - BX - 1]) + (K0[c1 + BX + 1] - K0[c1 + BX - 1]));
+                const float ky = fmaf(4.f, K1[c1 + BX] - K1[c1 - BX],
+                                      (K1[c1 + BX - 1] - K1[c1 - BX - 1]) + (K1[c1 + BX + 1] - K1[c1 - BX + 1]));
+                const float qm = fmaf(4.f, K2[c1 - 1], K2[c1 - BX - 1] + K2[c1 + BX - 1]);
+                const float q0 = fmaf(4.f, K2[c1], K2[c1 - BX] + K2[c1 + BX]);
+                const float qp = fmaf(4.f, K2[c1 + 1], K2[c1 - BX + 1] + K2[c1 + BX + 1]);
+                const float kz = fmaf(4.f, q0, qm + qp);
+                const float kap = (kx + ky + kz) * (1.f / 72.f);
 
                 // ---- steps 5-6: surface tension and external force
-                const float gr0 = s_g[z & 1][0][ly][lx], gr1 = s_g[z & 1][1][ly][lx];
-                const float gr2 = s_g[z & 1][2][ly][lx], grm = s_g[z & 1][3][ly][lx];
+                const float gr0 = s_grad[z & 1][0][e], gr1 = s_grad[z & 1][1][e];
+                const float gr2 = s_grad[z & 1][2][e], grm = s_grad[z & 1][3][e];
                 const float fsc = -a.beta * kap * grm;
                 float Fe0 = fsc * gr0, Fe1 = fsc * gr1, Fe2 = fsc * gr2;
                 if (a.force_kind == FK_CONST) {
@@ -372,33 +519,17 @@ fused_step_kernel(const StepArgs a) {
                     Fe2 += a.A_abc * (sy + cxv);
                 }
 
-                // ---- step 7: moments of f
-                float p = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f;
-                float P00 = 0.f, P11 = 0.f, P22 = 0.f, P01 = 0.f, P02 = 0.f, P12 = 0.f;
-#pragma unroll
-                for (int i = 0; i < 27; ++i) {
-                    const int cx = CX(i), cy = CY(i), cz = CZ(i);
-                    const float v = fl[i];
-                    p += v;
-                    if (cx > 0) m0 += v; else if (cx < 0) m0 -= v;
-                    if (cy > 0) m1 += v; else if (cy < 0) m1 -= v;
-                    if (cz > 0) m2 += v; else if (cz < 0) m2 -= v;
-                    if (cx != 0) P00 += v;
-                    if (cy != 0) P11 += v;
-                    if (cz != 0) P22 += v;
-                    if (cx * cy > 0) P01 += v; else if (cx * cy < 0) P01 -= v;
-                    if (cx * cz > 0) P02 += v; else if (cx * cz < 0) P02 -= v;
-                    if (cy * cz > 0) P12 += v; else if (cy * cz < 0) P12 -= v;
-                }
-
-                // ---- step 8: forced velocity and total force
-                const float inv = 1.f / (1.f - 0.5f * A_lin);
-                const float u0 = (m0 + 0.5f * Fe0) * inv;
-                const float u1 = (m1 + 0.5f * Fe1) * inv;
-                const float u2 = (m2 + 0.5f * Fe2) * inv;
+                // ---- step 7: moments of the shifted populations
+                float pp, m0, m1, m2, P00, P11, P22, P01, P02, P12;
+                shifted_moments(dl, pp, m0, m1, m2, P00, P11, P22, P01, P02, P12);
 
                 if (MODE == MODE_MOMENTS) {
-                    if (a.out_rho) a.out_rho[s] = p;
+                    // ---- step 8: forced velocity
+                    const float inv = 1.f / (1.f - 0.5f * A_lin);
+                    const float u0 = fmaf(0.5f, Fe0, m0) * inv;
+                    const float u1 = fmaf(0.5f, Fe1, m1) * inv;
+                    const float u2 = fmaf(0.5f, Fe2, m2) * inv;
+                    if (a.out_rho) a.out_rho[s] = 1.f + pp;
                     if (a.out_u) {
                         a.out_u[s] = u0;
                         a.out_u[N + s] = u1;
@@ -406,89 +537,55 @@ fused_step_kernel(const StepArgs a) {
                     }
                     if (a.out_phi) a.out_phi[s] = phi;
                 } else {
-                    const float F0 = Fe0 + A_lin * u0, F1 = Fe1 + A_lin * u1, F2 = Fe2 + A_lin * u2;
+                    // ---- steps 8-10: velocity, force, Hermite coefficient, collision
+                    float u0, u1, u2, aa, v[27];
+                    collide_site(pp, m0, m1, m2, P00, P11, P22, P01, P02, P12, Fe0, Fe1, Fe2, A_lin, a.omega,
+                                 u0, u1, u2, aa, v);
 
-                    // ---- step 9: a2 = Pi - p/3 I - u u + (u F + F u)/2
-                    const float p3 = p * (1.f / 3.f);
-                    const float a00 = P00 - p3 - u0 * u0 + u0 * F0;
-                    const float a11 = P11 - p3 - u1 * u1 + u1 * F1;
-                    const float a22 = P22 - p3 - u2 * u2 + u2 * F2;
-                    const float a01 = P01 - u0 * u1 + 0.5f * (u0 * F1 + F0 * u1);
-                    const float a02 = P02 - u0 * u2 + 0.5f * (u0 * F2 + F0 * u2);
-                    const float a12 = P12 - u1 * u2 + 0.5f * (u1 * F2 + F1 * u2);
-
-                    // ---- step 13 (per site): FP64 accumulation
+                    // ---- step 13 (per site): partial sums
                     const float uu = u0 * u0 + u1 * u1 + u2 * u2;
-                    const float aa = a00 * a00 + a11 * a11 + a22 * a22 +
-                                     2.f * (a01 * a01 + a02 * a02 + a12 * a12);
-                    d_phi += (double)phi;
-                    d_K += 0.5 * (double)uu;
-                    d_aa += (double)aa;
-                    d_umax = fmax(d_umax, (double)sqrtf(uu));
-                    if (!isfinite(p + uu + phi + aa)) d_bad = 1.0;
+                    s_phi_acc += phi;
+                    s_K = fmaf(0.5f, uu, s_K);
+                    s_aa += aa;
+                    s_mass += pp;
+                    s_umax2 = fmaxf(s_umax2, uu);
 
-                    // ---- step 10: regularized collision, written per opposite pair
-                    const float om1 = 1.f - a.omega;
-                    const float B00 = u0 * u0 + om1 * a00, B11 = u1 * u1 + om1 * a11;
-                    const float B22 = u2 * u2 + om1 * a22, B01 = u0 * u1 + om1 * a01;
-                    const float B02 = u0 * u2 + om1 * a02, B12 = u1 * u2 + om1 * a12;
-                    const float trB = B00 + B11 + B22;
-                    const float uF = u0 * F0 + u1 * F1 + u2 * F2;
-                    const float E0 = p - 1.5f * trB - 1.5f * uF;
-                    {
-                        const float f13 = W27(13) * E0;
-                        const long long dst = (long long)13 * N + s;
-                        F[dst] = C::enc(f13, 13);
-                    }
+                    // ---- step 12: AA streaming stores
 #pragma unroll
-                    for (int i = 14; i < 27; ++i) {
-                        const int cx = CX(i), cy = CY(i), cz = CZ(i);
-                        const float cu = cx * u0 + cy * u1 + cz * u2;
-                        const float cF = cx * F0 + cy * F1 + cz * F2;
-                        const float cBc = cx * cx * B00 + cy * cy * B11 + cz * cz * B22 +
-                                          2.f * (cx * cy * B01 + cx * cz * B02 + cy * cz * B12);
-                        const float E = E0 + 4.5f * cBc + 4.5f * cu * cF;
-                        const float O = 3.f * cu + 1.5f * cF;
-                        const float fi = W27(i) * (E + O);        // direction  c
-                        const float fj = W27(26 - i) * (E - O);   // direction -c
-                        long long di, dj;
+                    for (int i = 0; i < 27; ++i) {
                         if (PAR == 0) {  // f*_i to slot (x, opposite of i)
-                            di = (long long)(26 - i) * N + s;
-                            dj = (long long)i * N + s;
+                            C::st(static_cast<FT*>(a.fk[26 - i]) + s, v[i]);
                         } else {         // f*_i to slot (x + c_i, i)
-                            di = (long long)i * N + Zo[1 + cz] + Yo[1 + cy] + Xo[1 + cx];
-                            dj = (long long)(26 - i) * N + Zo[1 - cz] + Yo[1 - cy] + Xo[1 - cx];
+                            const int dst = s + DZ[1 + CZ(i)] + DY[1 + CY(i)] + DX[1 + CX(i)];
+                            C::st(static_cast<FT*>(a.fk[i]) + dst, v[i]);
                         }
-                        F[di] = C::enc(fi, PAR == 0 ? 26 - i : i);
-                        F[dj] = C::enc(fj, PAR == 0 ? i : 26 - i);
                     }
 
-                    // ---- step 11: D3Q7 BGK with the sharpening equilibrium; step 12: push
+                    // ---- step 11: D3Q7 BGK with the sharpening equilibrium, push
                     const float om = a.omega_phi;
-                    const float phs = a.sharp * phi * (1.f - phi);
-                    const float ge0 = 0.25f * phi;
-                    const float j0 = 4.f * phi * u0 + phs * n0;
-                    const float j1 = 4.f * phi * u1 + phs * n1;
-                    const float j2 = 4.f * phi * u2 + phs * n2;
-                    float* G = a.g_out;
-                    G[s] = gl[0] + om * (ge0 - gl[0]);
-                    G[N + Zo[1] + Yo[1] + Xo[2]] = gl[1] + om * (0.125f * (phi + j0) - gl[1]);
-                    G[2 * N + Zo[1] + Yo[1] + Xo[0]] = gl[2] + om * (0.125f * (phi - j0) - gl[2]);
-                    G[3 * N + Zo[1] + Yo[2] + Xo[1]] = gl[3] + om * (0.125f * (phi + j1) - gl[3]);
-                    G[4 * N + Zo[1] + Yo[0] + Xo[1]] = gl[4] + om * (0.125f * (phi - j1) - gl[4]);
-                    G[5 * N + Zo[2] + Yo[1] + Xo[1]] = gl[5] + om * (0.125f * (phi + j2) - gl[5]);
-                    G[6 * N + Zo[0] + Yo[1] + Xo[1]] = gl[6] + om * (0.125f * (phi - j2) - gl[6]);
+                    const float phs = a.sharp * fmaxf(phi * (1.f - phi), 0.f);  // interface indicator, 0 outside [0, 1]
+                    const float j0 = fmaf(4.f * phi, u0, phs * n0);
+                    const float j1 = fmaf(4.f * phi, u1, phs * n1);
+                    const float j2 = fmaf(4.f * phi, u2, phs * n2);
+                    a.gout[0][s] = fmaf(om, 0.25f * phi - gl[0], gl[0]);
+                    a.gout[1][s + DX[2]] = fmaf(om, 0.125f * (phi + j0) - gl[1], gl[1]);
+                    a.gout[2][s + DX[0]] = fmaf(om, 0.125f * (phi - j0) - gl[2], gl[2]);
+                    a.gout[3][s + DY[2]] = fmaf(om, 0.125f * (phi + j1) - gl[3], gl[3]);
+                    a.gout[4][s + DY[0]] = fmaf(om, 0.125f * (phi - j1) - gl[4], gl[4]);
+                    a.gout[5][s + DZ[2]] = fmaf(om, 0.125f * (phi + j2) - gl[5], gl[5]);
+                    a.gout[6][s + DZ[0]] = fmaf(om, 0.125f * (phi - j2) - gl[6], gl[6]);
                 }
             }
         }
     }
 
     if (MODE != MODE_MOMENTS) {
-        block_reduce5<NT>(d_phi, d_K, d_aa, d_umax, d_bad);
+        double v0 = s_phi_acc, v1 = s_K, v2 = s_aa, v3 = s_mass, v4 = s_umax2;
+        block_reduce5<NT>(v0, v1, v2, v3, v4);
         if (tid == 0) {
             const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
             double* out = a.partials + b * NPART;
-            out[0] = d_phi; out[1] = d_K; out[2] = d_aa; out[3] = d_umax; out[4] = d_bad;
+            out[0] = v0; out[1] = v1; out[2] = v2; out[3] = v3; out[4] = v4;
         }
     }
 }

@@ -35,7 +35,6 @@ cudaError_t launch_fused<LBGB_FT>(int mode, int parity, int ty, dim3 grid, const
     switch (ty) {
         case 4: return launch_ty<LBGB_FT, 4>(mode, parity, grid, a, st);
         case 8: return launch_ty<LBGB_FT, 8>(mode, parity, grid, a, st);
-        case 16: return launch_ty<LBGB_FT, 16>(mode, parity, grid, a, st);
         default: return cudaErrorInvalidValue;
     }
 }
