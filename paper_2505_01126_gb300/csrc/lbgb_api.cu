@@ -20,7 +20,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/lbgb.h"
+#include "lbgb.h"
 #include "lbgb_kernels.cuh"
 
 using namespace lbgb;
@@ -167,10 +167,12 @@ void set_g(StepArgs& a, const lb_ctx* c, int par) {
 
 cudaError_t launch_any(const lb_ctx* c, int mode, int parity, int ty, dim3 grid, const StepArgs& a,
                        cudaStream_t s) {
+    // float4 phase-A loads need 16-byte aligned rows: nx % 4 == 0 (planes then start aligned too)
+    const bool vec = (c->nx % 4) == 0;
     switch (c->storage) {
-        case LB_F32: return launch_fused<float>(mode, parity, ty, grid, a, s);
-        case LB_F16_SHIFTED: return launch_fused<__half>(mode, parity, ty, grid, a, s);
-        case LB_BF16_SHIFTED: return launch_fused<__nv_bfloat16>(mode, parity, ty, grid, a, s);
+        case LB_F32: return launch_fused<float>(mode, parity, ty, vec, grid, a, s);
+        case LB_F16_SHIFTED: return launch_fused<__half>(mode, parity, ty, vec, grid, a, s);
+        case LB_BF16_SHIFTED: return launch_fused<__nv_bfloat16>(mode, parity, ty, vec, grid, a, s);
     }
     return cudaErrorInvalidValue;
 }

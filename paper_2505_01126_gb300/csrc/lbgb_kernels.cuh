@@ -34,6 +34,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <stdint.h>
 
 namespace lbgb {
@@ -280,7 +281,11 @@ __host__ __device__ __forceinline__ void collide_site(float pp, float m0, float 
 //   Gz = sum_x sum_y k k D2,  k = (1, 4, 1),
 // the same sum as the 26-neighbour stencil, regrouped.  The curvature uses the
 // same factorisation on n (planes 6 Sz n_x, 6 Sz n_y, 2 Dz n_z).
-template <class FT, int TY, int MODE, int PAR>
+//
+// Phase A reads the D3Q7 planes either per site (VEC = false) or, when nx is a
+// multiple of 4, as float4 quads of 4 consecutive sites covering the halo row
+// x0-4 .. x0+TX+3 (VEC = true): 7 vector loads per 4 sites.
+template <class FT, int TY, int MODE, int PAR, bool VEC>
 __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 512 / (32 * TY)))
 fused_step_kernel(const StepArgs a) {
     constexpr int TX = 32;
@@ -306,18 +311,35 @@ fused_step_kernel(const StepArgs a) {
     const int z0 = blockIdx.z * a.zc;
     const int z1 = min(z0 + a.zc, nz);
 
-    // phase-A slots (halo-2 plane), fixed for the whole march
-    int a_row[NA], a_idx[NA], a_int[NA];
-    float ph1[NA], ph2[NA];  // phi one and two planes below, per slot
+    // phase-A slots (halo-2 plane), fixed for the whole march.  A slot is one
+    // site (scalar) or one float4 quad of 4 sites (VEC).
+    constexpr int QX = TX / 4 + 2;  // quads per halo row
+    constexpr int NQ = QX * HY;
+    constexpr int NS = VEC ? (NQ + NT - 1) / NT : NA;
+    constexpr int NV = VEC ? 4 : 1;
+    int a_row[NS], a_idx[NS], a_int[NS];
+    float ph1[NS][NV], ph2[NS][NV];  // phi one and two planes below, per site of a slot
 #pragma unroll
-    for (int k = 0; k < NA; ++k) {
+    for (int k = 0; k < NS; ++k) {
         const int idx = tid + k * NT;
-        a_idx[k] = idx < NHA ? idx : -1;
-        const int ly = idx / HX, lx = idx - (idx / HX) * HX;
-        a_row[k] = wrap_mod(y0 + ly - 2, ny) * nx + wrap_mod(x0 + lx - 2, nx);
-        a_int[k] = (idx < NHA && lx >= 2 && lx < TX + 2 && ly >= 2 && ly < TY + 2) ? (ly - 2) * TX + (lx - 2) : -1;
-        ph1[k] = 0.f;
-        ph2[k] = 0.f;
+        if (VEC) {
+            // a_idx: halo-plane index of the quad's row; a_int: halo x of its first
+            // site (-2 for the leftmost quad; sites outside [0, HX) are dropped)
+            const int ry = idx / QX, qx = idx - (idx / QX) * QX;
+            a_idx[k] = idx < NQ ? ry * HX : INT_MIN;
+            a_row[k] = wrap_mod(y0 + ry - 2, ny) * nx + wrap_mod(x0 - 4 + 4 * qx, nx);
+            a_int[k] = 4 * qx - 2;
+        } else {
+            a_idx[k] = idx < NHA ? idx : -1;
+            const int ly = idx / HX, lx = idx - (idx / HX) * HX;
+            a_row[k] = wrap_mod(y0 + ly - 2, ny) * nx + wrap_mod(x0 + lx - 2, nx);
+            a_int[k] = 0;
+        }
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            ph1[k][j] = 0.f;
+            ph2[k][j] = 0.f;
+        }
     }
 
     // phase-C site and its periodic neighbour offsets (32-bit site indices)
@@ -338,11 +360,39 @@ fused_step_kernel(const StepArgs a) {
     // FP32 per-thread partial sums over this thread's <= zc sites; FP64 beyond
     float s_phi_acc = 0.f, s_K = 0.f, s_aa = 0.f, s_mass = 0.f, s_umax2 = 0.f;
 
+    // one site of phase A: z-smoothed planes of zp-1 and the interior phi of zp
+    auto a_site = [&](int zp, bool make_zd, int hidx, float p, float& h1, float& h2) {
+        if (make_zd) {
+            s_Z[(zp - 1) & 1][hidx] = fmaf(4.f, h1, h2 + p);
+            s_D[(zp - 1) & 1][hidx] = p - h2;
+        }
+        const int hy = hidx / HX, hx = hidx - (hidx / HX) * HX;
+        if (hx >= 2 && hx < TX + 2 && hy >= 2 && hy < TY + 2) s_phi[zp & 3][(hy - 2) * TX + (hx - 2)] = p;
+        h2 = h1;
+        h1 = p;
+    };
+
     auto phaseA = [&](int zp, bool make_zd) {
         const int zb = wrap_mod(zp, nz) * plane;
 #pragma unroll
-        for (int k = 0; k < NA; ++k) {
-            if (a_idx[k] >= 0) {
+        for (int k = 0; k < NS; ++k) {
+            if (VEC) {
+                if (a_idx[k] != INT_MIN) {
+                    const int s = zb + a_row[k];
+                    float4 p4 = __ldg(reinterpret_cast<const float4*>(a.gin[0] + s));
+#pragma unroll
+                    for (int q = 1; q < 7; ++q) {
+                        const float4 t = __ldg(reinterpret_cast<const float4*>(a.gin[q] + s));
+                        p4.x += t.x; p4.y += t.y; p4.z += t.z; p4.w += t.w;
+                    }
+                    const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int hx = a_int[k] + j;
+                        if (hx >= 0 && hx < HX) a_site(zp, make_zd, a_idx[k] + hx, pv[j], ph1[k][j], ph2[k][j]);
+                    }
+                }
+            } else if (a_idx[k] >= 0) {
                 const int s = zb + a_row[k];
                 float p;
                 if (MODE == MODE_INIT) {
@@ -352,13 +402,7 @@ fused_step_kernel(const StepArgs a) {
 #pragma unroll
                     for (int q = 1; q < 7; ++q) p += __ldg(a.gin[q] + s);
                 }
-                if (make_zd) {
-                    s_Z[(zp - 1) & 1][a_idx[k]] = fmaf(4.f, ph1[k], ph2[k] + p);
-                    s_D[(zp - 1) & 1][a_idx[k]] = p - ph2[k];
-                }
-                if (a_int[k] >= 0) s_phi[zp & 3][a_int[k]] = p;
-                ph2[k] = ph1[k];
-                ph1[k] = p;
+                a_site(zp, make_zd, a_idx[k], p, ph1[k][0], ph2[k][0]);
             }
         }
     };
@@ -591,7 +635,8 @@ fused_step_kernel(const StepArgs a) {
 }
 
 // Launch one fused kernel instance.  Defined per storage type in lbgb_step_*.cu.
+// vec selects the float4 phase-A loads (requires nx % 4 == 0).
 template <class FT>
-cudaError_t launch_fused(int mode, int parity, int ty, dim3 grid, const StepArgs& a, cudaStream_t st);
+cudaError_t launch_fused(int mode, int parity, int ty, bool vec, dim3 grid, const StepArgs& a, cudaStream_t st);
 
 }  // namespace lbgb

@@ -7,34 +7,36 @@
 namespace lbgb {
 
 template <class FT, int TY>
-static cudaError_t launch_ty(int mode, int parity, dim3 grid, const StepArgs& a, cudaStream_t st) {
+static cudaError_t launch_ty(int mode, int parity, bool vec, dim3 grid, const StepArgs& a, cudaStream_t st) {
     const dim3 block(32 * TY);
-    if (mode == MODE_STEP) {
-        if (parity == 0) fused_step_kernel<FT, TY, MODE_STEP, 0><<<grid, block, 0, st>>>(a);
-        else fused_step_kernel<FT, TY, MODE_STEP, 1><<<grid, block, 0, st>>>(a);
+    if (mode != MODE_STEP) return cudaErrorInvalidValue;
+    if (vec) {
+        if (parity == 0) fused_step_kernel<FT, TY, MODE_STEP, 0, true><<<grid, block, 0, st>>>(a);
+        else fused_step_kernel<FT, TY, MODE_STEP, 1, true><<<grid, block, 0, st>>>(a);
     } else {
-        return cudaErrorInvalidValue;
+        if (parity == 0) fused_step_kernel<FT, TY, MODE_STEP, 0, false><<<grid, block, 0, st>>>(a);
+        else fused_step_kernel<FT, TY, MODE_STEP, 1, false><<<grid, block, 0, st>>>(a);
     }
     return cudaGetLastError();
 }
 
 template <>
-cudaError_t launch_fused<LBGB_FT>(int mode, int parity, int ty, dim3 grid, const StepArgs& a,
+cudaError_t launch_fused<LBGB_FT>(int mode, int parity, int ty, bool vec, dim3 grid, const StepArgs& a,
                                   cudaStream_t st) {
     if (mode == MODE_MOMENTS) {
         if (ty != 8) return cudaErrorInvalidValue;
-        if (parity == 0) fused_step_kernel<LBGB_FT, 8, MODE_MOMENTS, 0><<<grid, 256, 0, st>>>(a);
-        else fused_step_kernel<LBGB_FT, 8, MODE_MOMENTS, 1><<<grid, 256, 0, st>>>(a);
+        if (parity == 0) fused_step_kernel<LBGB_FT, 8, MODE_MOMENTS, 0, false><<<grid, 256, 0, st>>>(a);
+        else fused_step_kernel<LBGB_FT, 8, MODE_MOMENTS, 1, false><<<grid, 256, 0, st>>>(a);
         return cudaGetLastError();
     }
     if (mode == MODE_INIT) {
         if (ty != 8) return cudaErrorInvalidValue;
-        fused_step_kernel<LBGB_FT, 8, MODE_INIT, 0><<<grid, 256, 0, st>>>(a);
+        fused_step_kernel<LBGB_FT, 8, MODE_INIT, 0, false><<<grid, 256, 0, st>>>(a);
         return cudaGetLastError();
     }
     switch (ty) {
-        case 4: return launch_ty<LBGB_FT, 4>(mode, parity, grid, a, st);
-        case 8: return launch_ty<LBGB_FT, 8>(mode, parity, grid, a, st);
+        case 4: return launch_ty<LBGB_FT, 4>(mode, parity, vec, grid, a, st);
+        case 8: return launch_ty<LBGB_FT, 8>(mode, parity, vec, grid, a, st);
         default: return cudaErrorInvalidValue;
     }
 }

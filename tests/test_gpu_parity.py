@@ -141,10 +141,12 @@ def test_hit_64_two_bubbles(lbgb, orc):
 
 
 @pytest.mark.parametrize("tile", [(4, 8), (8, 16), (8, 64), (8, 5), (4, 1)])
-def test_tile_shapes_give_identical_fields(lbgb, tile):
+@pytest.mark.parametrize("nx", [45, 44])
+def test_tile_shapes_give_identical_fields(lbgb, tile, nx):
     """Every launch shape computes each site with the same arithmetic, so the
-    fields are bitwise identical across tile shapes (no forcing controller)."""
-    shape = (21, 19, 45)
+    fields are bitwise identical across tile shapes (no forcing controller);
+    nx = 44 takes the float4 phase-A path, nx = 45 the per-site one."""
+    shape = (21, 19, nx)
     phi, u = smooth_fields(shape, 4)
     nz, ny, nx = shape
     ref = lbgb.Box(nx, ny, nz, 0.8, 0.1, 3.0, 0.01)
