@@ -214,7 +214,7 @@ def main():
         box.set_tile(*args.tile)
     elif not args.no_tune:
         os.environ.setdefault("LBGB_TUNE_CACHE", os.path.join(ROOT, "paper_2505_01126_gb300", "tune_cache.txt"))
-        box.tune(3)
+        box.tune(8)
     ty, zc = box.tile()
     phi_d = torch.from_numpy(w.phi).cuda()
     u_d = torch.from_numpy(w.u).cuda()
