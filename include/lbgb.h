@@ -170,6 +170,34 @@ long long lb_launch_count(const lb_ctx* ctx);
 int lb_set_timing(lb_ctx* ctx, int on);
 int lb_kernel_time(lb_ctx* ctx, double* ms, long long* launches);
 
+/*
+ * lb_field_stats_static -- FP64 statistics of caller fields without any device
+ * allocation.  The paper has no counterpart; this call exists for callers that
+ * must not call cudaMalloc: a framework whose caching allocator owns the device
+ * memory budget, a latency-critical path where an allocation may synchronise
+ * the device, or a plugin that is handed its buffers.
+ *   phi    N floats, device memory, read only
+ *   u      3N floats (ux | uy | uz planes), device memory, read only
+ *   stream cudaStream_t for the work, or NULL for the legacy default stream
+ *   out    5 doubles: {Phi = sum phi, K = 1/2 sum |u|^2, 0, max|u|, 0}, the
+ *          numbers lb_diagnostics reports right after lb_init with these
+ *          fields.  Host memory: the call waits for the result.  Device
+ *          memory: the result is written in stream order and the call
+ *          returns at once.
+ * Scratch is a file-scope __device__ array of LB_STATIC_MAX_BLOCKS * 5 doubles
+ * (1.25 MiB), which every device that loads the library holds until the process
+ * exits.  A box needs ceil(nx/32)*ceil(ny/8)*ceil(nz/32) records; larger boxes
+ * (beyond 640^3 for a cube) are rejected with LB_EINVAL.  The first call on a
+ * device looks up the array's device address, so make that first call before
+ * any stream capture.  All calls on a device share the array: calls that
+ * overlap on the GPU (e.g. on two streams) race.
+ * Errors: LB_EINVAL (NULL, sizes, host phi/u), LB_ECUDA, LB_ENONFINITE (a NaN or
+ * Inf in phi or u; host out only, out still filled).
+ */
+#define LB_STATIC_MAX_BLOCKS 32768
+int lb_field_stats_static(const float* phi, const float* u, int nx, int ny, int nz, void* stream,
+                          double out[5]);
+
 #ifdef __cplusplus
 }
 #endif

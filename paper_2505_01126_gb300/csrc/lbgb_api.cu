@@ -273,6 +273,10 @@ long long max_blocks(const lb_ctx* c) {
 
 }  // namespace
 
+namespace lbgb {
+void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+}  // namespace lbgb
+
 extern "C" {
 
 const char* lb_last_error(void) { return g_err; }

@@ -635,6 +635,9 @@ fused_step_kernel(const StepArgs a) {
 }
 
 // Launch one fused kernel instance.  Defined per storage type in lbgb_step_*.cu.
+// Records a message for lb_last_error() (defined with the C ABI).
+void set_last_error(const char* msg);
+
 // vec selects the float4 phase-A loads (requires nx % 4 == 0).
 template <class FT>
 cudaError_t launch_fused(int mode, int parity, int ty, bool vec, dim3 grid, const StepArgs& a, cudaStream_t st);

@@ -37,7 +37,8 @@ class lb_force(ctypes.Structure):
 
 EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_step", "lb_moments", "lb_diagnostics",
            "lb_sync", "lb_time", "lb_set_tile", "lb_get_tile", "lb_tune", "lb_bytes_per_site",
-           "lb_destroy", "lb_last_error", "lb_launch_count", "lb_set_timing", "lb_kernel_time"]
+           "lb_destroy", "lb_last_error", "lb_launch_count", "lb_set_timing", "lb_kernel_time",
+           "lb_field_stats_static"]
 
 
 def _load():
@@ -70,6 +71,7 @@ def _load():
     lib.lb_launch_count.restype = ctypes.c_longlong
     lib.lb_set_timing.argtypes = [vp, i]
     lib.lb_kernel_time.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
+    lib.lb_field_stats_static.argtypes = [vp, vp, i, i, i, vp, ctypes.POINTER(d)]
     return lib
 
 
@@ -108,6 +110,19 @@ def _ptr(a, n_expected: int, writable: bool = False):
     if a.numel() != n_expected:
         raise ValueError(f"expected {n_expected} floats, got {a.numel()}")
     return ctypes.c_void_p(a.data_ptr()), a
+
+
+def field_stats_static(phi, u, stream=None) -> np.ndarray:
+    """FP64 {Phi, K, 0, max|u|, 0} of device fields phi (nz, ny, nx) and u (3, nz, ny, nx)
+    through lb_field_stats_static, which allocates no device memory (for callers
+    that must not call cudaMalloc); the result is returned in host memory."""
+    nz, ny, nx = (int(v) for v in phi.shape)
+    p, _a = _ptr(phi, nx * ny * nz)
+    q, _b = _ptr(u, 3 * nx * ny * nz)
+    handle = getattr(stream, "cuda_stream", stream)
+    out = (ctypes.c_double * 5)()
+    _check(_lib.lb_field_stats_static(p, q, nx, ny, nz, ctypes.c_void_p(int(handle) if handle else 0), out))
+    return np.array(list(out))
 
 
 @dataclass
