@@ -55,6 +55,25 @@ def dist_env():
         os.environ.get("LOCAL_RANK", "0"))
 
 
+def measured_traffic(storage: str, n_sites: int):
+    """DRAM bytes per fused-kernel launch from the committed ncu record, scaled to
+    n_sites, or None if the kernel sources changed since the capture."""
+    try:
+        import hashlib
+
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for src in rec["kernel_sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != rec["kernel_sources_sha256"] or storage not in rec["captures"]:
+            return None
+        return rec["captures"][storage]["bytes_per_site"] * n_sites
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -280,7 +299,7 @@ def main():
         kern_avg_s = kern_ms / max(kern_n, 1) * 1e-3
         achieved = bps * N / kern_avg_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "fused_step_kernel", "bytes_per_site": bps,
+                "traffic": measured_traffic(args.storage, N), "kernel": "fused_step_kernel", "bytes_per_site": bps,
                 "kernel_ms_avg": kern_avg_s * 1e3, "peak_source": peak_kind}
         cpu = None
         if not args.no_cpu_baseline and world == 1:
