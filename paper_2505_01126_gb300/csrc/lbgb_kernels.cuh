@@ -109,6 +109,17 @@ __device__ __forceinline__ int wrap_mod(int v, int n) {
     return r < 0 ? r + n : r;
 }
 
+// 16-byte asynchronous global -> shared copy (L2 only), its group commit and wait.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 __host__ __device__ constexpr int IDX(int cx, int cy, int cz) { return (cx + 1) + 3 * (cy + 1) + 9 * (cz + 1); }
 
 // ------------------------------------------------------- block reduction
@@ -301,6 +312,9 @@ fused_step_kernel(const StepArgs a) {
     __shared__ float s_n[4][3][NHB];     // unit normal, 4-plane ring
     __shared__ float s_k[3][NHB];        // 6 Sz n_x, 6 Sz n_y, 2 Dz n_z of one plane
     __shared__ float s_grad[2][4][NT];   // grad phi and |grad phi| of the interior
+    // VEC: phase-A quads of the D3Q7 planes staged by cp.async one plane ahead (2-plane ring)
+    constexpr int NQS = VEC ? (TX / 4 + 2) * HY : 1;  // quad index tid + k*NT < NQS
+    __shared__ __align__(16) float4 s_gA[VEC ? 2 : 1][VEC ? 7 : 1][NQS];
 
     using C = Codec<FT>;
     const int tid = threadIdx.x;
@@ -372,17 +386,35 @@ fused_step_kernel(const StepArgs a) {
         h1 = p;
     };
 
+    // VEC: start the asynchronous copies of plane zp's quads into ring slot zp & 1.
+    // Every thread commits one group per call (possibly empty) so that the
+    // group counts agree across the block.
+    auto a_issue = [&](int zp) {
+        if (VEC) {
+            const int zb = wrap_mod(zp, nz) * plane;
+#pragma unroll
+            for (int k = 0; k < NS; ++k)
+                if (a_idx[k] != INT_MIN) {
+#pragma unroll
+                    for (int q = 0; q < 7; ++q)
+                        cp_async16(&s_gA[zp & 1][q][tid + k * NT], a.gin[q] + zb + a_row[k]);
+                }
+            cp_async_commit();
+        }
+    };
+
+    // phi of plane zp (VEC: from the staged quads of slot zp & 1, which this
+    // thread copied itself and has waited for)
     auto phaseA = [&](int zp, bool make_zd) {
         const int zb = wrap_mod(zp, nz) * plane;
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
             if (VEC) {
                 if (a_idx[k] != INT_MIN) {
-                    const int s = zb + a_row[k];
-                    float4 p4 = __ldg(reinterpret_cast<const float4*>(a.gin[0] + s));
+                    float4 p4 = s_gA[zp & 1][0][tid + k * NT];
 #pragma unroll
                     for (int q = 1; q < 7; ++q) {
-                        const float4 t = __ldg(reinterpret_cast<const float4*>(a.gin[q] + s));
+                        const float4 t = s_gA[zp & 1][q][tid + k * NT];
                         p4.x += t.x; p4.y += t.y; p4.z += t.z; p4.w += t.w;
                     }
                     const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
@@ -454,14 +486,24 @@ fused_step_kernel(const StepArgs a) {
     };
 
     // prologue: phi history from z0-2, gradient planes and n at z0-1, z0
+    // (VEC: each plane's copies are waited for at once; plane z0+2 is left in flight)
+    a_issue(z0 - 2);
+    cp_async_wait<0>();
     phaseA(z0 - 2, false);
+    a_issue(z0 - 1);
+    cp_async_wait<0>();
     phaseA(z0 - 1, false);
+    a_issue(z0);
+    cp_async_wait<0>();
     phaseA(z0, true);
     __syncthreads();
     phaseB(z0 - 1, false);
+    a_issue(z0 + 1);
+    cp_async_wait<0>();
     phaseA(z0 + 1, true);
     __syncthreads();
     phaseB(z0, false);
+    a_issue(z0 + 2);
 
     for (int z = z0; z < z1; ++z) {
         const int DZ0 = z == 0 ? (nz - 1) * plane : -plane;
@@ -495,6 +537,8 @@ fused_step_kernel(const StepArgs a) {
             }
         }
 
+        a_issue(z + 3);       // next plane's phase-A copies
+        cp_async_wait<1>();   // this thread's copies of plane z+2 have landed
         phaseA(z + 2, true);
         __syncthreads();
         phaseB(z + 1, true);
