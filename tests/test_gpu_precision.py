@@ -1,0 +1,116 @@
+"""Error of the FP32 and 16-bit (FP16/BF16 shifted) population storage against
+the FP64 oracle, on the quantities the method is judged by: the Laplace
+pressure jump of a static droplet, the kinetic energy of bubbly forced HIT,
+and the drift of the phase mass sum(phi).
+
+The arithmetic is FP32 for every storage, and the reductions are FP64.  The
+measured errors are written to precision_report.json (in the directory named
+by LBGB_REPORT_DIR, default: the current directory) and bounded below.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2505_01126_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+REPORT = {}
+
+
+@pytest.fixture(scope="module")
+def lbgb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_01126_gb300 import build
+
+    build.build()
+    from paper_2505_01126_gb300 import lbgb as mod
+
+    yield mod
+    out = os.environ.get("LBGB_REPORT_DIR", ".")
+    with open(os.path.join(out, "precision_report.json"), "w") as f:
+        json.dump(REPORT, f, indent=1, sort_keys=True)
+
+
+def laplace_dp(rho, edge, R, W):
+    c = (edge - 1) / 2
+    z, y, x = np.meshgrid(*[np.arange(edge)] * 3, indexing="ij")
+    d = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
+    return (rho[d < R - 2 * W].mean() - rho[d > R + 2 * W].mean()) / 3
+
+
+def test_laplace_jump_by_storage(lbgb, orc):
+    """32^3 droplet R = 8, sigma = 0.01: dp averaged over steps 200-400, each storage
+    against the FP64 oracle."""
+    edge, R = 32, 8.0
+    w = inputs.static_droplet(edge=edge, R=R)
+    sample_steps = list(range(220, 401, 20))
+
+    def run(step, moments):
+        dps = []
+        done = 0
+        for t in sample_steps:
+            step(t - done)
+            done = t
+            dps.append(laplace_dp(moments(), edge, R, w.W))
+        return float(np.mean(dps))
+
+    o = orc.Oracle(edge, edge, edge, w.tau, w.M, w.W, w.sigma)
+    o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
+    ref = run(o.step, lambda: o.moments()[0])
+    REPORT["laplace_dp_oracle"] = ref
+    REPORT["laplace_dp_theory"] = 2 * w.sigma / R
+    # measured on GB300: 1.2e-7 (f32), 9.3e-6 (f16), 2.5e-4 (bf16)
+    bounds = {"f32": 2e-6, "f16": 1e-4, "bf16": 3e-3}
+    for st, bound in bounds.items():
+        b = lbgb.Box(edge, edge, edge, w.tau, w.M, w.W, w.sigma, storage=st)
+        b.init(w.phi, w.u)
+        dp = run(b.step, lambda: b.moments_numpy()[0].astype(np.float64))
+        rel = abs(dp / ref - 1)
+        REPORT[f"laplace_dp_{st}"] = dp
+        REPORT[f"laplace_dp_relerr_{st}"] = rel
+        assert rel < bound, (st, rel)
+
+
+def test_hit_energy_and_phase_mass_by_storage(lbgb, orc):
+    """64^3 surrogate of the 512^3 bubbly HIT workload: same generator (seed 3, modes
+    1 <= |k| <= 4, u_rms 0.02, tau 0.51, W = 3, sigma = 0.01, linear forcing) with one
+    bubble of R = 12; 500 steps.  Kinetic energy against the oracle, phase mass
+    sum(phi) against its initial value."""
+    n, steps = 64, 500
+    w = inputs.bubbly_hit(n, 1, 12.0, seed=3)
+    o = orc.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma, force_kind=3, T_relax=w.T_relax)
+    o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
+    Phi0 = float(w.phi.astype(np.float64).sum())
+    K_o, Phi_o = [], []
+    for _ in range(steps // 50):
+        o.step(50)
+        _, u, phi = o.moments()
+        K_o.append(0.5 * float((u * u).sum()))
+        Phi_o.append(float(phi.sum()))
+    REPORT["hit64_K_oracle"] = K_o[-1]
+    REPORT["hit64_phase_mass_drift_oracle"] = abs(Phi_o[-1] / Phi0 - 1)
+    # measured on GB300: K 2.1e-6 / 7.1e-6 / 5.4e-4 and mass drift ~3e-8 (g is FP32 in all)
+    bounds = {"f32": (2e-5, 1e-6), "f16": (1e-4, 1e-6), "bf16": (5e-3, 1e-6)}
+    for st, (kb, mb) in bounds.items():
+        b = lbgb.Box(n, n, n, w.tau, w.M, w.W, w.sigma, force=lbgb.Force(kind=3, T_relax=w.T_relax), storage=st)
+        b.init(w.phi, w.u)
+        kerr, Phi = 0.0, None
+        for j in range(steps // 50):
+            b.step(50)
+            _, u, phi = b.moments_numpy()
+            u = u.astype(np.float64)
+            K = 0.5 * float((u * u).sum())
+            kerr = max(kerr, abs(K / K_o[j] - 1))
+            Phi = float(phi.astype(np.float64).sum())
+        drift = abs(Phi / Phi0 - 1)
+        REPORT[f"hit64_K_maxrelerr_{st}"] = kerr
+        REPORT[f"hit64_phase_mass_drift_{st}"] = drift
+        assert kerr < kb, (st, kerr)
+        assert drift < mb, (st, drift)
