@@ -170,6 +170,42 @@ long long lb_launch_count(const lb_ctx* ctx);
 int lb_set_timing(lb_ctx* ctx, int on);
 int lb_kernel_time(lb_ctx* ctx, double* ms, long long* launches);
 
+/* --------------------------------------------------------- batched ensemble
+ * Many independent periodic boxes of uneven sizes advanced together: each step
+ * is ONE persistent kernel launch over a work list of (box, tile, z-chunk)
+ * items of all boxes, plus one per-box FP64 reduction launch; runs of two or
+ * more steps replay a captured CUDA graph.  Every box is computed by the same
+ * per-tile code as a single box (lb_step), so its fields are bitwise those of
+ * lb_step with the same tile shape.  No external force (LB_FORCE_NONE).
+ */
+typedef struct lb_batch lb_batch;
+
+/* count boxes; dims = count triples (nx, ny, nz); tau, M, W, sigma = count
+ * values each, with the meaning and limits of lb_create.  The batch owns one
+ * population array for all boxes (same storage), two D3Q7 arrays and the
+ * reduction scratch.  Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA. */
+int lb_batch_create(int count, const int* dims, const double* tau, const double* M, const double* W,
+                    const double* sigma, int storage, lb_batch** out);
+int lb_batch_set_stream(lb_batch* batch, void* stream);
+/* State of box `box` at t = 0 from phi (N_box floats) and u (3 N_box floats),
+ * host or device; as lb_init.  LB_ESTATE once the batch has stepped. */
+int lb_batch_init(lb_batch* batch, int box, const float* phi, const float* u);
+/* Advance every box n >= 0 steps; LB_ESTATE until every box is initialised. */
+int lb_batch_step(lb_batch* batch, int n);
+/* Fields of one box at the current time, as lb_moments. */
+int lb_batch_moments(lb_batch* batch, int box, float* rho, float* u, float* phi);
+/* FP64 reductions of one box's last step: {Phi, K, eps, max|u|, 0}; syncs. */
+int lb_batch_diagnostics(lb_batch* batch, int box, double out[5]);
+/* Tile height ty in {4, 8} and z-chunk zc >= 1 of the work items. */
+int lb_batch_set_tile(lb_batch* batch, int ty, int zc);
+int lb_batch_get_tile(const lb_batch* batch, int* ty, int* zc);
+/* Time every tile shape on the batch's own arrays (zeroed) and keep the
+ * fastest; call before lb_batch_init (LB_ESTATE otherwise). */
+int lb_batch_tune(lb_batch* batch, int steps);
+long long lb_batch_sites(const lb_batch* batch);  /* sum of the boxes' sites */
+long long lb_batch_time(const lb_batch* batch);   /* steps taken */
+void lb_batch_destroy(lb_batch* batch);            /* NULL is ignored */
+
 /*
  * lb_field_stats_static -- FP64 statistics of caller fields without any device
  * allocation.  The paper has no counterpart; this call exists for callers that

@@ -296,9 +296,8 @@ __host__ __device__ __forceinline__ void collide_site(float pp, float m0, float 
 // Phase A reads the D3Q7 planes either per site (VEC = false) or, when nx is a
 // multiple of 4, as float4 quads of 4 consecutive sites covering the halo row
 // x0-4 .. x0+TX+3 (VEC = true): 7 vector loads per 4 sites.
-template <class FT, int TY, int MODE, int PAR, bool VEC>
-__global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 512 / (32 * TY)))
-fused_step_kernel(const StepArgs a) {
+template <class FT, int TY, int MODE, int PAR, bool VEC, class Args>
+__device__ __forceinline__ void fused_tile(const Args& a, int bx, int by, int bz, long long pblock) {
     constexpr int TX = 32;
     constexpr int NT = TX * TY;
     constexpr int HX = TX + 4, HY = TY + 4, NHA = HX * HY;  // halo-2 plane (phi)
@@ -321,8 +320,8 @@ fused_step_kernel(const StepArgs a) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int N = a.N;
     const int plane = nx * ny;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * a.zc;
+    const int x0 = bx * TX, y0 = by * TY;
+    const int z0 = bz * a.zc;
     const int z1 = min(z0 + a.zc, nz);
 
     // phase-A slots (halo-2 plane), fixed for the whole march.  A slot is one
@@ -671,16 +670,99 @@ fused_step_kernel(const StepArgs a) {
         double v0 = s_phi_acc, v1 = s_K, v2 = s_aa, v3 = s_mass, v4 = s_umax2;
         block_reduce5<NT>(v0, v1, v2, v3, v4);
         if (tid == 0) {
-            const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-            double* out = a.partials + b * NPART;
+            double* out = a.partials + pblock * NPART;
             out[0] = v0; out[1] = v1; out[2] = v2; out[3] = v3; out[4] = v4;
         }
+    }
+}
+
+// One box: a block per (32 x TY tile, z-chunk).
+template <class FT, int TY, int MODE, int PAR, bool VEC>
+__global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 512 / (32 * TY)))
+fused_step_kernel(const __grid_constant__ StepArgs a) {
+    const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    fused_tile<FT, TY, MODE, PAR, VEC>(a, blockIdx.x, blockIdx.y, blockIdx.z, b);
+}
+
+// ------------------------------------------------------ batched ensemble
+// Many independent periodic boxes in one array set: box b's f planes start at
+// element f_off and are N_b apart; its g planes likewise at g_off in each of
+// the two g buffers.  The work list enumerates (box, tile, z-chunk) items.
+struct BoxDesc {
+    int nx, ny, nz, N;
+    long long f_off, g_off;                 // element offsets into the batch arrays
+    float omega, omega_phi, sharp, beta;
+    int item0, tiles_x, tiles_y, tiles_z;   // this box's slice of the work list
+};
+
+struct BatchArgs {
+    int nitems, zc;
+    const BoxDesc* boxes;
+    const int* item_box;   // box of each work item
+    void* f;               // all boxes' populations (storage type)
+    const float* g_in;
+    float* g_out;
+    double* partials;      // NPART per work item
+};
+
+// Plane q of a plane set stored q * stride elements apart.
+template <class T>
+struct PlaneSet {
+    T* base;
+    long long stride;
+    __device__ __forceinline__ T* operator[](int q) const { return base + q * stride; }
+};
+
+// The argument view of one box for fused_tile (steps only, no external force).
+template <class FT>
+struct BoxTileArgs {
+    int nx, ny, nz, zc, N;
+    PlaneSet<FT> fk;
+    PlaneSet<const float> gin;
+    PlaneSet<float> gout;
+    int force_kind;
+    float omega, omega_phi, sharp, beta, gc0, gc1, gc2, A_abc;
+    const float* abc;
+    const DevState* st;
+    double* partials;
+    float *out_rho, *out_u, *out_phi;
+    const float *in_phi, *in_u;
+};
+
+// Persistent kernel: the grid strides over the work list of all boxes.
+template <class FT, int TY, int PAR, bool VEC>
+__global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 512 / (32 * TY)))
+batch_step_kernel(const __grid_constant__ BatchArgs b) {
+    for (int item = blockIdx.x; item < b.nitems; item += gridDim.x) {
+        const BoxDesc d = b.boxes[b.item_box[item]];
+        BoxTileArgs<FT> t;
+        t.nx = d.nx; t.ny = d.ny; t.nz = d.nz; t.zc = b.zc; t.N = d.N;
+        t.fk = PlaneSet<FT>{static_cast<FT*>(b.f) + d.f_off, (long long)d.N};
+        t.gin = PlaneSet<const float>{b.g_in + d.g_off, (long long)d.N};
+        t.gout = PlaneSet<float>{b.g_out + d.g_off, (long long)d.N};
+        t.force_kind = FK_NONE;
+        t.omega = d.omega; t.omega_phi = d.omega_phi; t.sharp = d.sharp; t.beta = d.beta;
+        t.gc0 = t.gc1 = t.gc2 = t.A_abc = 0.f;
+        t.abc = nullptr; t.st = nullptr; t.partials = b.partials;
+        t.out_rho = t.out_u = t.out_phi = nullptr;
+        t.in_phi = t.in_u = nullptr;
+        const int local = item - d.item0;
+        const int tx = local % d.tiles_x, rest = local / d.tiles_x;
+        fused_tile<FT, TY, MODE_STEP, PAR, VEC>(t, tx, rest % d.tiles_y, rest / d.tiles_y, item);
+        __syncthreads();  // the shared rings are reused by the block's next item
     }
 }
 
 // Launch one fused kernel instance.  Defined per storage type in lbgb_step_*.cu.
 // Records a message for lb_last_error() (defined with the C ABI).
 void set_last_error(const char* msg);
+
+// One step of every box of a batch (persistent grid of `blocks` blocks).
+template <class FT>
+cudaError_t launch_batch(int parity, int ty, bool vec, int blocks, const BatchArgs& b, cudaStream_t st);
+// Resident blocks per SM of the batch kernel for this shape (0 on error).
+template <class FT>
+int batch_blocks_per_sm(int ty, bool vec);
 
 // vec selects the float4 phase-A loads (requires nx % 4 == 0).
 template <class FT>

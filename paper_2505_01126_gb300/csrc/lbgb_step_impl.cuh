@@ -41,4 +41,37 @@ cudaError_t launch_fused<LBGB_FT>(int mode, int parity, int ty, bool vec, dim3 g
     }
 }
 
+template <class FT, int TY, bool VEC>
+static cudaError_t launch_batch_ty(int parity, int blocks, const BatchArgs& b, cudaStream_t st) {
+    if (parity == 0) batch_step_kernel<FT, TY, 0, VEC><<<blocks, 32 * TY, 0, st>>>(b);
+    else batch_step_kernel<FT, TY, 1, VEC><<<blocks, 32 * TY, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_batch<LBGB_FT>(int parity, int ty, bool vec, int blocks, const BatchArgs& b, cudaStream_t st) {
+    if (ty == 4) return vec ? launch_batch_ty<LBGB_FT, 4, true>(parity, blocks, b, st)
+                            : launch_batch_ty<LBGB_FT, 4, false>(parity, blocks, b, st);
+    if (ty == 8) return vec ? launch_batch_ty<LBGB_FT, 8, true>(parity, blocks, b, st)
+                            : launch_batch_ty<LBGB_FT, 8, false>(parity, blocks, b, st);
+    return cudaErrorInvalidValue;
+}
+
+template <>
+int batch_blocks_per_sm<LBGB_FT>(int ty, bool vec) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (ty == 4)
+        e = vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LBGB_FT, 4, 0, true>, 128, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LBGB_FT, 4, 0, false>, 128, 0);
+    else if (ty == 8)
+        e = vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LBGB_FT, 8, 0, true>, 256, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LBGB_FT, 8, 0, false>, 256, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
 }  // namespace lbgb

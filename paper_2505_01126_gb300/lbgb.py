@@ -38,7 +38,9 @@ class lb_force(ctypes.Structure):
 EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_step", "lb_moments", "lb_diagnostics",
            "lb_sync", "lb_time", "lb_set_tile", "lb_get_tile", "lb_tune", "lb_bytes_per_site",
            "lb_destroy", "lb_last_error", "lb_launch_count", "lb_set_timing", "lb_kernel_time",
-           "lb_field_stats_static"]
+           "lb_field_stats_static", "lb_batch_create", "lb_batch_set_stream", "lb_batch_init",
+           "lb_batch_step", "lb_batch_moments", "lb_batch_diagnostics", "lb_batch_set_tile", "lb_batch_get_tile",
+           "lb_batch_tune", "lb_batch_sites", "lb_batch_time", "lb_batch_destroy"]
 
 
 def _load():
@@ -72,6 +74,22 @@ def _load():
     lib.lb_set_timing.argtypes = [vp, i]
     lib.lb_kernel_time.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
     lib.lb_field_stats_static.argtypes = [vp, vp, i, i, i, vp, ctypes.POINTER(d)]
+    dp_ = ctypes.POINTER(d)
+    lib.lb_batch_create.argtypes = [i, ctypes.POINTER(i), dp_, dp_, dp_, dp_, i, ctypes.POINTER(vp)]
+    lib.lb_batch_set_stream.argtypes = [vp, vp]
+    lib.lb_batch_init.argtypes = [vp, i, vp, vp]
+    lib.lb_batch_step.argtypes = [vp, i]
+    lib.lb_batch_moments.argtypes = [vp, i, vp, vp, vp]
+    lib.lb_batch_diagnostics.argtypes = [vp, i, dp_]
+    lib.lb_batch_set_tile.argtypes = [vp, i, i]
+    lib.lb_batch_get_tile.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.lb_batch_tune.argtypes = [vp, i]
+    lib.lb_batch_sites.argtypes = [vp]
+    lib.lb_batch_sites.restype = ctypes.c_longlong
+    lib.lb_batch_time.argtypes = [vp]
+    lib.lb_batch_time.restype = ctypes.c_longlong
+    lib.lb_batch_destroy.argtypes = [vp]
+    lib.lb_batch_destroy.restype = None
     return lib
 
 
@@ -247,3 +265,83 @@ class Box:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Independent periodic boxes advanced together by one persistent launch per
+    step (lb_batch_*).  dims: list of (nx, ny, nz); tau, M, W, sigma: per box."""
+
+    def __init__(self, dims, tau, M, W, sigma, storage="f32", stream=None):
+        self._h = None
+        self.dims = [tuple(int(v) for v in d) for d in dims]
+        n = len(self.dims)
+        flat = (ctypes.c_int * (3 * n))(*[v for d in self.dims for v in d])
+
+        def arr(x):
+            x = list(x) if hasattr(x, "__len__") else [x] * n
+            return (ctypes.c_double * n)(*[float(v) for v in x])
+
+        st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        h = ctypes.c_void_p()
+        _check(_lib.lb_batch_create(n, flat, arr(tau), arr(M), arr(W), arr(sigma), st, ctypes.byref(h)))
+        self._h = h
+        if stream is not None:
+            handle = getattr(stream, "cuda_stream", stream)
+            _check(_lib.lb_batch_set_stream(self._h, ctypes.c_void_p(int(handle) if handle else 0)))
+
+    def _N(self, box):
+        nx, ny, nz = self.dims[box]
+        return nx * ny * nz
+
+    def init(self, box, phi, u):
+        p, _a = _ptr(phi, self._N(box))
+        q, _b = _ptr(u, 3 * self._N(box))
+        _check(_lib.lb_batch_init(self._h, int(box), p, q))
+
+    def step(self, n=1):
+        _check(_lib.lb_batch_step(self._h, int(n)))
+
+    def moments_numpy(self, box):
+        nx, ny, nz = self.dims[box]
+        rho = np.zeros((nz, ny, nx), np.float32)
+        u = np.zeros((3, nz, ny, nx), np.float32)
+        phi = np.zeros((nz, ny, nx), np.float32)
+        _check(_lib.lb_batch_moments(self._h, int(box), ctypes.c_void_p(rho.ctypes.data),
+                                     ctypes.c_void_p(u.ctypes.data), ctypes.c_void_p(phi.ctypes.data)))
+        return rho, u, phi
+
+    def diagnostics(self, box) -> np.ndarray:
+        out = (ctypes.c_double * 5)()
+        _check(_lib.lb_batch_diagnostics(self._h, int(box), out))
+        return np.array(list(out))
+
+    def set_tile(self, ty, zc):
+        _check(_lib.lb_batch_set_tile(self._h, int(ty), int(zc)))
+
+    def tile(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.lb_batch_get_tile(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def tune(self, steps=3):
+        _check(_lib.lb_batch_tune(self._h, int(steps)))
+        return self.tile()
+
+    @property
+    def sites(self) -> int:
+        return int(_lib.lb_batch_sites(self._h))
+
+    @property
+    def time(self) -> int:
+        return int(_lib.lb_batch_time(self._h))
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.lb_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,124 @@
+"""Batched ensemble: many independent periodic boxes of uneven sizes advanced
+by one persistent launch per step.
+
+Every box is computed by the same per-tile code as a single box, so after any
+number of steps its fields (and FP64 reductions) must equal, bit for bit,
+those of the single-box path with the same tile shape.  Together with the
+single-box parity tests against the FP64 oracle, this carries the oracle
+parity over to every box of a batch.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2505_01126_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbgb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_01126_gb300 import build
+
+    build.build()
+    from paper_2505_01126_gb300 import lbgb as mod
+
+    return mod
+
+
+def box_fields(nx, ny, nz, seed):
+    rng = np.random.default_rng(seed)
+    R = 0.25 * min(nx, ny, nz) * (1 + rng.uniform(-0.2, 0.2))
+    c = (rng.uniform(0, nx), rng.uniform(0, ny), rng.uniform(0, nz))
+    phi = inputs.droplet(nx, ny, nz, R, 3.0, center=c)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    u = np.stack([0.01 * np.sin(2 * np.pi * (y / ny + rng.uniform())),
+                  0.01 * np.cos(2 * np.pi * (z / nz + rng.uniform())),
+                  0.01 * np.sin(2 * np.pi * (x / nx + rng.uniform()))])
+    return inputs.to_f32(phi), inputs.to_f32(u)
+
+
+@pytest.mark.parametrize("dims", [
+    [(32, 32, 32), (24, 24, 24), (48, 40, 36), (64, 16, 20), (8, 8, 8)],    # every nx % 4 == 0: float4 phase A
+    [(32, 32, 32), (37, 13, 11), (24, 24, 24)],                              # a ragged nx: per-site phase A
+])
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_batch_boxes_equal_single_boxes(lbgb, dims, storage):
+    tau = [0.8, 1.0, 0.6, 0.9, 0.7][: len(dims)]
+    sigma = [0.01, 0.005, 0.02, 0.015, 0.01][: len(dims)]
+    fields = [box_fields(*d, seed=k) for k, d in enumerate(dims)]
+    batch = lbgb.Batch(dims, tau, 0.1, 3.0, sigma, storage=storage)
+    batch.set_tile(4, 16)
+    for k, (phi, u) in enumerate(fields):
+        batch.init(k, phi, u)
+    batch.step(7)  # three graph pairs and one single step
+    assert batch.time == 7
+    for k, (d, (phi, u)) in enumerate(zip(dims, fields)):
+        box = lbgb.Box(*d, tau[k], 0.1, 3.0, sigma[k], storage=storage)
+        box.set_tile(4, 16)
+        box.init(phi, u)
+        box.step(7)
+        for a, b in zip(box.moments_numpy(), batch.moments_numpy(k)):
+            assert np.array_equal(a, b), (k, d)
+        np.testing.assert_array_equal(box.diagnostics()[:4], batch.diagnostics(k)[:4])
+        box.close()
+    batch.close()
+
+
+def test_batch_call_order(lbgb):
+    batch = lbgb.Batch([(16, 16, 16), (24, 8, 8)], 0.8, 0.1, 3.0, 0.01)
+    phi, u = box_fields(16, 16, 16, 1)
+    batch.init(0, phi, u)
+    with pytest.raises(lbgb.LBError) as e:
+        batch.step(1)
+    assert e.value.code == lbgb.LB_ESTATE
+    phi2, u2 = box_fields(24, 8, 8, 2)
+    batch.init(1, phi2, u2)
+    batch.step(1)
+    with pytest.raises(lbgb.LBError) as e:
+        batch.init(0, phi, u)
+    assert e.value.code == lbgb.LB_ESTATE
+    with pytest.raises(lbgb.LBError) as e:
+        batch.tune(2)
+    assert e.value.code == lbgb.LB_ESTATE
+
+
+def test_batch_tune_then_run(lbgb):
+    dims = [(24, 24, 24), (32, 32, 32), (48, 48, 48)]
+    batch = lbgb.Batch(dims, 1.0, 0.1, 3.0, 0.01)
+    ty, zc = batch.tune(2)
+    assert ty in (4, 8) and zc >= 1
+    for k, d in enumerate(dims):
+        batch.init(k, *box_fields(*d, seed=10 + k))
+    batch.step(4)
+    for k in range(len(dims)):
+        rho, u, phi = batch.moments_numpy(k)
+        assert np.isfinite(rho).all() and abs(rho.mean() - 1) < 1e-5
+
+
+def test_ensemble_laplace_per_box(lbgb):
+    """A small droplet ensemble drawn like the 512-box workload (edges 24-48, radius
+    0.25 edge +-20%, sigma in [0.005, 0.02], tau = 1, M = 0.1, W = 3), 300 steps:
+    every box holds a Laplace jump within 20% of 2 sigma / R (within 12% once R >= 8)."""
+    specs = inputs.ensemble_specs(8, seed=4, edges=(24, 32, 48))
+    dims = [(s["edge"],) * 3 for s in specs]
+    batch = lbgb.Batch(dims, [s["tau"] for s in specs], [s["M"] for s in specs], [s["W"] for s in specs],
+                       [s["sigma"] for s in specs])
+    for k, s in enumerate(specs):
+        e = s["edge"]
+        batch.init(k, inputs.to_f32(inputs.droplet(e, e, e, s["R"], s["W"])), np.zeros((3, e, e, e), np.float32))
+    batch.step(300)
+    for k, s in enumerate(specs):
+        e, R, W = s["edge"], s["R"], s["W"]
+        rho, _, _ = batch.moments_numpy(k)
+        c = (e - 1) / 2
+        z, y, x = np.meshgrid(*[np.arange(e)] * 3, indexing="ij")
+        d = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2)
+        dp = (rho[d < max(R - 2 * W, 1.5)].mean() - rho[d > R + 2 * W].mean()) / 3
+        rel = abs(dp / (2 * s["sigma"] / R) - 1)
+        assert rel < (0.12 if R >= 8 else 0.20), (k, e, R, rel)
