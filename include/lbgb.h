@@ -139,11 +139,13 @@ int lb_set_tile(lb_ctx* ctx, int ty, int zc);
 int lb_get_tile(const lb_ctx* ctx, int* ty, int* zc);
 
 /*
- * lb_tune -- time every supported (ty, zc) on a scratch box with this box's
- * nx, ny, storage and min(nz, 128) planes, for `steps` steps each, and keep
- * the fastest.  Allocates and frees its scratch; the context's state is not
- * touched.  Results are cached per (device name, nx, ny, nz, storage) in the
- * file named by LBGB_TUNE_CACHE, if set.
+ * lb_tune -- time every supported (ty, zc) for `steps` steps each (best of two
+ * windows) and keep the fastest.  Before lb_init it times on the context's own
+ * arrays, so the timed launches have the real box's block counts, and leaves
+ * the context uninitialised; after lb_init it times on a scratch box with this
+ * box's nx, ny, storage and min(nz, 128) planes, allocated and freed here,
+ * and leaves the state untouched.  Results are cached per (device name, nx,
+ * ny, nz, storage) in the file named by LBGB_TUNE_CACHE, if set.
  */
 int lb_tune(lb_ctx* ctx, int steps);
 

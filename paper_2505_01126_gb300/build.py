@@ -36,7 +36,7 @@ def _flags(verbose: bool):
 
 def _deps():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
+    files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".inc"))]
     files.append(os.path.join(ROOT, "include", "lbgb.h"))
     return files
 

@@ -563,20 +563,36 @@ int lb_tune(lb_ctx* c, int steps) {
             fclose(fp);
         }
     }
-    const int nzt = c->nz < 128 ? c->nz : 128;
+    // Before lb_init the context's own arrays are free: time the shapes on them
+    // (zeroed; the step's cost does not depend on the values) so the block
+    // counts are those of the real box.  After lb_init, time on a scratch box
+    // with this box's nx, ny and min(nz, 128) planes.
+    const bool in_place = !c->initialized;
     lb_ctx* s = nullptr;
-    int rc = lb_create(c->nx, c->ny, nzt, c->tau, c->M, c->W, c->sigma, &c->force, c->storage, &s);
-    if (rc) return rc;
-    lb_set_stream(s, c->stream);
-    // scratch state: phi = 0, u = 0 (the kernel's cost does not depend on the values)
     float* z = nullptr;
-    cudaError_t e = cudaMalloc(&z, (size_t)s->N * 4 * sizeof(float));
-    if (e != cudaSuccess) {
-        lb_destroy(s);
-        return fail(LB_ENOMEM, "tune scratch: %s", cudaGetErrorString(e));
+    int rc = LB_OK;
+    if (in_place) {
+        s = c;
+        LB_CUDA(cudaMemsetAsync(c->f, 0, (size_t)c->N * 27 * c->fsize, c->stream));
+        LB_CUDA(cudaMemsetAsync(c->g[0], 0, (size_t)c->N * 7 * sizeof(float), c->stream));
+        LB_CUDA(cudaMemsetAsync(c->g[1], 0, (size_t)c->N * 7 * sizeof(float), c->stream));
+        LB_CUDA(cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
+        c->initialized = true;
+        c->t = 0;
+    } else {
+        const int nzt = c->nz < 128 ? c->nz : 128;
+        rc = lb_create(c->nx, c->ny, nzt, c->tau, c->M, c->W, c->sigma, &c->force, c->storage, &s);
+        if (rc) return rc;
+        lb_set_stream(s, c->stream);
+        cudaError_t e = cudaMalloc(&z, (size_t)s->N * 4 * sizeof(float));
+        if (e != cudaSuccess) {
+            lb_destroy(s);
+            return fail(LB_ENOMEM, "tune scratch: %s", cudaGetErrorString(e));
+        }
+        cudaMemsetAsync(z, 0, (size_t)s->N * 4 * sizeof(float), c->stream);
+        rc = lb_init(s, z, z + s->N);
     }
-    cudaMemsetAsync(z, 0, (size_t)s->N * 4 * sizeof(float), c->stream);
-    rc = lb_init(s, z, z + s->N);
+    const int nzt = s->nz;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -610,8 +626,15 @@ int lb_tune(lb_ctx* c, int steps) {
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(z);
-    lb_destroy(s);
+    if (in_place) {
+        LB_CUDA(cudaStreamSynchronize(c->stream));
+        c->initialized = false;  // the timed steps left no usable state
+        c->t = 0;
+        c->launches = 0;
+    } else {
+        cudaFree(z);
+        lb_destroy(s);
+    }
     if (rc) return rc;
     if (cache) {
         FILE* fp = fopen(cache, "a");

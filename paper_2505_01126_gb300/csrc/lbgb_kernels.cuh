@@ -296,392 +296,19 @@ __host__ __device__ __forceinline__ void collide_site(float pp, float m0, float 
 // Phase A reads the D3Q7 planes either per site (VEC = false) or, when nx is a
 // multiple of 4, as float4 quads of 4 consecutive sites covering the halo row
 // x0-4 .. x0+TX+3 (VEC = true): 7 vector loads per 4 sites.
-template <class FT, int TY, int MODE, int PAR, bool VEC, class Args>
-__device__ __forceinline__ void fused_tile(const Args& a, int bx, int by, int bz, long long pblock) {
-    constexpr int TX = 32;
-    constexpr int NT = TX * TY;
-    constexpr int HX = TX + 4, HY = TY + 4, NHA = HX * HY;  // halo-2 plane (phi)
-    constexpr int BX = TX + 2, BY = TY + 2, NHB = BX * BY;  // halo-1 plane (n)
-    constexpr int NA = (NHA + NT - 1) / NT;
-    constexpr int NB = (NHB + NT - 1) / NT;
-
-    __shared__ float s_Z[2][NHA];        // 6 Sz phi, planes by parity
-    __shared__ float s_D[2][NHA];        // 2 Dz phi
-    __shared__ float s_phi[4][NT];       // phi of the interior, 4-plane ring
-    __shared__ float s_n[4][3][NHB];     // unit normal, 4-plane ring
-    __shared__ float s_k[3][NHB];        // 6 Sz n_x, 6 Sz n_y, 2 Dz n_z of one plane
-    __shared__ float s_grad[2][4][NT];   // grad phi and |grad phi| of the interior
-    // VEC: phase-A quads of the D3Q7 planes staged by cp.async one plane ahead (2-plane ring)
-    constexpr int NQS = VEC ? (TX / 4 + 2) * HY : 1;  // quad index tid + k*NT < NQS
-    __shared__ __align__(16) float4 s_gA[VEC ? 2 : 1][VEC ? 7 : 1][NQS];
-
-    using C = Codec<FT>;
-    const int tid = threadIdx.x;
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int N = a.N;
-    const int plane = nx * ny;
-    const int x0 = bx * TX, y0 = by * TY;
-    const int z0 = bz * a.zc;
-    const int z1 = min(z0 + a.zc, nz);
-
-    // phase-A slots (halo-2 plane), fixed for the whole march.  A slot is one
-    // site (scalar) or one float4 quad of 4 sites (VEC).
-    constexpr int QX = TX / 4 + 2;  // quads per halo row
-    constexpr int NQ = QX * HY;
-    constexpr int NS = VEC ? (NQ + NT - 1) / NT : NA;
-    constexpr int NV = VEC ? 4 : 1;
-    int a_row[NS], a_idx[NS], a_int[NS];
-    float ph1[NS][NV], ph2[NS][NV];  // phi one and two planes below, per site of a slot
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-        const int idx = tid + k * NT;
-        if (VEC) {
-            // a_idx: halo-plane index of the quad's row; a_int: halo x of its first
-            // site (-2 for the leftmost quad; sites outside [0, HX) are dropped)
-            const int ry = idx / QX, qx = idx - (idx / QX) * QX;
-            a_idx[k] = idx < NQ ? ry * HX : INT_MIN;
-            a_row[k] = wrap_mod(y0 + ry - 2, ny) * nx + wrap_mod(x0 - 4 + 4 * qx, nx);
-            a_int[k] = 4 * qx - 2;
-        } else {
-            a_idx[k] = idx < NHA ? idx : -1;
-            const int ly = idx / HX, lx = idx - (idx / HX) * HX;
-            a_row[k] = wrap_mod(y0 + ly - 2, ny) * nx + wrap_mod(x0 + lx - 2, nx);
-            a_int[k] = 0;
-        }
-#pragma unroll
-        for (int j = 0; j < NV; ++j) {
-            ph1[k][j] = 0.f;
-            ph2[k][j] = 0.f;
-        }
-    }
-
-    // phase-C site and its periodic neighbour offsets (32-bit site indices)
-    const int lx = tid % TX, ly = tid / TX;
-    const int gx = x0 + lx, gy = y0 + ly;
-    const bool active = gx < nx && gy < ny;
-    const int cxs = active ? gx : nx - 1, cys = active ? gy : ny - 1;
-    const int row_s = cys * nx + cxs;
-    const int DX0 = cxs == 0 ? nx - 1 : -1, DX2 = cxs == nx - 1 ? 1 - nx : 1;
-    const int DY0 = cys == 0 ? (ny - 1) * nx : -nx, DY2 = cys == ny - 1 ? (1 - ny) * nx : nx;
-    const int DX[3] = {DX0, 0, DX2};
-    const int DY[3] = {DY0, 0, DY2};
-    const int c1 = (ly + 1) * BX + (lx + 1);  // own site in the halo-1 plane
-
-    float A_lin = 0.f;
-    if (MODE != MODE_INIT && a.force_kind == FK_LINEAR) A_lin = (float)a.st->A;
-
-    // FP32 per-thread partial sums over this thread's <= zc sites; FP64 beyond
-    float s_phi_acc = 0.f, s_K = 0.f, s_aa = 0.f, s_mass = 0.f, s_umax2 = 0.f;
-
-    // one site of phase A: z-smoothed planes of zp-1 and the interior phi of zp
-    auto a_site = [&](int zp, bool make_zd, int hidx, float p, float& h1, float& h2) {
-        if (make_zd) {
-            s_Z[(zp - 1) & 1][hidx] = fmaf(4.f, h1, h2 + p);
-            s_D[(zp - 1) & 1][hidx] = p - h2;
-        }
-        const int hy = hidx / HX, hx = hidx - (hidx / HX) * HX;
-        if (hx >= 2 && hx < TX + 2 && hy >= 2 && hy < TY + 2) s_phi[zp & 3][(hy - 2) * TX + (hx - 2)] = p;
-        h2 = h1;
-        h1 = p;
-    };
-
-    // VEC: start the asynchronous copies of plane zp's quads into ring slot zp & 1.
-    // Every thread commits one group per call (possibly empty) so that the
-    // group counts agree across the block.
-    auto a_issue = [&](int zp) {
-        if (VEC) {
-            const int zb = wrap_mod(zp, nz) * plane;
-#pragma unroll
-            for (int k = 0; k < NS; ++k)
-                if (a_idx[k] != INT_MIN) {
-#pragma unroll
-                    for (int q = 0; q < 7; ++q)
-                        cp_async16(&s_gA[zp & 1][q][tid + k * NT], a.gin[q] + zb + a_row[k]);
-                }
-            cp_async_commit();
-        }
-    };
-
-    // phi of plane zp (VEC: from the staged quads of slot zp & 1, which this
-    // thread copied itself and has waited for)
-    auto phaseA = [&](int zp, bool make_zd) {
-        const int zb = wrap_mod(zp, nz) * plane;
-#pragma unroll
-        for (int k = 0; k < NS; ++k) {
-            if (VEC) {
-                if (a_idx[k] != INT_MIN) {
-                    float4 p4 = s_gA[zp & 1][0][tid + k * NT];
-#pragma unroll
-                    for (int q = 1; q < 7; ++q) {
-                        const float4 t = s_gA[zp & 1][q][tid + k * NT];
-                        p4.x += t.x; p4.y += t.y; p4.z += t.z; p4.w += t.w;
-                    }
-                    const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int hx = a_int[k] + j;
-                        if (hx >= 0 && hx < HX) a_site(zp, make_zd, a_idx[k] + hx, pv[j], ph1[k][j], ph2[k][j]);
-                    }
-                }
-            } else if (a_idx[k] >= 0) {
-                const int s = zb + a_row[k];
-                float p;
-                if (MODE == MODE_INIT) {
-                    p = a.in_phi[s];
-                } else {
-                    p = __ldg(a.gin[0] + s);
-#pragma unroll
-                    for (int q = 1; q < 7; ++q) p += __ldg(a.gin[q] + s);
-                }
-                a_site(zp, make_zd, a_idx[k], p, ph1[k][0], ph2[k][0]);
-            }
-        }
-    };
-
-    // n at plane zp on the halo-1 plane; with make_k also the curvature
-    // ingredients of plane zp-1 (needs n at zp-2, zp-1, zp of the same site,
-    // which this thread wrote itself).
-    auto phaseB = [&](int zp, bool make_k) {
-        const float* Z = s_Z[zp & 1];
-        const float* D = s_D[zp & 1];
-#pragma unroll
-        for (int k = 0; k < NB; ++k) {
-            const int idx = tid + k * NT;
-            if (idx < NHB) {
-                const int by = idx / BX, bx = idx - (idx / BX) * BX;
-                const int c = (by + 1) * HX + (bx + 1);
-                const float zmm = Z[c - HX - 1], zm0 = Z[c - HX], zmp = Z[c - HX + 1];
-                const float z0m = Z[c - 1], z0p = Z[c + 1];
-                const float zpm = Z[c + HX - 1], zp0 = Z[c + HX], zpp = Z[c + HX + 1];
-                // differences before sums keep the small gradients of a nearly uniform phi accurate
-                const float Gx = fmaf(4.f, z0p - z0m, (zmp - zmm) + (zpp - zpm));
-                const float Gy = fmaf(4.f, zp0 - zm0, (zpm - zmm) + (zpp - zmp));
-                const float rm = fmaf(4.f, D[c - 1], D[c - HX - 1] + D[c + HX - 1]);
-                const float r0 = fmaf(4.f, D[c], D[c - HX] + D[c + HX]);
-                const float rp = fmaf(4.f, D[c + 1], D[c - HX + 1] + D[c + HX + 1]);
-                const float Gz = fmaf(4.f, r0, rm + rp);
-                constexpr float k72 = 1.f / 72.f;
-                const float g0 = Gx * k72, g1 = Gy * k72, g2 = Gz * k72;
-                const float gg = g0 * g0 + g1 * g1 + g2 * g2;
-                const float r = rsqrtf(fmaxf(gg, 1e-20f));  // 1 / max(|grad phi|, 1e-10)
-                const float n0 = g0 * r, n1 = g1 * r, n2 = g2 * r;
-                s_n[zp & 3][0][idx] = n0;
-                s_n[zp & 3][1][idx] = n1;
-                s_n[zp & 3][2][idx] = n2;
-                if (bx >= 1 && bx <= TX && by >= 1 && by <= TY) {
-                    const int e = (by - 1) * TX + (bx - 1);
-                    s_grad[zp & 1][0][e] = g0;
-                    s_grad[zp & 1][1][e] = g1;
-                    s_grad[zp & 1][2][e] = g2;
-                    s_grad[zp & 1][3][e] = gg * r;  // |grad phi|
-                }
-                if (make_k) {
-                    s_k[0][idx] = fmaf(4.f, s_n[(zp - 1) & 3][0][idx], s_n[(zp - 2) & 3][0][idx] + n0);
-                    s_k[1][idx] = fmaf(4.f, s_n[(zp - 1) & 3][1][idx], s_n[(zp - 2) & 3][1][idx] + n1);
-                    s_k[2][idx] = n2 - s_n[(zp - 2) & 3][2][idx];
-                }
-            }
-        }
-    };
-
-    // prologue: phi history from z0-2, gradient planes and n at z0-1, z0
-    // (VEC: each plane's copies are waited for at once; plane z0+2 is left in flight)
-    a_issue(z0 - 2);
-    cp_async_wait<0>();
-    phaseA(z0 - 2, false);
-    a_issue(z0 - 1);
-    cp_async_wait<0>();
-    phaseA(z0 - 1, false);
-    a_issue(z0);
-    cp_async_wait<0>();
-    phaseA(z0, true);
-    __syncthreads();
-    phaseB(z0 - 1, false);
-    a_issue(z0 + 1);
-    cp_async_wait<0>();
-    phaseA(z0 + 1, true);
-    __syncthreads();
-    phaseB(z0, false);
-    a_issue(z0 + 2);
-
-    for (int z = z0; z < z1; ++z) {
-        const int DZ0 = z == 0 ? (nz - 1) * plane : -plane;
-        const int DZ2 = z == nz - 1 ? (1 - nz) * plane : plane;
-        const int DZ[3] = {DZ0, 0, DZ2};
-        const int s = z * plane + row_s;
-
-        // ---- issue this plane's population loads first
-        float dl[27];
-        float gl[7];
-        float uin0 = 0.f, uin1 = 0.f, uin2 = 0.f;
-        if (active) {
-            if (MODE == MODE_INIT) {
-                uin0 = a.in_u[s];
-                uin1 = a.in_u[N + s];
-                uin2 = a.in_u[2 * N + s];
-            } else {
-#pragma unroll
-                for (int i = 0; i < 27; ++i) {
-                    if (PAR == 0) {
-                        dl[i] = C::ld(static_cast<const FT*>(a.fk[i]) + s);
-                    } else {  // f_i(x) sits in slot (x - c_i, opposite of i)
-                        const int src = s + DZ[1 - CZ(i)] + DY[1 - CY(i)] + DX[1 - CX(i)];
-                        dl[i] = C::ld(static_cast<const FT*>(a.fk[26 - i]) + src);
-                    }
-                }
-                if (MODE == MODE_STEP) {
-#pragma unroll
-                    for (int q = 0; q < 7; ++q) gl[q] = __ldg(a.gin[q] + s);
-                }
-            }
-        }
-
-        a_issue(z + 3);       // next plane's phase-A copies
-        cp_async_wait<1>();   // this thread's copies of plane z+2 have landed
-        phaseA(z + 2, true);
-        __syncthreads();
-        phaseB(z + 1, true);
-        __syncthreads();
-
-        if (active) {
-            const int e = ly * TX + lx;
-            const float phi = s_phi[z & 3][e];
-            const float n0 = s_n[z & 3][0][c1], n1 = s_n[z & 3][1][c1], n2 = s_n[z & 3][2][c1];
-
-            if (MODE == MODE_INIT) {
-                // f = f^eq(p* = 1, u): delta_i = 3 c.u + 4.5 (c.u)^2 - 1.5 u^2 (even layout)
-                const float u0 = uin0, u1 = uin1, u2 = uin2;
-                const float uu = u0 * u0 + u1 * u1 + u2 * u2;
-                const float Pp[3] = {fmaf(4.5f * u0, u0, 3.f * u0), fmaf(4.5f * u1, u1, 3.f * u1),
-                                     fmaf(4.5f * u2, u2, 3.f * u2)};
-                const float Pm[3] = {fmaf(4.5f * u0, u0, -3.f * u0), fmaf(4.5f * u1, u1, -3.f * u1),
-                                     fmaf(4.5f * u2, u2, -3.f * u2)};
-                float v[27];
-                quad_poly27(-1.5f * uu, Pp, Pm, 9.f * u0 * u1, 9.f * u0 * u2, 9.f * u1 * u2, v);
-#pragma unroll
-                for (int i = 0; i < 27; ++i) C::st(static_cast<FT*>(a.fk[i]) + s, v[i]);
-                const float phs = a.sharp * fmaxf(phi * (1.f - phi), 0.f);  // interface indicator, 0 outside [0, 1]
-                const float j0 = fmaf(4.f * phi, u0, phs * n0);
-                const float j1 = fmaf(4.f * phi, u1, phs * n1);
-                const float j2 = fmaf(4.f * phi, u2, phs * n2);
-                a.gout[0][s] = 0.25f * phi;
-                a.gout[1][s] = 0.125f * (phi + j0);
-                a.gout[2][s] = 0.125f * (phi - j0);
-                a.gout[3][s] = 0.125f * (phi + j1);
-                a.gout[4][s] = 0.125f * (phi - j1);
-                a.gout[5][s] = 0.125f * (phi + j2);
-                a.gout[6][s] = 0.125f * (phi - j2);
-                s_phi_acc += phi;
-                s_K = fmaf(0.5f, uu, s_K);
-                s_umax2 = fmaxf(s_umax2, uu);
-            } else {
-                // ---- step 4: kappa = div n from the factorised planes (sum / 72)
-                const float* K0 = s_k[0];
-                const float* K1 = s_k[1];
-                const float* K2 = s_k[2];
-                const float kx = fmaf(4.f, K0[c1 + 1] - K0[c1 - 1],
-                                      (K0[c1 - BX + 1] - K0[c1 - BX - 1]) + (K0[c1 + BX + 1] - K0[c1 + BX - 1]));
-                const float ky = fmaf(4.f, K1[c1 + BX] - K1[c1 - BX],
-                                      (K1[c1 + BX - 1] - K1[c1 - BX - 1]) + (K1[c1 + BX + 1] - K1[c1 - BX + 1]));
-                const float qm = fmaf(4.f, K2[c1 - 1], K2[c1 - BX - 1] + K2[c1 + BX - 1]);
-                const float q0 = fmaf(4.f, K2[c1], K2[c1 - BX] + K2[c1 + BX]);
-                const float qp = fmaf(4.f, K2[c1 + 1], K2[c1 - BX + 1] + K2[c1 + BX + 1]);
-                const float kz = fmaf(4.f, q0, qm + qp);
-                const float kap = (kx + ky + kz) * (1.f / 72.f);
-
-                // ---- steps 5-6: surface tension and external force
-                const float gr0 = s_grad[z & 1][0][e], gr1 = s_grad[z & 1][1][e];
-                const float gr2 = s_grad[z & 1][2][e], grm = s_grad[z & 1][3][e];
-                const float fsc = -a.beta * kap * grm;
-                float Fe0 = fsc * gr0, Fe1 = fsc * gr1, Fe2 = fsc * gr2;
-                if (a.force_kind == FK_CONST) {
-                    Fe0 += a.gc0; Fe1 += a.gc1; Fe2 += a.gc2;
-                } else if (a.force_kind == FK_ABC) {
-                    const float* T = a.abc;
-                    const float sx = T[gx], cxv = T[nx + gx];
-                    const float sy = T[2 * nx + gy], cyv = T[2 * nx + ny + gy];
-                    const float sz = T[2 * nx + 2 * ny + z], czv = T[2 * nx + 2 * ny + nz + z];
-                    Fe0 += a.A_abc * (sz + cyv);
-                    Fe1 += a.A_abc * (sx + czv);
-                    Fe2 += a.A_abc * (sy + cxv);
-                }
-
-                // ---- step 7: moments of the shifted populations
-                float pp, m0, m1, m2, P00, P11, P22, P01, P02, P12;
-                shifted_moments(dl, pp, m0, m1, m2, P00, P11, P22, P01, P02, P12);
-
-                if (MODE == MODE_MOMENTS) {
-                    // ---- step 8: forced velocity
-                    const float inv = 1.f / (1.f - 0.5f * A_lin);
-                    const float u0 = fmaf(0.5f, Fe0, m0) * inv;
-                    const float u1 = fmaf(0.5f, Fe1, m1) * inv;
-                    const float u2 = fmaf(0.5f, Fe2, m2) * inv;
-                    if (a.out_rho) a.out_rho[s] = 1.f + pp;
-                    if (a.out_u) {
-                        a.out_u[s] = u0;
-                        a.out_u[N + s] = u1;
-                        a.out_u[2 * N + s] = u2;
-                    }
-                    if (a.out_phi) a.out_phi[s] = phi;
-                } else {
-                    // ---- steps 8-10: velocity, force, Hermite coefficient, collision
-                    float u0, u1, u2, aa, v[27];
-                    collide_site(pp, m0, m1, m2, P00, P11, P22, P01, P02, P12, Fe0, Fe1, Fe2, A_lin, a.omega,
-                                 u0, u1, u2, aa, v);
-
-                    // ---- step 13 (per site): partial sums
-                    const float uu = u0 * u0 + u1 * u1 + u2 * u2;
-                    s_phi_acc += phi;
-                    s_K = fmaf(0.5f, uu, s_K);
-                    s_aa += aa;
-                    s_mass += pp;
-                    s_umax2 = fmaxf(s_umax2, uu);
-
-                    // ---- step 12: AA streaming stores
-#pragma unroll
-                    for (int i = 0; i < 27; ++i) {
-                        if (PAR == 0) {  // f*_i to slot (x, opposite of i)
-                            C::st(static_cast<FT*>(a.fk[26 - i]) + s, v[i]);
-                        } else {         // f*_i to slot (x + c_i, i)
-                            const int dst = s + DZ[1 + CZ(i)] + DY[1 + CY(i)] + DX[1 + CX(i)];
-                            C::st(static_cast<FT*>(a.fk[i]) + dst, v[i]);
-                        }
-                    }
-
-                    // ---- step 11: D3Q7 BGK with the sharpening equilibrium, push
-                    const float om = a.omega_phi;
-                    const float phs = a.sharp * fmaxf(phi * (1.f - phi), 0.f);  // interface indicator, 0 outside [0, 1]
-                    const float j0 = fmaf(4.f * phi, u0, phs * n0);
-                    const float j1 = fmaf(4.f * phi, u1, phs * n1);
-                    const float j2 = fmaf(4.f * phi, u2, phs * n2);
-                    a.gout[0][s] = fmaf(om, 0.25f * phi - gl[0], gl[0]);
-                    a.gout[1][s + DX[2]] = fmaf(om, 0.125f * (phi + j0) - gl[1], gl[1]);
-                    a.gout[2][s + DX[0]] = fmaf(om, 0.125f * (phi - j0) - gl[2], gl[2]);
-                    a.gout[3][s + DY[2]] = fmaf(om, 0.125f * (phi + j1) - gl[3], gl[3]);
-                    a.gout[4][s + DY[0]] = fmaf(om, 0.125f * (phi - j1) - gl[4], gl[4]);
-                    a.gout[5][s + DZ[2]] = fmaf(om, 0.125f * (phi + j2) - gl[5], gl[5]);
-                    a.gout[6][s + DZ[0]] = fmaf(om, 0.125f * (phi - j2) - gl[6], gl[6]);
-                }
-            }
-        }
-    }
-
-    if (MODE != MODE_MOMENTS) {
-        double v0 = s_phi_acc, v1 = s_K, v2 = s_aa, v3 = s_mass, v4 = s_umax2;
-        block_reduce5<NT>(v0, v1, v2, v3, v4);
-        if (tid == 0) {
-            double* out = a.partials + pblock * NPART;
-            out[0] = v0; out[1] = v1; out[2] = v2; out[3] = v3; out[4] = v4;
-        }
-    }
-}
-
 // One box: a block per (32 x TY tile, z-chunk).
 template <class FT, int TY, int MODE, int PAR, bool VEC>
 __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 512 / (32 * TY)))
-fused_step_kernel(const __grid_constant__ StepArgs a) {
-    const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    fused_tile<FT, TY, MODE, PAR, VEC>(a, blockIdx.x, blockIdx.y, blockIdx.z, b);
+fused_step_kernel(const StepArgs a) {
+#define TILE_BX blockIdx.x
+#define TILE_BY blockIdx.y
+#define TILE_BZ blockIdx.z
+#define TILE_PBLOCK (((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x)
+#include "lbgb_tile_body.inc"
+#undef TILE_BX
+#undef TILE_BY
+#undef TILE_BZ
+#undef TILE_PBLOCK
 }
 
 // ------------------------------------------------------ batched ensemble
@@ -713,7 +340,7 @@ struct PlaneSet {
     __device__ __forceinline__ T* operator[](int q) const { return base + q * stride; }
 };
 
-// The argument view of one box for fused_tile (steps only, no external force).
+// The argument view of one box for the tile body (steps only, no external force).
 template <class FT>
 struct BoxTileArgs {
     int nx, ny, nz, zc, N;
@@ -747,8 +374,21 @@ batch_step_kernel(const __grid_constant__ BatchArgs b) {
         t.out_rho = t.out_u = t.out_phi = nullptr;
         t.in_phi = t.in_u = nullptr;
         const int local = item - d.item0;
-        const int tx = local % d.tiles_x, rest = local / d.tiles_x;
-        fused_tile<FT, TY, MODE_STEP, PAR, VEC>(t, tx, rest % d.tiles_y, rest / d.tiles_y, item);
+        const int tbx = local % d.tiles_x, rest = local / d.tiles_x;
+        const int tby = rest % d.tiles_y, tbz = rest / d.tiles_y;
+        {
+            const BoxTileArgs<FT>& a = t;
+            constexpr int MODE = MODE_STEP;
+#define TILE_BX tbx
+#define TILE_BY tby
+#define TILE_BZ tbz
+#define TILE_PBLOCK ((long long)item)
+#include "lbgb_tile_body.inc"
+#undef TILE_BX
+#undef TILE_BY
+#undef TILE_BZ
+#undef TILE_PBLOCK
+        }
         __syncthreads();  // the shared rings are reused by the block's next item
     }
 }
