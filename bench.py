@@ -55,6 +55,21 @@ def dist_env():
         os.environ.get("LOCAL_RANK", "0"))
 
 
+def whole_job(ms_local: float, sites_per_rank: int, steps: int, world: int, dist=None):
+    """Whole-job MLUPS over `world` replica ranks: the slowest rank's time (max over
+    ranks, via an all-reduce when `dist` is a torch.distributed module with an
+    initialised group) divides the sites all ranks updated.  Returns (MLUPS, t_max_ms)."""
+    t_max = float(ms_local)
+    if dist is not None and world > 1:
+        import torch
+
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([t_max], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    return sites_per_rank * steps * world / (t_max * 1e-3) / 1e6, t_max
+
+
 def measured_traffic(storage: str, n_sites: int):
     """DRAM bytes per fused-kernel launch from the committed ncu record, scaled to
     n_sites, or None if the kernel sources changed since the capture."""
@@ -95,7 +110,7 @@ class ClockSampler:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -209,6 +224,7 @@ def run_ensemble(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(torch.cuda.current_device())
+    time.sleep(0.3)
     e0.record(stream)
     batch.step(args.steps)
     e1.record(stream)
@@ -252,7 +268,7 @@ def run_ensemble(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
@@ -311,6 +327,9 @@ def main():
     phi_d = torch.from_numpy(w.phi).cuda()
     u_d = torch.from_numpy(w.u).cuda()
     box.init(phi_d, u_d)
+    # clock sampling starts before the warm-up so it is running throughout the timed region
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    time.sleep(0.3)
     box.step(args.warmup)
     box.sync()
 
@@ -318,7 +337,6 @@ def main():
     box.set_timing(True)
     launches0 = box.launches
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     barrier()
     torch.cuda.synchronize()
     e0.record(stream)
@@ -334,12 +352,7 @@ def main():
     diag = box.diagnostics(allow_nonfinite=True)
 
     # max over ranks
-    t_max = ms
-    if pg is not None:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = N * args.steps * world / (t_max * 1e-3) / 1e6
+    value, t_max = whole_job(ms, N, args.steps, world, pg)
 
     # ---- end to end through the public API with pinned host buffers
     phi_h = torch.from_numpy(w.phi).pin_memory()
@@ -358,11 +371,7 @@ def main():
     box.moments(rho_o.numpy(), u_o.numpy(), phi_o.numpy())
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
-    if pg is not None:
-        t = torch.tensor([t_e2e], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e_value = N * e2e_steps * world / t_e2e / 1e6
+    e2e_value, _ = whole_job(t_e2e * 1e3, N, e2e_steps, world, pg)
     h2d = 4 * N * 4 / e2e_steps
     d2h = 40 + 5 * N * 4 / e2e_steps
 
