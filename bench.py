@@ -45,9 +45,26 @@ SAMPLE_EDGE, SAMPLE_BUBBLES, SAMPLE_STEPS = 128, 8, 10
 REF_EDGE = 64
 
 
+# Presets of the bubbly forced HIT workload: edge, bubbles, radius, tau, seed.
+PRESETS = {
+    "hit256": (256, 64, 10.0, 0.51, 2),     # the default (bench) workload
+    "hit512": (512, 256, 12.0, 0.51, 3),    # 512^3, 256 bubbles R = 12
+    "hit768": (768, 864, 12.0, 0.505, 5),   # FP32 comparison box for hit1024 (same bubble fraction)
+    "hit1024": (1024, 2048, 12.0, 0.505, 5),  # 1024^3, 2048 bubbles R = 12, 16-bit storage
+}
+
+
 def workload(edge: int):
     nb = max(1, round(64 * (edge / 256) ** 3))
     return inputs.bubbly_hit(edge, nb, 10.0, seed=2), nb
+
+
+def preset_workload(name: str):
+    """Workload and bubble count of a preset; large boxes are generated on the device."""
+    edge, nb, R, tau, seed = PRESETS[name]
+    if edge >= 384:
+        return inputs.bubbly_hit_device(edge, nb, R, seed=seed, tau=tau), nb
+    return inputs.bubbly_hit(edge, nb, R, seed=seed, tau=tau), nb
 
 
 def dist_env():
@@ -279,6 +296,7 @@ def main():
     ap.add_argument("--workload", default="hit", choices=["hit", "ensemble"],
                     help="hit: one 256^3 bubbly HIT box (default); ensemble: the 512-box droplet batch")
     ap.add_argument("--boxes", type=int, default=512)
+    ap.add_argument("--preset", choices=sorted(PRESETS), help="bubbly HIT preset (overrides --edge)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -312,7 +330,11 @@ def main():
     barrier()
     from paper_2505_01126_gb300 import lbgb
 
-    w, nb = workload(args.edge)
+    if args.preset:
+        w, nb = preset_workload(args.preset)
+        args.edge = w.n[0]
+    else:
+        w, nb = workload(args.edge)
     n = args.edge
     N = n ** 3
     force = lbgb.Force(kind=lbgb.LB_FORCE_LINEAR, T_relax=w.T_relax)
@@ -324,8 +346,8 @@ def main():
         os.environ.setdefault("LBGB_TUNE_CACHE", os.path.join(ROOT, "paper_2505_01126_gb300", "tune_cache.txt"))
         box.tune(8)
     ty, zc = box.tile()
-    phi_d = torch.from_numpy(w.phi).cuda()
-    u_d = torch.from_numpy(w.u).cuda()
+    phi_d = w.phi if torch.is_tensor(w.phi) else torch.from_numpy(w.phi).cuda()
+    u_d = w.u if torch.is_tensor(w.u) else torch.from_numpy(w.u).cuda()
     box.init(phi_d, u_d)
     # clock sampling starts before the warm-up so it is running throughout the timed region
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
@@ -355,8 +377,9 @@ def main():
     value, t_max = whole_job(ms, N, args.steps, world, pg)
 
     # ---- end to end through the public API with pinned host buffers
-    phi_h = torch.from_numpy(w.phi).pin_memory()
-    u_h = torch.from_numpy(w.u).pin_memory()
+    phi_h = (phi_d.cpu() if torch.is_tensor(w.phi) else torch.from_numpy(w.phi)).pin_memory()
+    u_h = (u_d.cpu() if torch.is_tensor(w.u) else torch.from_numpy(w.u)).pin_memory()
+    del phi_d, u_d
     rho_o = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
     u_o = torch.empty((3, n, n, n), dtype=torch.float32).pin_memory()
     phi_o = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
@@ -392,7 +415,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-                "config": {"workload": f"{n}^3 periodic bubbly forced HIT, {nb} bubbles R=10, W=3, sigma=0.01, "
+                "config": {"workload": f"{n}^3 periodic bubbly forced HIT, {nb} bubbles R="
+                                       f"{PRESETS[args.preset][2] if args.preset else 10.0:g}, W=3, sigma=0.01, "
                                        f"tau={w.tau}, M=0.1, u_rms=0.02, linear forcing",
                            "edge": n, "storage": args.storage, "tile": [32, ty, zc],
                            "l2": "inputs larger than L2 (populations %.2f GB), no flush" % (bps * N / 2 / 1e9),

@@ -251,3 +251,54 @@ def ensemble_specs(count: int, seed: int, edges=(24, 32, 48, 64, 96)):
         sigma = 0.005 + 0.015 * rng.uniform()
         specs.append({"edge": e, "R": R, "sigma": sigma, "tau": 1.0, "M": 0.1, "W": 3.0})
     return specs
+
+
+def bubbly_hit_device(edge: int, n_bubbles: int, R: float, seed: int, tau: float = 0.51, u_rms: float = 0.02,
+                      W: float = 3.0, sigma: float = 0.01, M: float = 0.1, force_kind: int = 3, device="cuda"):
+    """bubbly_hit built on a CUDA device, for boxes too large for host FFTs (512^3 and
+    up): the same splitmix64 draws, spectrum, bubble centres and profile, evaluated in
+    FP64 with torch's FFT on the device and rounded to FP32.  Returns a Workload whose
+    phi and u are device tensors."""
+    import torch
+
+    n = edge
+    rng = SplitMix64(seed)
+    centers = bubble_centers((n, n, n), n_bubbles, R, W, rng)
+    phi = torch.zeros((n, n, n), dtype=torch.float64, device=device)
+    h = int(math.ceil(R + 8.0 * W))
+    for c in centers:
+        idx = []
+        dist = []
+        for ax in range(3):
+            i = np.unique(np.mod(np.arange(int(math.floor(c[ax])) - h, int(math.floor(c[ax])) + h + 2), n))
+            idx.append(torch.from_numpy(i).to(device))
+            dist.append(torch.from_numpy(_min_image(i - c[ax], n)).to(device))
+        d = torch.sqrt(dist[2][:, None, None] ** 2 + dist[1][None, :, None] ** 2 + dist[0][None, None, :] ** 2)
+        local = 0.5 - 0.5 * torch.tanh(2.0 * (d - R) / W)
+        iz, iy, ix = idx[2][:, None, None], idx[1][None, :, None], idx[0][None, None, :]
+        phi[iz, iy, ix] = torch.maximum(phi[iz, iy, ix], local)
+    rng_u = SplitMix64(seed + 0x5EED)
+    ks = fourier_modes(1.0, 4.0)
+    amp = solenoidal_amplitudes(rng_u, ks)
+    u = torch.empty((3, n, n, n), dtype=torch.float32, device=device)
+    sq = torch.zeros((), dtype=torch.float64, device=device)
+    for comp in range(3):
+        spec = torch.zeros((n, n, n), dtype=torch.complex128, device=device)
+        for m, k in enumerate(ks):
+            spec[k[2] % n, k[1] % n, k[0] % n] += complex(amp[m, comp])
+        uc = torch.fft.ifftn(spec).real * float(n ** 3)
+        del spec
+        sq += (uc * uc).sum()
+        u[comp] = uc.to(torch.float32)
+        del uc
+    rms = math.sqrt(float(sq) / n ** 3 / 3.0)
+    # rescale in FP64 before the final rounding, as bubbly_hit does
+    u64_scale = u_rms / rms if rms > 0 else 1.0
+    for comp in range(3):
+        spec = torch.zeros((n, n, n), dtype=torch.complex128, device=device)
+        for m, k in enumerate(ks):
+            spec[k[2] % n, k[1] % n, k[0] % n] += complex(amp[m, comp])
+        u[comp] = (torch.fft.ifftn(spec).real * float(n ** 3) * u64_scale).to(torch.float32)
+        del spec
+    return Workload(f"hit{edge}_b{n_bubbles}", (n, n, n), tau, M, W, sigma, force_kind,
+                    phi.to(torch.float32), u)
