@@ -11,7 +11,7 @@ lattice-site updates per second, the paper's GLUPS x 1000) and the fraction of
 the measured HBM bandwidth reached by the fused kernel.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                       [--storage f32|f16|bf16] [--edge E]
+                       [--storage f32|f16|bf16|moments] [--edge E]
 Under torchrun (N > 1) every rank advances its own replica box (weak scaling,
 no collective on the data path); value = sum of sites*steps over ranks divided
 by the slowest rank's time.
@@ -265,7 +265,7 @@ def run_ensemble(args):
     errs = np.array(errs)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": args.storage, "data": "synthetic",
+            "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{len(specs)} independent periodic droplet boxes, edges in {{24,32,48,64,96}}, "
                                    "R = 0.25 edge (1 +- 20%), sigma in [0.005, 0.02], tau 1, M 0.1, W 3; one "
                                    "persistent launch per step under a CUDA graph",
@@ -288,7 +288,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300")
-    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "moments"],
+                    help="population storage: FP32/FP16/BF16 AA populations, or the moment-only coefficients")
     ap.add_argument("--edge", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
@@ -414,7 +415,7 @@ def main():
                 cpu = {"error": str(ex)}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"{n}^3 periodic bubbly forced HIT, {nb} bubbles R="
                                        f"{PRESETS[args.preset][2] if args.preset else 10.0:g}, W=3, sigma=0.01, "
                                        f"tau={w.tau}, M=0.1, u_rms=0.02, linear forcing",

@@ -55,11 +55,19 @@ extern "C" {
 #define LB_ESTATE (-5)     /* call out of order (e.g. lb_step before lb_init) */
 
 /* ---------------------------------------------------- population storage */
-/* Every storage holds the shifted population delta_i = (f_i - w_i)/w_i; the
- * arithmetic is FP32 and the D3Q7 populations g are FP32 in all three. */
+/* The first three hold the shifted population delta_i = (f_i - w_i)/w_i, 27
+ * planes updated in place with the AA access pattern.  LB_F32_MOMENTS holds no
+ * populations: each site keeps the ten FP32 coefficients of its post-collision
+ * population, a quadratic polynomial in c_i fixed by p*, u, a2 and F (Eq. 7,
+ * the reconstruction from macroscopic fields of the thread-safe scheme,
+ * Sec. 3), in two buffers; a step rebuilds f_i(x) from the coefficients of the
+ * neighbour x - c_i.  It computes the same FP32 numbers as LB_F32 and moves
+ * 136 instead of 272 bytes per site and step.  In all four the arithmetic is
+ * FP32 and the D3Q7 populations g are FP32. */
 #define LB_F32 0          /* delta_i stored as FP32 */
 #define LB_F16_SHIFTED 1  /* delta_i stored as FP16 */
 #define LB_BF16_SHIFTED 2 /* delta_i stored as BF16 */
+#define LB_F32_MOMENTS 3  /* post-collision coefficients, FP32 (single boxes only) */
 
 /* ------------------------------------------------------------ forcing */
 #define LB_FORCE_NONE 0
@@ -86,10 +94,10 @@ typedef struct lb_ctx lb_ctx;
  *          sharpening flux off (then sigma must be 0)
  *   sigma  surface tension, >= 0
  *   force  NULL for no external force
- *   storage  LB_F32, LB_F16_SHIFTED or LB_BF16_SHIFTED
+ *   storage  LB_F32, LB_F16_SHIFTED, LB_BF16_SHIFTED or LB_F32_MOMENTS
  * The context owns the populations (f: 27 planes, in place with the AA access
- * pattern; g: two buffers of 7 planes), the reduction scratch and the device
- * state.  Sizes: 1 <= nx, ny, nz and nx*ny*nz < 2^31 - 1 (1024^3 fits).
+ * pattern, or two buffers of 10 coefficient planes; g: two buffers of 7
+ * planes), the reduction scratch and the device state.  Sizes: 1 <= nx, ny, nz and nx*ny*nz < 2^31 - 1 (1024^3 fits).
  * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA; *out is set to NULL on error.
  */
 int lb_create(int nx, int ny, int nz, double tau, double M, double W, double sigma,
@@ -150,7 +158,8 @@ int lb_get_tile(const lb_ctx* ctx, int* ty, int* zc);
 int lb_tune(lb_ctx* ctx, int steps);
 
 /* Algorithmic bytes moved per site per step by the fused kernel (population
- * reads and writes): 27*2*sizeof(f) + 7*2*sizeof(g). */
+ * reads and writes): 27*2*sizeof(f) + 7*2*sizeof(g), or 10*2*4 + 7*2*4 for
+ * LB_F32_MOMENTS. */
 double lb_bytes_per_site(const lb_ctx* ctx);
 
 /* Free everything the context owns.  NULL is ignored. */
@@ -185,7 +194,8 @@ typedef struct lb_batch lb_batch;
 /* count boxes; dims = count triples (nx, ny, nz); tau, M, W, sigma = count
  * values each, with the meaning and limits of lb_create.  The batch owns one
  * population array for all boxes (same storage), two D3Q7 arrays and the
- * reduction scratch.  Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA. */
+ * reduction scratch.  storage is LB_F32, LB_F16_SHIFTED or LB_BF16_SHIFTED.
+ * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA. */
 int lb_batch_create(int count, const int* dims, const double* tau, const double* M, const double* W,
                     const double* sigma, int storage, lb_batch** out);
 int lb_batch_set_stream(lb_batch* batch, void* stream);

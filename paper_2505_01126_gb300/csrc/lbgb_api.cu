@@ -109,7 +109,7 @@ struct lb_ctx {
     size_t fsize;  // bytes per stored f value
     int device;
 
-    void* f = nullptr;
+    void* f = nullptr;  // AA: 27 planes; LB_F32_MOMENTS: 2 buffers x 10 coefficient planes
     float* g[2] = {nullptr, nullptr};
     double* partials = nullptr;
     long long npart_cap = 0;
@@ -138,12 +138,17 @@ dim3 grid_for(const lb_ctx* c, int ty, int zc) {
                 (unsigned)((c->nz + zc - 1) / zc));
 }
 
+bool is_mc(const lb_ctx* c) { return c->storage == LB_F32_MOMENTS; }
+
+size_t f_bytes(const lb_ctx* c) { return (size_t)c->N * (is_mc(c) ? 20 * sizeof(float) : 27 * c->fsize); }
+
 StepArgs base_args(const lb_ctx* c) {
     StepArgs a;
     memset(&a, 0, sizeof(a));
     a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.zc = c->zc;
     a.N = (int)c->N;
-    for (int i = 0; i < 27; ++i) a.fk[i] = (char*)c->f + (size_t)i * (size_t)c->N * c->fsize;
+    if (!is_mc(c))
+        for (int i = 0; i < 27; ++i) a.fk[i] = (char*)c->f + (size_t)i * (size_t)c->N * c->fsize;
     a.force_kind = c->force.kind;
     a.omega = (float)(1.0 / c->tau);
     a.omega_phi = (float)(1.0 / (c->M / 0.25 + 0.5));
@@ -157,19 +162,30 @@ StepArgs base_args(const lb_ctx* c) {
     return a;
 }
 
-// D3Q7 plane pointers: read buffer `par`, write buffer par ^ 1.
+// D3Q7 plane pointers: read buffer `par`, write buffer par ^ 1 (and likewise
+// the coefficient buffers of the moment-only storage).
 void set_g(StepArgs& a, const lb_ctx* c, int par) {
     for (int q = 0; q < 7; ++q) {
         a.gin[q] = c->g[par] + (size_t)q * (size_t)c->N;
         a.gout[q] = c->g[par ^ 1] + (size_t)q * (size_t)c->N;
     }
+    if (is_mc(c)) {
+        float* C = static_cast<float*>(c->f);
+        for (int k = 0; k < 10; ++k) {
+            a.cin[k] = C + (size_t)(10 * par + k) * (size_t)c->N;
+            a.cout[k] = C + (size_t)(10 * (par ^ 1) + k) * (size_t)c->N;
+        }
+    }
 }
 
+// parity: AA parity (t & 1); for the moment-only storage, 1 when the state
+// at t is a set of post-collision coefficients to pull from (t > 0).
 cudaError_t launch_any(const lb_ctx* c, int mode, int parity, int ty, dim3 grid, const StepArgs& a,
                        cudaStream_t s) {
     // float4 phase-A loads need 16-byte aligned rows: nx % 4 == 0 (planes then start aligned too)
     const bool vec = (c->nx % 4) == 0;
     switch (c->storage) {
+        case LB_F32_MOMENTS: return launch_fused_mc(mode, parity, ty, vec, grid, a, s);
         case LB_F32: return launch_fused<float>(mode, parity, ty, vec, grid, a, s);
         case LB_F16_SHIFTED: return launch_fused<__half>(mode, parity, ty, vec, grid, a, s);
         case LB_BF16_SHIFTED: return launch_fused<__nv_bfloat16>(mode, parity, ty, vec, grid, a, s);
@@ -188,8 +204,10 @@ FinalizeArgs fin_args(const lb_ctx* c, int mode) {
     return fa;
 }
 
-// One time step at parity `par` on stream s (2 launches).
-int enqueue_step(lb_ctx* c, int par, cudaStream_t s) {
+// One time step at parity `par` on stream s (2 launches); `first` marks the
+// step from t = 0 of the moment-only storage, which evaluates each site's own
+// coefficients instead of pulling.
+int enqueue_step(lb_ctx* c, int par, cudaStream_t s, bool first = false) {
     StepArgs a = base_args(c);
     a.zc = c->zc;
     set_g(a, c, par);
@@ -207,7 +225,7 @@ int enqueue_step(lb_ctx* c, int par, cudaStream_t s) {
         }
         LB_CUDA(cudaEventRecord(c->ev_start[c->ev_used], s));
     }
-    LB_CUDA(launch_any(c, MODE_STEP, par, c->ty, grid, a, s));
+    LB_CUDA(launch_any(c, MODE_STEP, is_mc(c) ? (first ? 0 : 1) : par, c->ty, grid, a, s));
     if (timed) {
         LB_CUDA(cudaEventRecord(c->ev_stop[c->ev_used], s));
         c->ev_used += 1;
@@ -312,7 +330,7 @@ int lb_create(int nx, int ny, int nz, double tau, double M, double W, double sig
     if (!(W > 0)) return fail(LB_EINVAL, "W = %g must be > 0 (or +inf)", W);
     if (!(sigma >= 0) || !isfinite(sigma)) return fail(LB_EINVAL, "sigma = %g must be >= 0", sigma);
     if (isinf(W) && sigma > 0) return fail(LB_EINVAL, "sigma > 0 needs a finite W");
-    if (storage != LB_F32 && storage != LB_F16_SHIFTED && storage != LB_BF16_SHIFTED)
+    if (storage != LB_F32 && storage != LB_F16_SHIFTED && storage != LB_BF16_SHIFTED && storage != LB_F32_MOMENTS)
         return fail(LB_EINVAL, "unknown storage %d", storage);
     lb_force fz;
     memset(&fz, 0, sizeof(fz));
@@ -326,7 +344,7 @@ int lb_create(int nx, int ny, int nz, double tau, double M, double W, double sig
     c->tau = tau; c->M = M; c->W = W; c->sigma = sigma;
     c->force = fz;
     c->storage = storage;
-    c->fsize = storage == LB_F32 ? 4 : 2;
+    c->fsize = (storage == LB_F32 || storage == LB_F32_MOMENTS) ? 4 : 2;
     cudaGetDevice(&c->device);
     // default launch shape: z chunk of 32 planes, smaller for thin boxes
     c->ty = 8;
@@ -342,7 +360,7 @@ int lb_create(int nx, int ny, int nz, double tau, double M, double W, double sig
                       cudaGetErrorString(e));
         }
     };
-    alloc(&c->f, (size_t)c->N * 27 * c->fsize);
+    alloc(&c->f, f_bytes(c));
     alloc((void**)&c->g[0], (size_t)c->N * 7 * sizeof(float));
     alloc((void**)&c->g[1], (size_t)c->N * 7 * sizeof(float));
     c->npart_cap = max_blocks(c);
@@ -425,7 +443,8 @@ int lb_step(lb_ctx* c, int n) {
     if (rc) return rc;
     while (n > 0) {
         const int par = (int)(c->t & 1);
-        if (par == 0 && n >= 2 && !c->timing) {
+        const bool first = is_mc(c) && c->t == 0;
+        if (par == 0 && n >= 2 && !c->timing && !first) {
             if (!c->graph || c->graph_ty != c->ty || c->graph_zc != c->zc) {
                 rc = capture_graph(c);
                 if (rc) return rc;
@@ -435,7 +454,7 @@ int lb_step(lb_ctx* c, int n) {
             c->t += 2;
             n -= 2;
         } else {
-            rc = enqueue_step(c, par, c->stream);
+            rc = enqueue_step(c, par, c->stream, first);
             if (rc) return rc;
             c->t += 1;
             n -= 1;
@@ -462,7 +481,8 @@ int lb_moments(lb_ctx* c, float* rho, float* u, float* phi) {
     a.out_rho = hr ? c->stage : rho;
     a.out_u = hu ? c->stage + N : u;
     a.out_phi = hp ? c->stage + 4 * N : phi;
-    LB_CUDA(launch_any(c, MODE_MOMENTS, par, 8, grid_for(c, 8, a.zc), a, c->stream));
+    const int kpar = is_mc(c) ? (c->t > 0 ? 1 : 0) : par;
+    LB_CUDA(launch_any(c, MODE_MOMENTS, kpar, 8, grid_for(c, 8, a.zc), a, c->stream));
     c->launches += 1;
     if (hr) LB_CUDA(cudaMemcpyAsync(rho, c->stage, (size_t)N * sizeof(float), cudaMemcpyDefault, c->stream));
     if (hu) LB_CUDA(cudaMemcpyAsync(u, c->stage + N, (size_t)N * 3 * sizeof(float), cudaMemcpyDefault, c->stream));
@@ -531,6 +551,7 @@ int lb_get_tile(const lb_ctx* c, int* ty, int* zc) {
 
 double lb_bytes_per_site(const lb_ctx* c) {
     if (!c) return 0.0;
+    if (is_mc(c)) return 10.0 * 2.0 * 4.0 + 7.0 * 2.0 * 4.0;
     return 27.0 * 2.0 * (double)c->fsize + 7.0 * 2.0 * 4.0;
 }
 
@@ -573,7 +594,7 @@ int lb_tune(lb_ctx* c, int steps) {
     int rc = LB_OK;
     if (in_place) {
         s = c;
-        LB_CUDA(cudaMemsetAsync(c->f, 0, (size_t)c->N * 27 * c->fsize, c->stream));
+        LB_CUDA(cudaMemsetAsync(c->f, 0, f_bytes(c), c->stream));
         LB_CUDA(cudaMemsetAsync(c->g[0], 0, (size_t)c->N * 7 * sizeof(float), c->stream));
         LB_CUDA(cudaMemsetAsync(c->g[1], 0, (size_t)c->N * 7 * sizeof(float), c->stream));
         LB_CUDA(cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));

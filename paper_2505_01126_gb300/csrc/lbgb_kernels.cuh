@@ -76,6 +76,10 @@ struct StepArgs {
     float* out_phi;
     const float* in_phi;    // INIT inputs
     const float* in_u;
+    // moment-only storage: the 10 coefficients (e0, P+[3], P-[3], Xxy, Xxz, Xyz)
+    // of the post-collision polynomial f*_i/w_i - 1 of each site (see quad_poly27)
+    const float* cin[10];   // at t (written by step t-1, or by INIT at t = 0)
+    float* cout[10];        // at t+1 (INIT: at 0)
 };
 
 // ---------------------------------------------------------- storage codecs
@@ -113,6 +117,11 @@ __device__ __forceinline__ int wrap_mod(int v, int n) {
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+// 4-byte asynchronous global -> shared copy (any 4-byte aligned address).
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -250,10 +259,13 @@ __host__ __device__ __forceinline__ void quad_poly27(float e0, const float (&Pp)
 //   f*_i/w_i = p* + 3 c.u + 4.5 (c.B.c - tr B/3) + 1.5 c.F - 1.5 u.F + 4.5 (c.u)(c.F),
 //   B = u u + (1 - omega) a2.
 // Also returns a2:a2 for the dissipation estimate.
-__host__ __device__ __forceinline__ void collide_site(float pp, float m0, float m1, float m2, float P00, float P11,
-                                                      float P22, float P01, float P02, float P12, float Fe0,
-                                                      float Fe1, float Fe2, float A_lin, float omega, float& u0,
-                                                      float& u1, float& u2, float& aa, float (&v)[27]) {
+// collide_coefs stops at the ten coefficients of that polynomial (the state
+// kept by the moment-only storage); collide_site also evaluates it.
+__host__ __device__ __forceinline__ void collide_coefs(float pp, float m0, float m1, float m2, float P00, float P11,
+                                                       float P22, float P01, float P02, float P12, float Fe0,
+                                                       float Fe1, float Fe2, float A_lin, float omega, float& u0,
+                                                       float& u1, float& u2, float& aa, float& e0, float (&Pp)[3],
+                                                       float (&Pm)[3], float& Xxy, float& Xxz, float& Xyz) {
     const float inv = 1.f / (1.f - 0.5f * A_lin);
     u0 = fmaf(0.5f, Fe0, m0) * inv;
     u1 = fmaf(0.5f, Fe1, m1) * inv;
@@ -273,15 +285,62 @@ __host__ __device__ __forceinline__ void collide_site(float pp, float m0, float 
     const float B22 = fmaf(om1, a22, u2 * u2), B01 = fmaf(om1, a01, u0 * u1);
     const float B02 = fmaf(om1, a02, u0 * u2), B12 = fmaf(om1, a12, u1 * u2);
     const float uF = u0 * F0 + u1 * F1 + u2 * F2;
-    const float e0 = pp - 1.5f * (B00 + B11 + B22 + uF);
+    e0 = pp - 1.5f * (B00 + B11 + B22 + uF);
     const float L0 = fmaf(1.5f, F0, 3.f * u0), L1 = fmaf(1.5f, F1, 3.f * u1), L2 = fmaf(1.5f, F2, 3.f * u2);
     const float Q0 = 4.5f * fmaf(u0, F0, B00), Q1 = 4.5f * fmaf(u1, F1, B11), Q2 = 4.5f * fmaf(u2, F2, B22);
-    const float Pp[3] = {Q0 + L0, Q1 + L1, Q2 + L2};
-    const float Pm[3] = {Q0 - L0, Q1 - L1, Q2 - L2};
-    const float Xxy = fmaf(9.f, B01, 4.5f * (u0 * F1 + u1 * F0));
-    const float Xxz = fmaf(9.f, B02, 4.5f * (u0 * F2 + u2 * F0));
-    const float Xyz = fmaf(9.f, B12, 4.5f * (u1 * F2 + u2 * F1));
+    Pp[0] = Q0 + L0; Pp[1] = Q1 + L1; Pp[2] = Q2 + L2;
+    Pm[0] = Q0 - L0; Pm[1] = Q1 - L1; Pm[2] = Q2 - L2;
+    Xxy = fmaf(9.f, B01, 4.5f * (u0 * F1 + u1 * F0));
+    Xxz = fmaf(9.f, B02, 4.5f * (u0 * F2 + u2 * F0));
+    Xyz = fmaf(9.f, B12, 4.5f * (u1 * F2 + u2 * F1));
+}
+
+__host__ __device__ __forceinline__ void collide_site(float pp, float m0, float m1, float m2, float P00, float P11,
+                                                      float P22, float P01, float P02, float P12, float Fe0,
+                                                      float Fe1, float Fe2, float A_lin, float omega, float& u0,
+                                                      float& u1, float& u2, float& aa, float (&v)[27]) {
+    float e0, Pp[3], Pm[3], Xxy, Xxz, Xyz;
+    collide_coefs(pp, m0, m1, m2, P00, P11, P22, P01, P02, P12, Fe0, Fe1, Fe2, A_lin, omega, u0, u1, u2, aa, e0, Pp,
+                  Pm, Xxy, Xxz, Xyz);
     quad_poly27(e0, Pp, Pm, Xxy, Xxz, Xyz, v);
+}
+
+// One pulled column of the moment-only storage: the three directions
+// (cx, cy, -1), (cx, cy, 0), (cx, cy, +1) of the post-collision polynomial of
+// a source site whose ten coefficients are read through ld(k), k in the order
+// e0, P+x, P+y, P+z, P-x, P-y, P-z, Xxy, Xxz, Xyz.  Each value is formed by
+// the same sequence of FP32 additions as in quad_poly27, so it equals, bit for
+// bit, the population the AA storage would have stored and reloaded.
+template <int CX, int CY, class LD>
+__device__ __forceinline__ void pull_column(LD ld, float& vm, float& v0, float& vp) {
+    const float e0 = ld(0);
+    const float Pp2 = ld(3), Pm2 = ld(6);
+    if (CX == 0 && CY == 0) {
+        v0 = e0;
+        vp = e0 + Pp2;
+        vm = e0 + Pm2;
+    } else if (CY == 0) {  // x face: fx = e0 + P(cx)_x; z term cx*cz*Xxz
+        const float fx = e0 + (CX > 0 ? ld(1) : ld(4));
+        const float X = ld(8);
+        v0 = fx;
+        vp = fx + (CX > 0 ? Pp2 + X : Pp2 - X);
+        vm = fx + (CX > 0 ? Pm2 - X : Pm2 + X);
+    } else if (CX == 0) {  // y face: fy = e0 + P(cy)_y; z term cy*cz*Xyz
+        const float fy = e0 + (CY > 0 ? ld(2) : ld(5));
+        const float X = ld(9);
+        v0 = fy;
+        vp = fy + (CY > 0 ? Pp2 + X : Pp2 - X);
+        vm = fy + (CY > 0 ? Pm2 - X : Pm2 + X);
+    } else {  // xy edge e = fx + (P(cy)_y +- Xxy); corners add cz (cx Xxz + cy Xyz)
+        const float fx = e0 + (CX > 0 ? ld(1) : ld(4));
+        const float Xxy = ld(7), Xxz = ld(8), Xyz = ld(9);
+        const float Py = CY > 0 ? ld(2) : ld(5);
+        const float e = fx + (CX * CY > 0 ? Py + Xxy : Py - Xxy);
+        const float V = CX == CY ? Xxz + Xyz : Xxz - Xyz;  // Vpp or Vpm of quad_poly27
+        v0 = e;
+        vp = e + (CX > 0 ? Pp2 + V : Pp2 - V);
+        vm = e + (CX > 0 ? Pm2 - V : Pm2 + V);
+    }
 }
 
 // ------------------------------------------------------------ fused kernel
@@ -297,7 +356,12 @@ __host__ __device__ __forceinline__ void collide_site(float pp, float m0, float 
 // multiple of 4, as float4 quads of 4 consecutive sites covering the halo row
 // x0-4 .. x0+TX+3 (VEC = true): 7 vector loads per 4 sites.
 // One box: a block per (32 x TY tile, z-chunk).
-template <class FT, int TY, int MODE, int PAR, bool VEC>
+// MC selects the moment-only storage: f is not stored; each site keeps the
+// ten coefficients of its post-collision polynomial and the next step pulls
+// f_i(x) = w_i (1 + v_i(x - c_i)) from the neighbours' coefficients.  With MC,
+// PAR = 0 evaluates the site's own coefficients (t = 0, where lb_init stored
+// those of f^eq) and PAR = 1 pulls; FT is float.
+template <class FT, int TY, int MODE, int PAR, bool VEC, bool MC = false>
 __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 512 / (32 * TY)))
 fused_step_kernel(const StepArgs a) {
 #define TILE_BX blockIdx.x
@@ -379,6 +443,7 @@ batch_step_kernel(const __grid_constant__ BatchArgs b) {
         {
             const BoxTileArgs<FT>& a = t;
             constexpr int MODE = MODE_STEP;
+            constexpr bool MC = false;
 #define TILE_BX tbx
 #define TILE_BY tby
 #define TILE_BZ tbz
@@ -396,6 +461,11 @@ batch_step_kernel(const __grid_constant__ BatchArgs b) {
 // Launch one fused kernel instance.  Defined per storage type in lbgb_step_*.cu.
 // Records a message for lb_last_error() (defined with the C ABI).
 void set_last_error(const char* msg);
+
+// One launch of the moment-only storage kernel: mode INIT, MOMENTS or STEP;
+// pull = 0 evaluates each site's own coefficients (the state lb_init leaves),
+// pull = 1 rebuilds f from the neighbours' coefficients.
+cudaError_t launch_fused_mc(int mode, int pull, int ty, bool vec, dim3 grid, const StepArgs& a, cudaStream_t st);
 
 // One step of every box of a batch (persistent grid of `blocks` blocks).
 template <class FT>

@@ -1,0 +1,38 @@
+// Moment-only storage: launcher of the fused kernel with MC = true (the f
+// populations are rebuilt from the neighbours' ten post-collision
+// coefficients; FP32 throughout).
+#include "lbgb_kernels.cuh"
+
+namespace lbgb {
+
+template <int TY, int MODE, bool VEC>
+static void launch_mc_kernel(int pull, dim3 grid, const StepArgs& a, cudaStream_t st) {
+    if (pull) fused_step_kernel<float, TY, MODE, 1, VEC, true><<<grid, 32 * TY, 0, st>>>(a);
+    else fused_step_kernel<float, TY, MODE, 0, VEC, true><<<grid, 32 * TY, 0, st>>>(a);
+}
+
+cudaError_t launch_fused_mc(int mode, int pull, int ty, bool vec, dim3 grid, const StepArgs& a, cudaStream_t st) {
+    if (mode == MODE_INIT) {
+        if (ty != 8) return cudaErrorInvalidValue;
+        fused_step_kernel<float, 8, MODE_INIT, 0, false, true><<<grid, 256, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    if (mode == MODE_MOMENTS) {
+        if (ty != 8) return cudaErrorInvalidValue;
+        launch_mc_kernel<8, MODE_MOMENTS, false>(pull, grid, a, st);
+        return cudaGetLastError();
+    }
+    if (mode != MODE_STEP) return cudaErrorInvalidValue;
+    if (ty == 4) {
+        if (vec) launch_mc_kernel<4, MODE_STEP, true>(pull, grid, a, st);
+        else launch_mc_kernel<4, MODE_STEP, false>(pull, grid, a, st);
+    } else if (ty == 8) {
+        if (vec) launch_mc_kernel<8, MODE_STEP, true>(pull, grid, a, st);
+        else launch_mc_kernel<8, MODE_STEP, false>(pull, grid, a, st);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbgb

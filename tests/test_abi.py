@@ -61,6 +61,12 @@ def test_create_rejects_bad_storage_and_force(lbgb):
     assert e.value.code == lbgb.LB_EINVAL
 
 
+def test_batch_rejects_moment_only_storage(lbgb):
+    with pytest.raises(lbgb.LBError) as e:
+        lbgb.Batch([(8, 8, 8)], 1.0, 0.1, 3.0, 0.01, storage="moments")
+    assert e.value.code == lbgb.LB_EINVAL
+
+
 def test_null_context_calls_fail_cleanly(lbgb):
     lib = lbgb.lib()
     assert lib.lb_step(None, 1) == lbgb.LB_EINVAL
