@@ -90,20 +90,31 @@ struct StepArgs {
 template <class T>
 struct Codec;
 
+// ldr loads the stored value as is and dec widens it to FP32, so that a load
+// can be issued well ahead of the conversion that waits for it.
 template <>
 struct Codec<float> {
+    using raw = float;
+    static __device__ __forceinline__ raw ldr(const float* p) { return *p; }
+    static __device__ __forceinline__ float dec(raw r) { return r; }
     static __device__ __forceinline__ float ld(const float* p) { return *p; }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 };
 
 template <>
 struct Codec<__half> {
+    using raw = __half;
+    static __device__ __forceinline__ raw ldr(const __half* p) { return *p; }
+    static __device__ __forceinline__ float dec(raw r) { return __half2float(r); }
     static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 };
 
 template <>
 struct Codec<__nv_bfloat16> {
+    using raw = __nv_bfloat16;
+    static __device__ __forceinline__ raw ldr(const __nv_bfloat16* p) { return *p; }
+    static __device__ __forceinline__ float dec(raw r) { return __bfloat162float(r); }
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
