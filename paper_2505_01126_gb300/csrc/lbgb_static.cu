@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(ST_NT) field_stats_kernel(const float* __restr
     if (gx < nx && gy < ny) {
         for (int z = z0; z < z1; ++z) {
             const int s = (z * ny + gy) * nx + gx;
-            const float u0 = u[s], u1 = u[N + s], u2 = u[2 * N + s];
+            const float u0 = u[s], u1 = (u + N)[s], u2 = (u + 2 * (long long)N)[s];
             const float uu = u0 * u0 + u1 * u1 + u2 * u2;
             s_phi += phi[s];
             s_K = fmaf(0.5f, uu, s_K);
