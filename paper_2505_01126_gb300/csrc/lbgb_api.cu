@@ -284,6 +284,56 @@ int check_tile(int ty, int zc) {
     return LB_OK;
 }
 
+// Z-chunks the tuner times for tile height ty: 16, 32, 64 and 128 planes
+// (those that give distinct launches), plus the two chunkings whose block
+// count best fills the last wave of resident blocks (at least 24 planes each,
+// so the chunk prologue stays small).  Returns how many were written to zcs.
+int tune_chunks(const lb_ctx* c, int ty, int zcs[6]) {
+    int n = 0;
+    const int fixed[4] = {16, 32, 64, 128};
+    for (int b = 0; b < 4; ++b) {
+        if (b > 0 && fixed[b - 1] >= c->nz) break;  // larger chunks clamp to the same launch
+        zcs[n++] = fixed[b];
+    }
+    const bool vec = (c->nx % 4) == 0;
+    int per_sm = 0;
+    switch (c->storage) {
+        case LB_F32: per_sm = fused_blocks_per_sm<float>(ty, vec); break;
+        case LB_F16_SHIFTED: per_sm = fused_blocks_per_sm<__half>(ty, vec); break;
+        case LB_BF16_SHIFTED: per_sm = fused_blocks_per_sm<__nv_bfloat16>(ty, vec); break;
+        case LB_F32_MOMENTS: per_sm = fused_mc_blocks_per_sm(ty, vec); break;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 0;
+    }
+    const long long resident = (long long)sms * per_sm;
+    if (resident <= 0) return n;
+    const long long tiles = (long long)((c->nx + 31) / 32) * ((c->ny + ty - 1) / ty);
+    double fill[2] = {0.0, 0.0};
+    int pick[2] = {0, 0};
+    for (int nc = (c->nz + 127) / 128; nc <= c->nz / 24; ++nc) {
+        const int zc = (c->nz + nc - 1) / nc;
+        if ((c->nz + zc - 1) / zc != nc) continue;  // this chunking is reached by another zc
+        const long long blocks = tiles * nc;
+        const long long waves = (blocks + resident - 1) / resident;
+        const double f = (double)blocks / (double)(waves * resident);
+        if (f > fill[0]) {
+            fill[1] = fill[0]; pick[1] = pick[0];
+            fill[0] = f; pick[0] = zc;
+        } else if (f > fill[1]) {
+            fill[1] = f; pick[1] = zc;
+        }
+    }
+    for (int k = 0; k < 2; ++k) {
+        bool dup = pick[k] == 0;
+        for (int j = 0; j < n && !dup; ++j) dup = zcs[j] == pick[k];
+        if (!dup) zcs[n++] = pick[k];
+    }
+    return n;
+}
+
 long long max_blocks(const lb_ctx* c) {
     // the smallest tile (ty = 4) with zc = 1 bounds every configuration
     return (long long)((c->nx + 31) / 32) * ((c->ny + 3) / 4) * c->nz;
@@ -618,12 +668,12 @@ int lb_tune(lb_ctx* c, int steps) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int tys[2] = {4, 8};
-    const int zcs[4] = {16, 32, 64, 128};
     float best = 1e30f;
     int bty = c->ty, bzc = c->zc;
-    for (int a = 0; a < 2 && rc == LB_OK; ++a)
-        for (int b = 0; b < 4 && rc == LB_OK; ++b) {
-            if (b > 0 && zcs[b - 1] >= nzt) continue;  // larger chunks clamp to the same launch
+    for (int a = 0; a < 2 && rc == LB_OK; ++a) {
+        int zcs[6];
+        const int nzc = tune_chunks(s, tys[a], zcs);
+        for (int b = 0; b < nzc && rc == LB_OK; ++b) {
             if (lb_set_tile(s, tys[a], zcs[b]) != LB_OK) continue;
             if (lb_step(s, 2) != LB_OK) {  // warm-up and graph capture; skip shapes that fail
                 cudaGetLastError();
@@ -645,6 +695,7 @@ int lb_tune(lb_ctx* c, int steps) {
                 bzc = zcs[b];
             }
         }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (in_place) {

@@ -473,6 +473,11 @@ batch_step_kernel(const __grid_constant__ BatchArgs b) {
 // Records a message for lb_last_error() (defined with the C ABI).
 void set_last_error(const char* msg);
 
+// Resident blocks per SM of the single-box STEP kernel (0 if unknown).
+template <class FT>
+int fused_blocks_per_sm(int ty, bool vec);
+int fused_mc_blocks_per_sm(int ty, bool vec);
+
 // One launch of the moment-only storage kernel: mode INIT, MOMENTS or STEP;
 // pull = 0 evaluates each site's own coefficients (the state lb_init leaves),
 // pull = 1 rebuilds f from the neighbours' coefficients.

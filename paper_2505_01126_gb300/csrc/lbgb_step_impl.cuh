@@ -41,6 +41,23 @@ cudaError_t launch_fused<LBGB_FT>(int mode, int parity, int ty, bool vec, dim3 g
     }
 }
 
+template <>
+int fused_blocks_per_sm<LBGB_FT>(int ty, bool vec) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (ty == 4)
+        e = vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_step_kernel<LBGB_FT, 4, MODE_STEP, 1, true>, 128, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_step_kernel<LBGB_FT, 4, MODE_STEP, 1, false>, 128, 0);
+    else if (ty == 8)
+        e = vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_step_kernel<LBGB_FT, 8, MODE_STEP, 1, true>, 256, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_step_kernel<LBGB_FT, 8, MODE_STEP, 1, false>, 256, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
 template <class FT, int TY, bool VEC>
 static cudaError_t launch_batch_ty(int parity, int blocks, const BatchArgs& b, cudaStream_t st) {
     if (parity == 0) batch_step_kernel<FT, TY, 0, VEC><<<blocks, 32 * TY, 0, st>>>(b);

@@ -35,4 +35,20 @@ cudaError_t launch_fused_mc(int mode, int pull, int ty, bool vec, dim3 grid, con
     return cudaGetLastError();
 }
 
+int fused_mc_blocks_per_sm(int ty, bool vec) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (ty == 4)
+        e = vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_step_kernel<float, 4, MODE_STEP, 1, true, true>, 128, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_step_kernel<float, 4, MODE_STEP, 1, false, true>, 128, 0);
+    else if (ty == 8)
+        e = vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_step_kernel<float, 8, MODE_STEP, 1, true, true>, 256, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_step_kernel<float, 8, MODE_STEP, 1, false, true>, 256, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
 }  // namespace lbgb
