@@ -87,9 +87,10 @@ def whole_job(ms_local: float, sites_per_rank: int, steps: int, world: int, dist
     return sites_per_rank * steps * world / (t_max * 1e-3) / 1e6, t_max
 
 
-def measured_traffic(storage: str, n_sites: int):
+def measured_traffic(storage: str, n_sites: int, tile=None):
     """DRAM bytes per fused-kernel launch from the committed ncu record, scaled to
-    n_sites, or None if the kernel sources changed since the capture."""
+    n_sites, or None if the kernel sources changed since the capture or the
+    capture was taken in another launch shape."""
     try:
         import hashlib
 
@@ -101,7 +102,10 @@ def measured_traffic(storage: str, n_sites: int):
                 h.update(f.read())
         if h.hexdigest() != rec["kernel_sources_sha256"] or storage not in rec["captures"]:
             return None
-        return rec["captures"][storage]["bytes_per_site"] * n_sites
+        cap = rec["captures"][storage]
+        if tile is not None and list(cap["tile"]) != list(tile):
+            return None
+        return cap["bytes_per_site"] * n_sites
     except Exception:
         return None
 
@@ -406,7 +410,7 @@ def main():
         kern_avg_s = kern_ms / max(kern_n, 1) * 1e-3
         achieved = bps * N / kern_avg_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": measured_traffic(args.storage, N), "kernel": "fused_step_kernel", "bytes_per_site": bps,
+                "traffic": measured_traffic(args.storage, N, [32, ty, zc]), "kernel": "fused_step_kernel", "bytes_per_site": bps,
                 "kernel_ms_avg": kern_avg_s * 1e3, "peak_source": peak_kind}
         cpu = None
         if not args.no_cpu_baseline and world == 1:
