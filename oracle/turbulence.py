@@ -1,0 +1,91 @@
+"""FP64 oracle of the velocity statistics of homogeneous isotropic turbulence
+(Sec. 5.1: the PDF of the longitudinal velocity gradient with its skewness S
+and flatness F, and the second- and third-order structure functions).
+
+TEST INFRASTRUCTURE, like the rest of this package: plain numpy, written out
+from the definitions, sharing nothing with the CUDA library.
+
+Definitions (readings of Sec. 5.1, which defines S, F, S_2 and S_3 but not
+the discretisation or the sampling):
+- Longitudinal gradient samples: g = d_a u_a for a = x, y, z at every site
+  (3N samples of a periodic nx*ny*nz field), with the lattice gradient of
+  Sec. 2.3, (1/cs^2) sum_i w_i c_ia psi(x + c_i).  Using the factorisation of
+  the D3Q27 weights this is (1/72) sum over the two transverse offsets of
+  k(c) k(c') [psi(+1) - psi(-1)], k = (1, 4, 1); the sums are taken in the
+  order written in `longitudinal_gradients`, which the device code follows.
+- Moments M_n = mean of g^n (n = 2, 3, 4); S = M3 / M2^(3/2), F = M4 / M2^2.
+- Histogram of g / scale over nbins equal bins on [-range, range): bin
+  floor((g/scale + range) * (nbins / (2 range))), with counts below and above.
+- Longitudinal structure functions S_n(r) = mean over a and sites of
+  (u_a(x + r e_a) - u_a(x))^n, n = 2, 3, periodic.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# array axes of a (nz, ny, nx) field for the Cartesian directions x, y, z
+_AX = {0: 2, 1: 1, 2: 0}
+
+
+def _shift(f: np.ndarray, axis: int, c: int) -> np.ndarray:
+    """psi(x + c e_axis) on the periodic grid."""
+    return np.roll(f, -c, axis=axis)
+
+
+def longitudinal_gradients(u: np.ndarray) -> np.ndarray:
+    """d_a u_a for a = x, y, z: array (3, nz, ny, nx), FP64.
+
+    For each a, with t1 < t2 the two transverse directions:
+      d(c1, c2) = u_a(x + e_a + c1 e_t1 + c2 e_t2) - u_a(x - e_a + c1 e_t1 + c2 e_t2)
+      e(c2)     = (d(-1, c2) + d(+1, c2)) + 4 d(0, c2)
+      g         = ((e(-1) + e(+1)) + 4 e(0)) / 72
+    """
+    u = np.asarray(u, dtype=np.float64)
+    out = np.empty_like(u)
+    for a in range(3):
+        ua = u[a]
+        ax = _AX[a]
+        t1, t2 = [_AX[t] for t in range(3) if t != a]
+        d = _shift(ua, ax, 1) - _shift(ua, ax, -1)
+        e = {}
+        for c2 in (-1, 0, 1):
+            dc = _shift(d, t2, c2)
+            e[c2] = (_shift(dc, t1, -1) + _shift(dc, t1, 1)) + 4.0 * dc
+        out[a] = ((e[-1] + e[1]) + 4.0 * e[0]) / 72.0
+    return out
+
+
+def gradient_moments(u: np.ndarray) -> dict:
+    g = longitudinal_gradients(u).ravel()
+    g2 = g * g
+    m2, m3, m4 = g2.mean(), (g2 * g).mean(), (g2 * g2).mean()
+    return {"M2": m2, "M3": m3, "M4": m4, "S": m3 / m2 ** 1.5, "F": m4 / (m2 * m2), "samples": g.size}
+
+
+def gradient_histogram(u: np.ndarray, nbins: int, rng: float, scale: float) -> np.ndarray:
+    """Counts (nbins + 2 integers): the nbins bins, then below and above."""
+    g = longitudinal_gradients(u).ravel()
+    f = nbins / (2.0 * rng)
+    b = np.floor((g / scale + rng) * f)
+    out = np.zeros(nbins + 2, dtype=np.int64)
+    inside = (b >= 0) & (b < nbins)
+    np.add.at(out, b[inside].astype(np.int64), 1)
+    out[nbins] = int((b < 0).sum())
+    out[nbins + 1] = int((b >= nbins).sum())
+    return out
+
+
+def structure_functions(u: np.ndarray, rmax: int) -> tuple[np.ndarray, np.ndarray]:
+    """(S_2(r), S_3(r)) for r = 1 .. rmax."""
+    u = np.asarray(u, dtype=np.float64)
+    s2 = np.zeros(rmax)
+    s3 = np.zeros(rmax)
+    for r in range(1, rmax + 1):
+        acc2 = acc3 = 0.0
+        for a in range(3):
+            d = _shift(u[a], _AX[a], r) - u[a]
+            acc2 += (d * d).sum()
+            acc3 += (d * d * d).sum()
+        s2[r - 1] = acc2 / (3 * u[0].size)
+        s3[r - 1] = acc3 / (3 * u[0].size)
+    return s2, s3

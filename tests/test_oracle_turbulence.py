@@ -1,0 +1,99 @@
+"""Pins of the turbulence-statistics oracle (oracle/turbulence.py, Sec. 5.1)
+against closed forms and brute force, independent of the oracle's own code.
+
+Closed forms: for u_a = A_a sin(k_a x_a + p_a) (each component a function of
+its own coordinate) with k_a = 2 pi m_a / n_a, the lattice gradient is
+d_a u_a = A_a sin(k_a) cos(k_a x_a + p_a) exactly, so over the 3N samples
+M2 = (1/3) sum_a A_a^2 sin^2(k_a) / 2, M3 = 0, M4 = (1/3) sum_a A_a^4 sin^4(k_a) 3/8
+(full periods, 4 m_a not a multiple of n_a), and
+S_2(r) = (1/3) sum_a A_a^2 (1 - cos k_a r), S_3(r) = 0.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import turbulence as T
+
+
+def mode_field(n, m, A, p):
+    nz, ny, nx = n
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    coords = (x, y, z)
+    ns = (nx, ny, nz)
+    u = np.zeros((3,) + n)
+    for a in range(3):
+        u[a] = A[a] * np.sin(2 * math.pi * m[a] / ns[a] * coords[a] + p[a])
+    return u
+
+
+@pytest.mark.parametrize("n,m", [((24, 20, 16), (3, 2, 5)), ((9, 14, 11), (1, 3, 2))])
+def test_single_mode_closed_forms(n, m):
+    nz, ny, nx = n
+    ns = (nx, ny, nz)
+    A, p = (0.02, 0.013, 0.007), (0.3, 1.1, -0.7)
+    u = mode_field(n, m, A, p)
+    k = [2 * math.pi * m[a] / ns[a] for a in range(3)]
+    mo = T.gradient_moments(u)
+    m2 = sum(A[a] ** 2 * math.sin(k[a]) ** 2 / 2 for a in range(3)) / 3
+    m4 = sum(A[a] ** 4 * math.sin(k[a]) ** 4 * 3 / 8 for a in range(3)) / 3
+    assert mo["M2"] == pytest.approx(m2, rel=1e-12)
+    assert mo["M4"] == pytest.approx(m4, rel=1e-12)
+    assert abs(mo["M3"]) < 1e-12 * m2 ** 1.5
+    s2, s3 = T.structure_functions(u, 6)
+    for r in range(1, 7):
+        want = sum(A[a] ** 2 * (1 - math.cos(k[a] * r)) for a in range(3)) / 3
+        assert s2[r - 1] == pytest.approx(want, rel=1e-12, abs=1e-18)
+        assert abs(s3[r - 1]) < 1e-12 * max(want, 1e-12) ** 1.5
+
+
+def test_gradient_is_the_lattice_stencil_by_brute_force():
+    """(1/cs^2) sum over the 27 D3Q27 directions of w_i c_ia u_a(x + c_i), looped."""
+    rng = np.random.default_rng(5)
+    n = (4, 5, 6)
+    u = rng.standard_normal((3,) + n)
+    w1 = {-1: 1 / 6, 0: 2 / 3, 1: 1 / 6}
+    g = T.longitudinal_gradients(u)
+    nz, ny, nx = n
+    for a in range(3):
+        for z, y, x in itertools.product(range(nz), range(ny), range(nx)):
+            acc = 0.0
+            for cx, cy, cz in itertools.product((-1, 0, 1), repeat=3):
+                c = (cx, cy, cz)
+                acc += w1[cx] * w1[cy] * w1[cz] * c[a] * u[a][(z + cz) % nz, (y + cy) % ny, (x + cx) % nx]
+            assert g[a, z, y, x] == pytest.approx(3.0 * acc, abs=1e-14)
+
+
+def test_structure_functions_by_brute_force():
+    rng = np.random.default_rng(6)
+    n = (5, 4, 7)
+    u = rng.standard_normal((3,) + n)
+    s2, s3 = T.structure_functions(u, 4)
+    nz, ny, nx = n
+    ns = (nx, ny, nz)
+    for r in range(1, 5):
+        a2 = a3 = 0.0
+        for a in range(3):
+            for z, y, x in itertools.product(range(nz), range(ny), range(nx)):
+                q = [x, y, z]
+                q[a] = (q[a] + r) % ns[a]
+                d = u[a][q[2], q[1], q[0]] - u[a][z, y, x]
+                a2 += d ** 2
+                a3 += d ** 3
+        assert s2[r - 1] == pytest.approx(a2 / (3 * u[0].size), rel=1e-12)
+        assert s3[r - 1] == pytest.approx(a3 / (3 * u[0].size), rel=1e-10, abs=1e-14)
+
+
+def test_histogram_counts():
+    u = np.zeros((3, 6, 5, 4))
+    h = T.gradient_histogram(u, 10, 5.0, 1.0)
+    assert h.sum() == 3 * u[0].size
+    assert h[5] == 3 * u[0].size  # g = 0 falls in bin floor(5 * 10 / 10) = 5
+    rng = np.random.default_rng(7)
+    u = rng.standard_normal((3, 6, 5, 4))
+    g = T.longitudinal_gradients(u).ravel()
+    h = T.gradient_histogram(u, 8, 1.0, float(np.sqrt((g * g).mean())))
+    assert h.sum() == g.size
+    sig = np.sqrt((g * g).mean())
+    assert h[8] == int((g / sig < -1.0).sum()) and h[9] == int((g / sig >= 1.0).sum())
