@@ -15,7 +15,11 @@ the discretisation or the sampling):
   order written in `longitudinal_gradients`, which the device code follows.
 - Moments M_n = mean of g^n (n = 2, 3, 4); S = M3 / M2^(3/2), F = M4 / M2^2.
 - Histogram of g / scale over nbins equal bins on [-range, range): bin
-  floor((g/scale + range) * (nbins / (2 range))), with counts below and above.
+  floor((g * (1/scale) + range) * (nbins / (2 range))) in FP64, with counts
+  below and above.  A bin is an integer decided by floating point, so it is
+  decided from the samples in the precision the device computes them in:
+  FP32, with every operation of the stencil rounded on its own
+  (`longitudinal_gradients(u, np.float32)`).
 - Longitudinal structure functions S_n(r) = mean over a and sites of
   (u_a(x + r e_a) - u_a(x))^n, n = 2, 3, periodic.
 """
@@ -32,15 +36,17 @@ def _shift(f: np.ndarray, axis: int, c: int) -> np.ndarray:
     return np.roll(f, -c, axis=axis)
 
 
-def longitudinal_gradients(u: np.ndarray) -> np.ndarray:
-    """d_a u_a for a = x, y, z: array (3, nz, ny, nx), FP64.
+def longitudinal_gradients(u: np.ndarray, dtype=np.float64) -> np.ndarray:
+    """d_a u_a for a = x, y, z: array (3, nz, ny, nx) in `dtype` (FP64, or FP32
+    with each operation rounded to FP32, as the device evaluates it).
 
     For each a, with t1 < t2 the two transverse directions:
       d(c1, c2) = u_a(x + e_a + c1 e_t1 + c2 e_t2) - u_a(x - e_a + c1 e_t1 + c2 e_t2)
       e(c2)     = (d(-1, c2) + d(+1, c2)) + 4 d(0, c2)
       g         = ((e(-1) + e(+1)) + 4 e(0)) / 72
     """
-    u = np.asarray(u, dtype=np.float64)
+    u = np.asarray(u, dtype=dtype)
+    four, c72 = dtype(4.0), dtype(72.0)
     out = np.empty_like(u)
     for a in range(3):
         ua = u[a]
@@ -50,8 +56,8 @@ def longitudinal_gradients(u: np.ndarray) -> np.ndarray:
         e = {}
         for c2 in (-1, 0, 1):
             dc = _shift(d, t2, c2)
-            e[c2] = (_shift(dc, t1, -1) + _shift(dc, t1, 1)) + 4.0 * dc
-        out[a] = ((e[-1] + e[1]) + 4.0 * e[0]) / 72.0
+            e[c2] = (_shift(dc, t1, -1) + _shift(dc, t1, 1)) + four * dc
+        out[a] = ((e[-1] + e[1]) + four * e[0]) / c72
     return out
 
 
@@ -64,9 +70,9 @@ def gradient_moments(u: np.ndarray) -> dict:
 
 def gradient_histogram(u: np.ndarray, nbins: int, rng: float, scale: float) -> np.ndarray:
     """Counts (nbins + 2 integers): the nbins bins, then below and above."""
-    g = longitudinal_gradients(u).ravel()
+    g = longitudinal_gradients(u, np.float32).ravel().astype(np.float64)
     f = nbins / (2.0 * rng)
-    b = np.floor((g / scale + rng) * f)
+    b = np.floor((g * (1.0 / scale) + rng) * f)
     out = np.zeros(nbins + 2, dtype=np.int64)
     inside = (b >= 0) & (b < nbins)
     np.add.at(out, b[inside].astype(np.int64), 1)

@@ -93,7 +93,21 @@ def test_histogram_counts():
     rng = np.random.default_rng(7)
     u = rng.standard_normal((3, 6, 5, 4))
     g = T.longitudinal_gradients(u).ravel()
-    h = T.gradient_histogram(u, 8, 1.0, float(np.sqrt((g * g).mean())))
+    sig = float(np.sqrt((g * g).mean()))
+    h = T.gradient_histogram(u, 8, 1.0, sig)
     assert h.sum() == g.size
-    sig = np.sqrt((g * g).mean())
     assert h[8] == int((g / sig < -1.0).sum()) and h[9] == int((g / sig >= 1.0).sum())
+    # bin b holds -1 + b/4 <= g/sig < -1 + (b+1)/4 (no sample of this field sits within FP32 rounding of an edge)
+    for b in range(8):
+        assert h[b] == int(((g / sig >= -1 + b / 4) & (g / sig < -1 + (b + 1) / 4)).sum())
+
+
+def test_fp32_gradients_follow_the_fp64_ones():
+    """The FP32 evaluation that decides histogram bins stays within FP32
+    rounding of the FP64 gradient (a few ulps of the largest stencil term)."""
+    rng = np.random.default_rng(8)
+    u = rng.standard_normal((3, 7, 6, 5)).astype(np.float32)
+    g64 = T.longitudinal_gradients(u.astype(np.float64))
+    g32 = T.longitudinal_gradients(u, np.float32)
+    assert g32.dtype == np.float32
+    assert float(np.abs(g32 - g64).max()) < 1e-6 * float(np.abs(u).max())
