@@ -167,6 +167,35 @@ double lb_bytes_per_site(const lb_ctx* ctx);
 /* Free everything the context owns.  NULL is ignored. */
 void lb_destroy(lb_ctx* ctx);
 
+/*
+ * lb_velocity_statistics -- statistics of homogeneous isotropic turbulence
+ * (Sec. 5.1) of a periodic velocity field, computed on the device.
+ *   u        device array of 3N floats, planes u_x | u_y | u_z (the layout
+ *            lb_moments writes), N = nx*ny*nz < 2^31 - 1; caller-owned, read only
+ *   rmax     structure functions for r = 1 .. rmax (0: none; at most 65535)
+ *   nbins    histogram bins (0: no histogram; at most 8192)
+ *   range    histogram range [-range, range) in units of `scale` (> 0 if nbins > 0)
+ *   scale    bin unit: > 0 as given, <= 0 the RMS gradient sqrt(M2)
+ *   stream   cudaStream_t (NULL: legacy default stream); the call returns
+ *            when its results are on the host
+ *   out      host, 3 + 2*rmax doubles: M2, M3, M4, then S_2(1..rmax), then
+ *            S_3(1..rmax)
+ *   hist     host, nbins + 2 counts (NULL allowed when nbins == 0): the bins,
+ *            then the samples below and above the range
+ * The samples are the longitudinal gradients g = d_a u_a, a = x, y, z, at
+ * every site (3N samples), with the lattice gradient of Sec. 2.3 evaluated in
+ * FP32 with each operation rounded on its own; M_n is the mean of g^n (FP32
+ * per-thread sums, FP64 across threads), so the skewness is M3 / M2^(3/2) and
+ * the flatness M4 / M2^2.  Sample g falls in bin
+ * floor((g * (1/scale) + range) * (nbins / (2 range))), evaluated in FP64.
+ * S_n(r) is the mean over a and sites of (u_a(x + r e_a) - u_a(x))^n (FP32
+ * differences and per-thread sums, FP64 across threads).  Scratch memory is
+ * allocated and freed here.
+ * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA.
+ */
+int lb_velocity_statistics(const float* u, int nx, int ny, int nz, int rmax, int nbins, double range, double scale,
+                           void* stream, double* out, unsigned long long* hist);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* lb_last_error(void);
 

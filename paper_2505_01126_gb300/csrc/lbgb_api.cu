@@ -663,7 +663,6 @@ int lb_tune(lb_ctx* c, int steps) {
         cudaMemsetAsync(z, 0, (size_t)s->N * 4 * sizeof(float), c->stream);
         rc = lb_init(s, z, z + s->N);
     }
-    const int nzt = s->nz;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

@@ -40,7 +40,7 @@ EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_step", "lb_moments", "lb
            "lb_destroy", "lb_last_error", "lb_launch_count", "lb_set_timing", "lb_kernel_time",
            "lb_field_stats_static", "lb_batch_create", "lb_batch_set_stream", "lb_batch_init",
            "lb_batch_step", "lb_batch_moments", "lb_batch_diagnostics", "lb_batch_set_tile", "lb_batch_get_tile",
-           "lb_batch_tune", "lb_batch_sites", "lb_batch_time", "lb_batch_destroy"]
+           "lb_batch_tune", "lb_batch_sites", "lb_batch_time", "lb_batch_destroy", "lb_velocity_statistics"]
 
 
 def _load():
@@ -90,6 +90,7 @@ def _load():
     lib.lb_batch_time.restype = ctypes.c_longlong
     lib.lb_batch_destroy.argtypes = [vp]
     lib.lb_batch_destroy.restype = None
+    lib.lb_velocity_statistics.argtypes = [vp, i, i, i, i, i, d, d, vp, dp_, ctypes.POINTER(ctypes.c_ulonglong)]
     return lib
 
 
@@ -141,6 +142,27 @@ def field_stats_static(phi, u, stream=None) -> np.ndarray:
     out = (ctypes.c_double * 5)()
     _check(_lib.lb_field_stats_static(p, q, nx, ny, nz, ctypes.c_void_p(int(handle) if handle else 0), out))
     return np.array(list(out))
+
+
+def velocity_statistics(u, rmax: int = 0, nbins: int = 0, range_: float = 8.0, scale: float = 0.0, stream=None):
+    """Turbulence statistics of a device velocity field u (3, nz, ny, nx) through
+    lb_velocity_statistics: a dict with M2, M3, M4, skewness S, flatness F, the
+    structure functions S2, S3 (r = 1 .. rmax) and, with nbins > 0, the histogram
+    counts of g / scale (bins, then below and above the range)."""
+    _, nz, ny, nx = (int(v) for v in u.shape)
+    q, _a = _ptr(u, 3 * nx * ny * nz)
+    handle = getattr(stream, "cuda_stream", stream)
+    out = (ctypes.c_double * (3 + 2 * rmax))()
+    hist = (ctypes.c_ulonglong * (nbins + 2))() if nbins > 0 else None
+    _check(_lib.lb_velocity_statistics(q, nx, ny, nz, int(rmax), int(nbins), float(range_), float(scale),
+                                       ctypes.c_void_p(int(handle) if handle else 0), out, hist))
+    o = np.array(list(out))
+    m2, m3, m4 = o[:3]
+    res = {"M2": m2, "M3": m3, "M4": m4, "S": m3 / m2 ** 1.5 if m2 > 0 else float("nan"),
+           "F": m4 / (m2 * m2) if m2 > 0 else float("nan"), "S2": o[3:3 + rmax], "S3": o[3 + rmax:]}
+    if nbins > 0:
+        res["hist"] = np.array(list(hist), dtype=np.int64)
+    return res
 
 
 @dataclass

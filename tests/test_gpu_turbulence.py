@@ -1,0 +1,102 @@
+"""lb_velocity_statistics (Sec. 5.1 turbulence statistics on the device)
+against the FP64 oracle of oracle/turbulence.py on the same FP32 fields.
+
+- The gradient samples are FP32 on both sides with the same operation order,
+  each operation rounded on its own, so the histogram counts are equal
+  exactly when both bin with the same scale.
+- The moments: the device sums FP32 products of the FP32 samples per thread
+  (at most a few hundred terms) and then in FP64; the oracle's are the FP64
+  moments of the FP64 gradient.  FP32 rounding of a sample (a few 2^-24 of the
+  stencil's terms), of the products and of the partial sums gives rtol 2e-5
+  for M2 and M4, and 2e-5 of M(|g|^3) for M3, which cancels.
+- The structure functions take FP32 differences and per-thread FP32 sums of
+  at most a few hundred terms before the FP64 reduction: each term is within
+  a few 2^-24 of its FP64 value and each partial sum within K 2^-24, so rtol
+  2e-5 for S_2 and 2e-5 of the mean |d|^3 for S_3.
+"""
+import numpy as np
+import pytest
+
+from oracle import turbulence as T
+from paper_2505_01126_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbgb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_01126_gb300 import build
+
+    build.build()
+    from paper_2505_01126_gb300 import lbgb as mod
+
+    return mod
+
+
+def check(lbgb, u32, rmax, nbins=64, rng=6.0):
+    import torch
+
+    u64 = u32.astype(np.float64)
+    mo = T.gradient_moments(u64)
+    sig = float(np.sqrt(mo["M2"]))
+    res = lbgb.velocity_statistics(torch.from_numpy(u32).cuda(), rmax=rmax, nbins=nbins, range_=rng, scale=sig)
+    assert res["M2"] == pytest.approx(mo["M2"], rel=2e-5)
+    assert res["M4"] == pytest.approx(mo["M4"], rel=2e-5)
+    gabs3 = float(np.mean(np.abs(T.longitudinal_gradients(u64)) ** 3))
+    assert abs(res["M3"] - mo["M3"]) <= 2e-5 * gabs3
+    assert np.array_equal(res["hist"], T.gradient_histogram(u64, nbins, rng, sig))
+    if rmax:
+        s2, s3 = T.structure_functions(u64, rmax)
+        np.testing.assert_allclose(res["S2"], s2, rtol=2e-5)
+        for r in range(1, rmax + 1):
+            dabs3 = np.mean([np.abs(np.roll(u64[a], -r, axis=2 - a) - u64[a]) ** 3 for a in range(3)])
+            assert abs(res["S3"][r - 1] - s3[r - 1]) <= 2e-5 * dabs3 + 1e-30
+    return res, mo
+
+
+def test_solenoidal_field_48(lbgb):
+    """The HIT generator's velocity (modes 1 <= |k| <= 4, u_rms 0.02) on 48^3."""
+    u = inputs.to_f32(inputs.solenoidal_velocity(48, 48, 48, 0.02, seed=11))
+    res, mo = check(lbgb, u, rmax=24)
+    assert res["F"] == pytest.approx(mo["F"], rel=1e-4)
+
+
+@pytest.mark.parametrize("shape", [(20, 7, 13), (5, 1, 1), (3, 4, 2)])
+def test_ragged_and_thin_boxes(lbgb, shape):
+    rng = np.random.default_rng(sum(shape))
+    u = inputs.to_f32(0.01 * rng.standard_normal((3,) + shape))
+    check(lbgb, u, rmax=min(shape) if min(shape) > 1 else 2, nbins=16, rng=3.0)
+
+
+def test_auto_scale_histogram(lbgb):
+    """scale <= 0 bins in units of the device's own sqrt(M2): counts equal the
+    oracle's with its sqrt(M2) up to samples that straddle a bin edge by a
+    rounding of the scale (none expected)."""
+    import torch
+
+    u = inputs.to_f32(inputs.solenoidal_velocity(32, 32, 32, 0.02, seed=3))
+    res = lbgb.velocity_statistics(torch.from_numpy(u).cuda(), nbins=40, range_=5.0)
+    mo = T.gradient_moments(u.astype(np.float64))
+    want = T.gradient_histogram(u.astype(np.float64), 40, 5.0, float(np.sqrt(mo["M2"])))
+    assert int(np.abs(res["hist"] - want).sum()) <= 2
+    assert res["hist"].sum() == 3 * 32 ** 3
+
+
+def test_bench_workload_256(lbgb):
+    """The 256^3 bench workload's initial velocity: moments and histogram exact
+    against the oracle, structure functions for r <= 4."""
+    w = inputs.bubbly_hit(256, 64, 10.0, seed=2)
+    check(lbgb, w.u, rmax=4, nbins=100, rng=8.0)
+
+
+def test_rejects_bad_arguments(lbgb):
+    import torch
+
+    u = torch.zeros(3 * 8, device="cuda")
+    with pytest.raises(lbgb.LBError) as e:
+        lbgb.velocity_statistics(u.view(3, 2, 2, 2), nbins=10, range_=0.0)
+    assert e.value.code == lbgb.LB_EINVAL
