@@ -1,6 +1,7 @@
 """FP64 oracle of the velocity statistics of homogeneous isotropic turbulence
 (Sec. 5.1: the PDF of the longitudinal velocity gradient with its skewness S
-and flatness F, and the second- and third-order structure functions).
+and flatness F, the second- and third-order structure functions, and the
+energy and pressure spectra).
 
 TEST INFRASTRUCTURE, like the rest of this package: plain numpy, written out
 from the definitions, sharing nothing with the CUDA library.
@@ -95,3 +96,27 @@ def structure_functions(u: np.ndarray, rmax: int) -> tuple[np.ndarray, np.ndarra
         s2[r - 1] = acc2 / (3 * u[0].size)
         s3[r - 1] = acc3 / (3 * u[0].size)
     return s2, s3
+
+
+def spectrum(f: np.ndarray, kmax: int) -> np.ndarray:
+    """Shell spectrum E(k), k = 0 .. kmax, of a periodic cubic field f of shape
+    (ncomp, n, n, n): E(k) = 1/2 sum over the components and over the integer
+    wavevectors m with round(|m|) = k of |f_hat(m)|^2, f_hat = FFT(f) / N.
+    For a velocity field this is the energy spectrum, with sum_k E(k) = mean
+    |u|^2 / 2 when kmax covers every shell (Parseval); for the pressure, 1/2
+    |p_hat|^2 per shell."""
+    f = np.asarray(f, dtype=np.float64)
+    n = f.shape[-1]
+    assert f.shape[-3:] == (n, n, n)
+    N = n ** 3
+    m = np.fft.fftfreq(n, 1.0 / n)  # signed integer wavenumbers
+    mz, my, mx = np.meshgrid(m, m, m, indexing="ij")
+    k = np.floor(np.sqrt(mx * mx + my * my + mz * mz) + 0.5).astype(np.int64)
+    p = np.zeros(k.shape)
+    for c in range(f.shape[0]):
+        fh = np.fft.fftn(f[c]) / N
+        p += 0.5 * (fh.real ** 2 + fh.imag ** 2)
+    out = np.zeros(kmax + 1)
+    sel = k <= kmax
+    np.add.at(out, k[sel], p[sel])
+    return out

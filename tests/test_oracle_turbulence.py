@@ -111,3 +111,35 @@ def test_fp32_gradients_follow_the_fp64_ones():
     g32 = T.longitudinal_gradients(u, np.float32)
     assert g32.dtype == np.float32
     assert float(np.abs(g32 - g64).max()) < 1e-6 * float(np.abs(u).max())
+
+
+def test_spectrum_single_modes_and_parseval():
+    """A cosine mode A cos(2 pi m.x / n) puts A^2/4 in shell round(|m|); any
+    field's shells sum to mean |f|^2 / 2 (Parseval)."""
+    n = 16
+    z, y, x = np.meshgrid(*[np.arange(n)] * 3, indexing="ij")
+    u = np.zeros((3, n, n, n))
+    u[0] = 0.02 * np.cos(2 * math.pi * (3 * x + 4 * z) / n + 0.4)   # |m| = 5
+    u[2] = 0.01 * np.cos(2 * math.pi * (1 * y) / n)                 # |m| = 1
+    E = T.spectrum(u, 14)
+    want = np.zeros(15)
+    want[5] = 0.02 ** 2 / 4
+    want[1] = 0.01 ** 2 / 4
+    np.testing.assert_allclose(E, want, atol=1e-18)
+    rng = np.random.default_rng(9)
+    f = rng.standard_normal((3, 8, 8, 8))
+    E = T.spectrum(f, 7)  # 7 > sqrt(3)*4 = 6.93: every shell
+    assert E.sum() == pytest.approx(0.5 * (f * f).sum(axis=0).mean(), rel=1e-12)
+    # brute-force DFT of one scalar field, one shell
+    g = rng.standard_normal((1, 4, 4, 4))
+    E = T.spectrum(g, 3)
+    acc = 0.0
+    for mz, my, mx in itertools.product(range(4), repeat=3):
+        sm = [v if v < 2 else v - 4 for v in (mx, my, mz)]
+        if int(math.floor(math.sqrt(sum(v * v for v in sm)) + 0.5)) != 1:
+            continue
+        c = 0j
+        for zz, yy, xx in itertools.product(range(4), repeat=3):
+            c += g[0, zz, yy, xx] * np.exp(-2j * math.pi * (mx * xx + my * yy + mz * zz) / 4)
+        acc += 0.5 * abs(c / 64) ** 2
+    assert E[1] == pytest.approx(acc, rel=1e-12)
