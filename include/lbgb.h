@@ -196,6 +196,26 @@ void lb_destroy(lb_ctx* ctx);
 int lb_velocity_statistics(const float* u, int nx, int ny, int nz, int rmax, int nbins, double range, double scale,
                            void* stream, double* out, unsigned long long* hist);
 
+/*
+ * lb_spectrum -- shell spectrum of a periodic cubic field (the energy and
+ * pressure spectra of Sec. 5.1), computed on the device.
+ *   f       device array of ncomp * n^3 floats (ncomp = 1 .. 3 component
+ *           planes, x fastest); caller-owned, read only
+ *   n       edge of the cubic box, n^3 < 2^31 - 1
+ *   kmax    last shell (shells 0 .. kmax; at most 6143)
+ *   stream  cudaStream_t (NULL: legacy default stream); the call returns when
+ *           the result is on the host
+ *   out     host, kmax + 1 doubles: E(k) = 1/2 sum over the components and the
+ *           integer wavevectors m with round(|m|) = k of |f_hat(m)|^2, with
+ *           f_hat = FFT(f) / n^3.  For a velocity field the shells sum to the
+ *           mean kinetic energy per site (Parseval) once kmax >= sqrt(3) n/2;
+ *           for the pressure pass p = p^* c_s^2 from lb_moments (one component).
+ * The FFT is cuFFT's single-precision R2C; shell sums are FP64 (per-block
+ * shared-memory sums, then a fixed-order sum over blocks).  Scratch is
+ * allocated and freed here.  Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA.
+ */
+int lb_spectrum(const float* f, int ncomp, int n, int kmax, void* stream, double* out);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* lb_last_error(void);
 

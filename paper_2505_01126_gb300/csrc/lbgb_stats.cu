@@ -1,11 +1,14 @@
 // lbgb_stats.cu -- velocity statistics of homogeneous isotropic turbulence
 // (Sec. 5.1): moments and histogram of the longitudinal velocity gradient
-// (skewness, flatness, PDF) and the longitudinal structure functions S_2(r),
-// S_3(r) of a periodic velocity field on the device.  See lb_velocity_statistics
-// in include/lbgb.h for the definitions.
+// (skewness, flatness, PDF), the longitudinal structure functions S_2(r),
+// S_3(r), and shell spectra (energy, pressure) of periodic fields on the
+// device.  See lb_velocity_statistics and lb_spectrum in include/lbgb.h for
+// the definitions.
 #include <cuda_runtime.h>
+#include <cufft.h>
 
 #include <math.h>
+#include <stdint.h>
 #include <stdio.h>
 
 #include "lbgb.h"
@@ -203,6 +206,42 @@ __global__ void __launch_bounds__(ST_NT) structure_reduce_kernel(const double* p
     }
 }
 
+// Shell sums of 1/2 |c / N|^2 over one R2C half-spectrum (n x n x (n/2+1)
+// complex values), each entry weighted by the number of full-spectrum
+// wavevectors it stands for (1 on the planes mx = 0 and mx = n/2, else 2).
+// Per-block FP64 shell sums in shared memory, then per-block rows.
+__global__ void __launch_bounds__(ST_NT) shell_kernel(const cufftComplex* c, int n, int kmax, double invN,
+                                                     double* rows) {
+    extern __shared__ double sh_shell[];
+    for (int k = threadIdx.x; k <= kmax; k += ST_NT) sh_shell[k] = 0.0;
+    __syncthreads();
+    const int nh = n / 2 + 1;
+    const long long total = (long long)n * n * nh;
+    for (long long e = blockIdx.x * (long long)ST_NT + threadIdx.x; e < total; e += (long long)gridDim.x * ST_NT) {
+        const int mx = (int)(e % nh);
+        const long long r = e / nh;
+        const int my0 = (int)(r % n), mz0 = (int)(r / n);
+        const int my = my0 <= n / 2 ? my0 : my0 - n, mz = mz0 <= n / 2 ? mz0 : mz0 - n;
+        const long long m2 = (long long)mx * mx + (long long)my * my + (long long)mz * mz;
+        const int k = (int)floor(sqrt((double)m2) + 0.5);
+        if (k > kmax) continue;
+        const double re = (double)c[e].x * invN, im = (double)c[e].y * invN;
+        const double w = (mx == 0 || (n % 2 == 0 && mx == n / 2)) ? 0.5 : 1.0;  // 1/2 x multiplicity
+        atomicAdd(&sh_shell[k], w * (re * re + im * im));
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k <= kmax; k += ST_NT) rows[(long long)blockIdx.x * (kmax + 1) + k] = sh_shell[k];
+}
+
+// out[k] = sum over blocks of rows[b][k] (fixed order), accumulated onto out.
+__global__ void __launch_bounds__(ST_NT) shell_reduce_kernel(const double* rows, int blocks, int kmax, double* out) {
+    for (int k = blockIdx.x * ST_NT + threadIdx.x; k <= kmax; k += gridDim.x * ST_NT) {
+        double v = 0.0;
+        for (int b = 0; b < blocks; ++b) v += rows[(long long)b * (kmax + 1) + k];
+        out[k] += v;
+    }
+}
+
 thread_local char s_err[256] = "";
 
 int sfail(int code, const char* msg, cudaError_t e = cudaSuccess) {
@@ -284,5 +323,87 @@ extern "C" int lb_velocity_statistics(const float* u, int nx, int ny, int nz, in
     if (e != cudaSuccess) rc = sfail(LB_ECUDA, "CUDA error", e);
     cudaFree(scratch);
     if (dhist) cudaFree(dhist);
+    return rc;
+}
+
+extern "C" int lb_spectrum(const float* f, int ncomp, int n, int kmax, void* stream, double* out) {
+    const char* who = "lb_spectrum";
+    auto err = [&](int code, const char* msg, cudaError_t e = cudaSuccess) {
+        if (e != cudaSuccess) cudaGetLastError();
+        snprintf(s_err, sizeof(s_err), "%s: %s%s%s", who, msg, e != cudaSuccess ? ": " : "",
+                 e != cudaSuccess ? cudaGetErrorString(e) : "");
+        lbgb::set_last_error(s_err);
+        return code;
+    };
+    if (!f || !out) return err(LB_EINVAL, "NULL argument");
+    if (ncomp < 1 || ncomp > 3 || n < 2 || (long long)n * n * n >= (1LL << 31) - 1 || kmax < 0 || kmax > 8192)
+        return err(LB_EINVAL, "bad size");
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long N = (long long)n * n * n;
+    const long long nc = (long long)n * n * (n / 2 + 1);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return err(LB_ECUDA, "device query", e);
+    const long long want = (nc + ST_NT - 1) / ST_NT;
+    const int blocks = (int)(want < 2LL * sms ? want : 2LL * sms);
+    if ((size_t)(kmax + 1) * sizeof(double) > 48 * 1024) return err(LB_EINVAL, "kmax too large");
+
+    cufftComplex* c = nullptr;
+    double* rows = nullptr;
+    double* dout = nullptr;
+    float* aligned = nullptr;  // a component plane off an 8-byte boundary is copied here first
+    bool need_copy = false;
+    for (int q = 0; q < ncomp; ++q)
+        if (reinterpret_cast<uintptr_t>(f + (long long)q * N) % sizeof(cufftComplex)) need_copy = true;
+    e = cudaMalloc(&c, (size_t)nc * sizeof(cufftComplex));
+    if (e == cudaSuccess && need_copy) e = cudaMalloc(&aligned, (size_t)N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&rows, (size_t)blocks * (kmax + 1) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&dout, (size_t)(kmax + 1) * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaFree(c); cudaFree(rows); cudaFree(dout); cudaFree(aligned);
+        return err(e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA, "cudaMalloc", e);
+    }
+    cufftHandle plan;
+    if (cufftPlan3d(&plan, n, n, n, CUFFT_R2C) != CUFFT_SUCCESS) {
+        cudaFree(c); cudaFree(rows); cudaFree(dout); cudaFree(aligned);
+        return err(LB_ECUDA, "cufftPlan3d failed");
+    }
+    int rc = LB_OK;
+    do {
+        if (cufftSetStream(plan, st) != CUFFT_SUCCESS) { rc = err(LB_ECUDA, "cufftSetStream failed"); break; }
+        if ((e = cudaMemsetAsync(dout, 0, (size_t)(kmax + 1) * sizeof(double), st)) != cudaSuccess) {
+            rc = err(LB_ECUDA, "memset", e);
+            break;
+        }
+        for (int q = 0; q < ncomp && rc == LB_OK; ++q) {
+            const float* src = f + (long long)q * N;
+            if (reinterpret_cast<uintptr_t>(src) % sizeof(cufftComplex)) {
+                if ((e = cudaMemcpyAsync(aligned, src, (size_t)N * sizeof(float), cudaMemcpyDeviceToDevice, st)) !=
+                    cudaSuccess) {
+                    rc = err(LB_ECUDA, "copy", e);
+                    break;
+                }
+                src = aligned;
+            }
+            // out-of-place R2C leaves its input unchanged
+            if (cufftExecR2C(plan, const_cast<cufftReal*>(src), c) != CUFFT_SUCCESS) {
+                rc = err(LB_ECUDA, "cufftExecR2C failed");
+                break;
+            }
+            shell_kernel<<<blocks, ST_NT, (size_t)(kmax + 1) * sizeof(double), st>>>(c, n, kmax, 1.0 / (double)N, rows);
+            shell_reduce_kernel<<<(kmax + ST_NT) / ST_NT, ST_NT, 0, st>>>(rows, blocks, kmax, dout);
+            if ((e = cudaGetLastError()) != cudaSuccess) rc = err(LB_ECUDA, "launch", e);
+        }
+        if (rc != LB_OK) break;
+        if ((e = cudaMemcpyAsync(out, dout, (size_t)(kmax + 1) * sizeof(double), cudaMemcpyDefault, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            rc = err(LB_ECUDA, "copy", e);
+    } while (0);
+    cufftDestroy(plan);
+    cudaFree(c);
+    cudaFree(rows);
+    cudaFree(dout);
+    cudaFree(aligned);
     return rc;
 }

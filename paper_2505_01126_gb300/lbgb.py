@@ -40,7 +40,8 @@ EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_step", "lb_moments", "lb
            "lb_destroy", "lb_last_error", "lb_launch_count", "lb_set_timing", "lb_kernel_time",
            "lb_field_stats_static", "lb_batch_create", "lb_batch_set_stream", "lb_batch_init",
            "lb_batch_step", "lb_batch_moments", "lb_batch_diagnostics", "lb_batch_set_tile", "lb_batch_get_tile",
-           "lb_batch_tune", "lb_batch_sites", "lb_batch_time", "lb_batch_destroy", "lb_velocity_statistics"]
+           "lb_batch_tune", "lb_batch_sites", "lb_batch_time", "lb_batch_destroy", "lb_velocity_statistics",
+           "lb_spectrum"]
 
 
 def _load():
@@ -91,6 +92,7 @@ def _load():
     lib.lb_batch_destroy.argtypes = [vp]
     lib.lb_batch_destroy.restype = None
     lib.lb_velocity_statistics.argtypes = [vp, i, i, i, i, i, d, d, vp, dp_, ctypes.POINTER(ctypes.c_ulonglong)]
+    lib.lb_spectrum.argtypes = [vp, i, i, i, vp, dp_]
     return lib
 
 
@@ -163,6 +165,19 @@ def velocity_statistics(u, rmax: int = 0, nbins: int = 0, range_: float = 8.0, s
     if nbins > 0:
         res["hist"] = np.array(list(hist), dtype=np.int64)
     return res
+
+
+def spectrum(f, kmax: int, stream=None) -> np.ndarray:
+    """Shell spectrum E(0 .. kmax) of a device field f of shape (ncomp, n, n, n)
+    (or (n, n, n) for one component) through lb_spectrum."""
+    shape = tuple(int(v) for v in f.shape)
+    ncomp = 1 if len(shape) == 3 else shape[0]
+    n = shape[-1]
+    q, _a = _ptr(f, ncomp * n ** 3)
+    handle = getattr(stream, "cuda_stream", stream)
+    out = (ctypes.c_double * (kmax + 1))()
+    _check(_lib.lb_spectrum(q, ncomp, n, int(kmax), ctypes.c_void_p(int(handle) if handle else 0), out))
+    return np.array(list(out))
 
 
 @dataclass

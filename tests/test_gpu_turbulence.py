@@ -100,3 +100,37 @@ def test_rejects_bad_arguments(lbgb):
     with pytest.raises(lbgb.LBError) as e:
         lbgb.velocity_statistics(u.view(3, 2, 2, 2), nbins=10, range_=0.0)
     assert e.value.code == lbgb.LB_EINVAL
+
+
+@pytest.mark.parametrize("n", [16, 15])
+def test_spectrum_modes_and_parseval(lbgb, n):
+    """Cosine modes land in their shells; the shells of a random field sum to
+    mean |u|^2 / 2 (cuFFT single precision: rtol 1e-5)."""
+    import torch
+
+    z, y, x = np.meshgrid(*[np.arange(n)] * 3, indexing="ij")
+    u = np.zeros((3, n, n, n), np.float32)
+    u[0] = 0.02 * np.cos(2 * np.pi * (3 * x + 4 * z) / n + 0.4)
+    u[2] = 0.01 * np.cos(2 * np.pi * y / n)
+    kmax = int(np.ceil(np.sqrt(3) * n / 2))
+    E = lbgb.spectrum(torch.from_numpy(u).cuda(), kmax)
+    want = T.spectrum(u.astype(np.float64), kmax)
+    np.testing.assert_allclose(E, want, rtol=1e-5, atol=1e-6 * want.sum())
+    rng = np.random.default_rng(n)
+    f = rng.standard_normal((3, n, n, n)).astype(np.float32)
+    E = lbgb.spectrum(torch.from_numpy(f).cuda(), kmax)
+    assert E.sum() == pytest.approx(0.5 * float((f.astype(np.float64) ** 2).sum(axis=0).mean()), rel=1e-5)
+
+
+def test_spectrum_bench_workload(lbgb):
+    """Energy spectrum of the 256^3 bench workload's velocity and the spectrum of
+    one scalar field (its phi) against the FP64 oracle: cuFFT FP32 gives each
+    coefficient to ~1e-6 of the field's norm, so shells within 1e-4 relative
+    or 1e-6 of the total."""
+    import torch
+
+    w = inputs.bubbly_hit(256, 64, 10.0, seed=2)
+    for f, kmax in ((w.u, 128), (w.phi[None], 64)):
+        E = lbgb.spectrum(torch.from_numpy(np.ascontiguousarray(f)).cuda(), kmax)
+        want = T.spectrum(f.astype(np.float64), kmax)
+        np.testing.assert_allclose(E, want, rtol=1e-4, atol=1e-6 * want.sum())
