@@ -254,7 +254,7 @@ def run_ensemble(args):
     ms = e0.elapsed_time(e1)
     sites = batch.sites
     value = sites * args.steps / (ms * 1e-3) / 1e6
-    bps = 272.0 if args.storage == "f32" else 164.0
+    bps = {"f32": 272.0, "f16": 164.0, "bf16": 164.0, "moments": 136.0}[args.storage]
     peak, peak_kind = peaks()
     achieved = bps * sites / (ms / args.steps * 1e-3) / 1e9
     errs = []

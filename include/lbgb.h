@@ -67,7 +67,7 @@ extern "C" {
 #define LB_F32 0          /* delta_i stored as FP32 */
 #define LB_F16_SHIFTED 1  /* delta_i stored as FP16 */
 #define LB_BF16_SHIFTED 2 /* delta_i stored as BF16 */
-#define LB_F32_MOMENTS 3  /* post-collision coefficients, FP32 (single boxes only) */
+#define LB_F32_MOMENTS 3  /* post-collision coefficients, FP32 */
 
 /* ------------------------------------------------------------ forcing */
 #define LB_FORCE_NONE 0
@@ -245,7 +245,7 @@ typedef struct lb_batch lb_batch;
 /* count boxes; dims = count triples (nx, ny, nz); tau, M, W, sigma = count
  * values each, with the meaning and limits of lb_create.  The batch owns one
  * population array for all boxes (same storage), two D3Q7 arrays and the
- * reduction scratch.  storage is LB_F32, LB_F16_SHIFTED or LB_BF16_SHIFTED.
+ * reduction scratch.  storage is any LB_* storage.
  * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA. */
 int lb_batch_create(int count, const int* dims, const double* tau, const double* M, const double* W,
                     const double* sigma, int storage, lb_batch** out);

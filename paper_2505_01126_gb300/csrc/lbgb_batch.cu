@@ -4,8 +4,9 @@
 // graph two steps at a time.  See include/lbgb.h for the contract of each call.
 //
 // Memory: one population array for all boxes (box b's 27 planes of N_b sites
-// start at element f_off_b), two D3Q7 arrays likewise, per-item FP64 partials,
-// and one DevState per box.  The work list enumerates (box, 32 x ty tile,
+// start at element f_off_b; with the moment-only storage two buffers of 10
+// coefficient planes per box instead, from c_off_b), two D3Q7 arrays likewise,
+// per-item FP64 partials, and one DevState per box.  The work list enumerates (box, 32 x ty tile,
 // z-chunk) items; the persistent grid strides over it, so every box is
 // computed by the same per-tile code as a single box.
 #include <cuda_runtime.h>
@@ -97,6 +98,7 @@ struct lb_batch {
     size_t fsize = 4;
     int device = 0;
     std::vector<BoxDesc> boxes;       // host copy (item fields follow the current tile)
+    bool mc = false;                  // moment-only storage
     std::vector<double> tau, M, W, sigma;
     long long total_sites = 0, max_N = 0;
     bool vec = true;                  // every box has nx % 4 == 0
@@ -166,6 +168,7 @@ int build_work(lb_batch* B) {
     B->nitems = item;
     int per_sm = 0;
     switch (B->storage) {
+        case LB_F32_MOMENTS: per_sm = batch_mc_blocks_per_sm(B->ty, B->vec); break;
         case LB_F32: per_sm = batch_blocks_per_sm<float>(B->ty, B->vec); break;
         case LB_F16_SHIFTED: per_sm = batch_blocks_per_sm<__half>(B->ty, B->vec); break;
         default: per_sm = batch_blocks_per_sm<__nv_bfloat16>(B->ty, B->vec); break;
@@ -185,7 +188,16 @@ StepArgs box_args(const lb_batch* B, int box, int par) {
     a.nx = d.nx; a.ny = d.ny; a.nz = d.nz;
     a.zc = d.nz < 32 ? d.nz : 32;
     a.N = d.N;
-    for (int i = 0; i < 27; ++i) a.fk[i] = (char*)B->f + ((size_t)d.f_off + (size_t)i * d.N) * B->fsize;
+    if (B->mc) {
+        float* C = static_cast<float*>(B->f);
+        const size_t buf = 10 * (size_t)B->total_sites;
+        for (int k = 0; k < 10; ++k) {
+            a.cin[k] = C + buf * (size_t)par + (size_t)d.c_off + (size_t)k * d.N;
+            a.cout[k] = C + buf * (size_t)(par ^ 1) + (size_t)d.c_off + (size_t)k * d.N;
+        }
+    } else {
+        for (int i = 0; i < 27; ++i) a.fk[i] = (char*)B->f + ((size_t)d.f_off + (size_t)i * d.N) * B->fsize;
+    }
     for (int q = 0; q < 7; ++q) {
         a.gin[q] = B->g[par] + d.g_off + (size_t)q * d.N;
         a.gout[q] = B->g[par ^ 1] + d.g_off + (size_t)q * d.N;
@@ -197,15 +209,18 @@ StepArgs box_args(const lb_batch* B, int box, int par) {
     return a;
 }
 
+// par: AA parity; for the moment-only storage, 1 to pull (t > 0).
 cudaError_t launch_box(const lb_batch* B, int mode, int par, dim3 grid, const StepArgs& a, bool vec) {
     switch (B->storage) {
+        case LB_F32_MOMENTS: return launch_fused_mc(mode, par, 8, vec, grid, a, B->stream);
         case LB_F32: return launch_fused<float>(mode, par, 8, vec, grid, a, B->stream);
         case LB_F16_SHIFTED: return launch_fused<__half>(mode, par, 8, vec, grid, a, B->stream);
         default: return launch_fused<__nv_bfloat16>(mode, par, 8, vec, grid, a, B->stream);
     }
 }
 
-int enqueue_batch_step(lb_batch* B, int par, cudaStream_t s) {
+// One step at parity par; `first` marks the moment-only step from t = 0.
+int enqueue_batch_step(lb_batch* B, int par, cudaStream_t s, bool first = false) {
     BatchArgs b;
     b.nitems = B->nitems;
     b.zc = B->zc;
@@ -214,9 +229,17 @@ int enqueue_batch_step(lb_batch* B, int par, cudaStream_t s) {
     b.f = B->f;
     b.g_in = B->g[par];
     b.g_out = B->g[par ^ 1];
+    b.c_in = b.c_out = nullptr;
+    if (B->mc) {
+        float* C = static_cast<float*>(B->f);
+        const size_t buf = 10 * (size_t)B->total_sites;
+        b.c_in = C + buf * (size_t)par;
+        b.c_out = C + buf * (size_t)(par ^ 1);
+    }
     b.partials = B->partials;
     cudaError_t e;
     switch (B->storage) {
+        case LB_F32_MOMENTS: e = launch_batch_mc(first ? 0 : 1, B->ty, B->vec, B->grid_blocks, b, s); break;
         case LB_F32: e = launch_batch<float>(par, B->ty, B->vec, B->grid_blocks, b, s); break;
         case LB_F16_SHIFTED: e = launch_batch<__half>(par, B->ty, B->vec, B->grid_blocks, b, s); break;
         default: e = launch_batch<__nv_bfloat16>(par, B->ty, B->vec, B->grid_blocks, b, s); break;
@@ -290,15 +313,15 @@ int lb_batch_create(int count, const int* dims, const double* tau, const double*
     if (!out) return bfail(LB_EINVAL, "out is NULL");
     *out = nullptr;
     if (count < 1 || !dims || !tau || !M || !W || !sigma) return bfail(LB_EINVAL, "lb_batch_create: bad arguments");
-    if (storage == LB_F32_MOMENTS) return bfail(LB_EINVAL, "moment-only storage is for single boxes");
-    if (storage != LB_F32 && storage != LB_F16_SHIFTED && storage != LB_BF16_SHIFTED)
+    if (storage != LB_F32 && storage != LB_F16_SHIFTED && storage != LB_BF16_SHIFTED && storage != LB_F32_MOMENTS)
         return bfail(LB_EINVAL, "unknown storage %d", storage);
     lb_batch* B = new lb_batch();
     B->count = count;
     B->storage = storage;
-    B->fsize = storage == LB_F32 ? 4 : 2;
+    B->mc = storage == LB_F32_MOMENTS;
+    B->fsize = (storage == LB_F32 || B->mc) ? 4 : 2;
     cudaGetDevice(&B->device);
-    long long f_off = 0, g_off = 0;
+    long long f_off = 0, g_off = 0, c_off = 0;
     for (int b = 0; b < count; ++b) {
         const int nx = dims[3 * b], ny = dims[3 * b + 1], nz = dims[3 * b + 2];
         const double t = tau[b], m = M[b], w = W[b], sg = sigma[b];
@@ -313,6 +336,7 @@ int lb_batch_create(int count, const int* dims, const double* tau, const double*
         d.N = nx * ny * nz;
         d.f_off = f_off;
         d.g_off = g_off;
+        d.c_off = c_off;
         d.omega = (float)(1.0 / t);
         d.omega_phi = (float)(1.0 / (m / 0.25 + 0.5));
         d.sharp = isinf(w) ? 0.f : (float)((m / 0.25) * (4.0 / w));
@@ -324,6 +348,7 @@ int lb_batch_create(int count, const int* dims, const double* tau, const double*
         B->sigma.push_back(sg);
         f_off += 27LL * d.N;
         g_off += 7LL * d.N;
+        c_off += 10LL * d.N;
         B->total_sites += d.N;
         if (d.N > B->max_N) B->max_N = d.N;
         if (nx % 4) B->vec = false;
@@ -346,7 +371,7 @@ int lb_batch_create(int count, const int* dims, const double* tau, const double*
                        cudaGetErrorString(e));
         }
     };
-    alloc(&B->f, (size_t)f_off * B->fsize);
+    alloc(&B->f, B->mc ? (size_t)(2 * c_off) * sizeof(float) : (size_t)f_off * B->fsize);
     alloc((void**)&B->g[0], (size_t)g_off * sizeof(float));
     alloc((void**)&B->g[1], (size_t)g_off * sizeof(float));
     alloc((void**)&B->partials, (size_t)cap * NPART * sizeof(double));
@@ -419,7 +444,8 @@ int lb_batch_step(lb_batch* B, int n) {
                      B->n_initialized, B->count);
     while (n > 0) {
         const int par = (int)(B->t & 1);
-        if (par == 0 && n >= 2) {
+        const bool first = B->mc && B->t == 0;
+        if (par == 0 && n >= 2 && !first) {
             if (!B->graph || B->graph_ty != B->ty || B->graph_zc != B->zc) {
                 int rc = capture_batch_graph(B);
                 if (rc) return rc;
@@ -429,7 +455,7 @@ int lb_batch_step(lb_batch* B, int n) {
             B->t += 2;
             n -= 2;
         } else {
-            int rc = enqueue_batch_step(B, par, B->stream);
+            int rc = enqueue_batch_step(B, par, B->stream, first);
             if (rc) return rc;
             B->t += 1;
             n -= 1;
@@ -452,7 +478,7 @@ int lb_batch_moments(lb_batch* B, int box, float* rho, float* u, float* phi) {
     a.out_u = hu ? B->stage + N : u;
     a.out_phi = hp ? B->stage + 4 * N : phi;
     const dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + a.zc - 1) / a.zc);
-    BCUDA(launch_box(B, MODE_MOMENTS, par, grid, a, false));
+    BCUDA(launch_box(B, MODE_MOMENTS, B->mc ? (B->t > 0 ? 1 : 0) : par, grid, a, false));
     B->launches += 1;
     if (hr) BCUDA(cudaMemcpyAsync(rho, B->stage, (size_t)N * sizeof(float), cudaMemcpyDefault, B->stream));
     if (hu) BCUDA(cudaMemcpyAsync(u, B->stage + N, (size_t)N * 3 * sizeof(float), cudaMemcpyDefault, B->stream));
@@ -494,7 +520,8 @@ int lb_batch_tune(lb_batch* B, int steps) {
     if (B->n_initialized != 0 || B->t != 0)
         return bfail(LB_ESTATE, "lb_batch_tune times steps on the batch's own arrays: call it before lb_batch_init");
     // zero state: the step's cost does not depend on the values
-    BCUDA(cudaMemsetAsync(B->f, 0, (size_t)(B->total_sites * 27) * B->fsize, B->stream));
+    BCUDA(cudaMemsetAsync(B->f, 0, B->mc ? (size_t)(B->total_sites * 20) * sizeof(float)
+                                          : (size_t)(B->total_sites * 27) * B->fsize, B->stream));
     BCUDA(cudaMemsetAsync(B->g[0], 0, (size_t)(B->total_sites * 7) * sizeof(float), B->stream));
     BCUDA(cudaMemsetAsync(B->g[1], 0, (size_t)(B->total_sites * 7) * sizeof(float), B->stream));
     cudaEvent_t e0, e1;

@@ -393,6 +393,7 @@ fused_step_kernel(const StepArgs a) {
 struct BoxDesc {
     int nx, ny, nz, N;
     long long f_off, g_off;                 // element offsets into the batch arrays
+    long long c_off;                        // moment-only storage: offset of the box's 10 planes in a buffer
     float omega, omega_phi, sharp, beta;
     int item0, tiles_x, tiles_y, tiles_z;   // this box's slice of the work list
 };
@@ -404,6 +405,8 @@ struct BatchArgs {
     void* f;               // all boxes' populations (storage type)
     const float* g_in;
     float* g_out;
+    const float* c_in;     // moment-only storage: coefficient buffers at t and t+1
+    float* c_out;
     double* partials;      // NPART per work item
 };
 
@@ -429,10 +432,14 @@ struct BoxTileArgs {
     double* partials;
     float *out_rho, *out_u, *out_phi;
     const float *in_phi, *in_u;
+    PlaneSet<const float> cin;  // moment-only storage
+    PlaneSet<float> cout;
 };
 
-// Persistent kernel: the grid strides over the work list of all boxes.
-template <class FT, int TY, int PAR, bool VEC>
+// Persistent kernel: the grid strides over the work list of all boxes.  With
+// MC_ (moment-only storage, FT float) PAR = 0 evaluates each site's own
+// coefficients (the step from t = 0) and PAR = 1 pulls.
+template <class FT, int TY, int PAR, bool VEC, bool MC_ = false>
 __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 512 / (32 * TY)))
 batch_step_kernel(const __grid_constant__ BatchArgs b) {
     for (int item = blockIdx.x; item < b.nitems; item += gridDim.x) {
@@ -448,13 +455,15 @@ batch_step_kernel(const __grid_constant__ BatchArgs b) {
         t.abc = nullptr; t.st = nullptr; t.partials = b.partials;
         t.out_rho = t.out_u = t.out_phi = nullptr;
         t.in_phi = t.in_u = nullptr;
+        t.cin = PlaneSet<const float>{MC_ ? b.c_in + d.c_off : nullptr, (long long)d.N};
+        t.cout = PlaneSet<float>{MC_ ? b.c_out + d.c_off : nullptr, (long long)d.N};
         const int local = item - d.item0;
         const int tbx = local % d.tiles_x, rest = local / d.tiles_x;
         const int tby = rest % d.tiles_y, tbz = rest / d.tiles_y;
         {
             const BoxTileArgs<FT>& a = t;
             constexpr int MODE = MODE_STEP;
-            constexpr bool MC = false;
+            constexpr bool MC = MC_;
 #define TILE_BX tbx
 #define TILE_BY tby
 #define TILE_BZ tbz
@@ -482,6 +491,8 @@ int fused_mc_blocks_per_sm(int ty, bool vec);
 // pull = 0 evaluates each site's own coefficients (the state lb_init leaves),
 // pull = 1 rebuilds f from the neighbours' coefficients.
 cudaError_t launch_fused_mc(int mode, int pull, int ty, bool vec, dim3 grid, const StepArgs& a, cudaStream_t st);
+cudaError_t launch_batch_mc(int pull, int ty, bool vec, int blocks, const BatchArgs& b, cudaStream_t st);
+int batch_mc_blocks_per_sm(int ty, bool vec);
 
 // One step of every box of a batch (persistent grid of `blocks` blocks).
 template <class FT>

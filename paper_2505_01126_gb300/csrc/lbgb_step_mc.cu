@@ -35,6 +35,41 @@ cudaError_t launch_fused_mc(int mode, int pull, int ty, bool vec, dim3 grid, con
     return cudaGetLastError();
 }
 
+template <int TY, bool VEC>
+static void launch_batch_mc_ty(int pull, int blocks, const BatchArgs& b, cudaStream_t st) {
+    if (pull) batch_step_kernel<float, TY, 1, VEC, true><<<blocks, 32 * TY, 0, st>>>(b);
+    else batch_step_kernel<float, TY, 0, VEC, true><<<blocks, 32 * TY, 0, st>>>(b);
+}
+
+cudaError_t launch_batch_mc(int pull, int ty, bool vec, int blocks, const BatchArgs& b, cudaStream_t st) {
+    if (ty == 4) {
+        if (vec) launch_batch_mc_ty<4, true>(pull, blocks, b, st);
+        else launch_batch_mc_ty<4, false>(pull, blocks, b, st);
+    } else if (ty == 8) {
+        if (vec) launch_batch_mc_ty<8, true>(pull, blocks, b, st);
+        else launch_batch_mc_ty<8, false>(pull, blocks, b, st);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int batch_mc_blocks_per_sm(int ty, bool vec) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (ty == 4)
+        e = vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<float, 4, 1, true, true>, 128, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<float, 4, 1, false, true>, 128, 0);
+    else if (ty == 8)
+        e = vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<float, 8, 1, true, true>, 256, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<float, 8, 1, false, true>, 256, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
 int fused_mc_blocks_per_sm(int ty, bool vec) {
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;

@@ -61,9 +61,9 @@ def test_create_rejects_bad_storage_and_force(lbgb):
     assert e.value.code == lbgb.LB_EINVAL
 
 
-def test_batch_rejects_moment_only_storage(lbgb):
+def test_batch_rejects_unknown_storage(lbgb):
     with pytest.raises(lbgb.LBError) as e:
-        lbgb.Batch([(8, 8, 8)], 1.0, 0.1, 3.0, 0.01, storage="moments")
+        lbgb.Batch([(8, 8, 8)], 1.0, 0.1, 3.0, 0.01, storage=9)
     assert e.value.code == lbgb.LB_EINVAL
 
 

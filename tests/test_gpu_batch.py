@@ -47,7 +47,7 @@ def box_fields(nx, ny, nz, seed):
     [(32, 32, 32), (24, 24, 24), (48, 40, 36), (64, 16, 20), (8, 8, 8)],    # every nx % 4 == 0: float4 phase A
     [(32, 32, 32), (37, 13, 11), (24, 24, 24)],                              # a ragged nx: per-site phase A
 ])
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "moments"])
 def test_batch_boxes_equal_single_boxes(lbgb, dims, storage):
     tau = [0.8, 1.0, 0.6, 0.9, 0.7][: len(dims)]
     sigma = [0.01, 0.005, 0.02, 0.015, 0.01][: len(dims)]
