@@ -4,17 +4,22 @@
 // 2505.01126, Sec. 2); the numbered steps 1-13 are those listed in lbgb.h.
 //
 // Work decomposition.  A thread block owns a 32 x TY column of sites and
-// marches it through a chunk of zc planes.  Per plane z it
-//   A. computes phi = sum_q g_q (step 1) on the (32+4) x (TY+4) plane z+2 into
-//      a 4-plane shared-memory ring (halo 2: kappa needs phi within radius 2),
-//   B. computes grad phi and n (steps 2-3) on the (32+2) x (TY+2) plane z+1
-//      into a 4-plane ring,
-//   C. for the 32 x TY interior of plane z: kappa from the n ring (step 4),
-//      the forces (5-6), the hydrodynamic moments of its own populations (7),
-//      velocity, Hermite coefficient and regularized collision (8-10), the
-//      D3Q7 BGK (11), streaming stores (12) and FP64 partial sums (13).
-// The 27 f and 7 g loads of plane z are issued at the top of the iteration,
-// before phase A, so their latency overlaps phases A and B.
+// marches it through a chunk of zc planes.  In the interval of plane z it
+//   A. computes phi = sum_q g_q (step 1) on the (32+4) x (TY+4) plane z+4
+//      (halo 2: kappa needs phi within radius 2) and the z-smoothed planes
+//      of z+3,
+//   B. computes grad phi and n (steps 2-3) on the (32+2) x (TY+2) plane z+2
+//      and the curvature ingredients of plane z+1,
+//   C. for the 32 x TY interior of plane z: kappa (step 4), the forces (5-6),
+//      the hydrodynamic moments of its populations (7), velocity, Hermite
+//      coefficient and regularized collision (8-10), the D3Q7 BGK (11),
+//      streaming stores (12) and FP64 partial sums (13),
+// with one barrier per plane: each phase reads only what earlier intervals
+// wrote, and shared-memory rings keep each plane until its last reader.  The
+// 27 f and 7 g loads of plane z+1 are issued by each warp right after its
+// phase C of plane z, so they are in flight across the barrier and phases A
+// and B.  The moment-only storage (MC) replaces the f loads by coefficient
+// planes staged in shared memory and pulled in phase C.
 //
 // Layout in HBM (structure of arrays, site s = x + nx*(y + ny*z), 32-bit):
 //   f: 27 planes of N holding delta_i = f_i/w_i - 1, in place with the AA
