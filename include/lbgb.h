@@ -42,6 +42,8 @@
 #ifndef LBGB_H
 #define LBGB_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -158,6 +160,24 @@ int lb_get_tile(const lb_ctx* ctx, int* ty, int* zc);
  * ny, nz, storage) in the file named by LBGB_TUNE_CACHE, if set.
  */
 int lb_tune(lb_ctx* ctx, int steps);
+
+/*
+ * Checkpoint / restart.  lb_save copies the complete state of time t to host
+ * memory: a header (sizes, storage, t), the device state (forcing amplitude
+ * and target, last diagnostics, non-finite flag), the populations of time t
+ * (the AA array, or the moment-only coefficients the next step reads) and
+ * the D3Q7 populations of time t.  lb_load restores it into a context of the
+ * same sizes and storage (initialised or not), after which lb_step continues
+ * exactly as the saved run would have: the results are bitwise those of an
+ * uninterrupted run.  Both calls are synchronous on the context's stream.
+ *   buf    host memory of at least lb_state_bytes(ctx) bytes (pinned memory
+ *          makes the copies faster); caller-owned
+ * Errors: LB_EINVAL (NULL, short buffer, foreign or mismatched checkpoint),
+ * LB_ESTATE (lb_save before lb_init), LB_ECUDA.
+ */
+size_t lb_state_bytes(const lb_ctx* ctx);
+int lb_save(lb_ctx* ctx, void* buf, size_t bytes);
+int lb_load(lb_ctx* ctx, const void* buf, size_t bytes);
 
 /* Algorithmic bytes moved per site per step by the fused kernel (population
  * reads and writes): 27*2*sizeof(f) + 7*2*sizeof(g), or 10*2*4 + 7*2*4 for

@@ -599,6 +599,76 @@ int lb_get_tile(const lb_ctx* c, int* ty, int* zc) {
     return LB_OK;
 }
 
+// Checkpoint layout: header, DevState, the populations of time t (the AA
+// array, or the coefficient buffer the next step reads), the D3Q7 buffer of
+// time t.
+struct CkptHeader {
+    char magic[8];  // "LBGBCKP1"
+    int nx, ny, nz, storage;
+    long long t;
+    long long f_bytes, g_bytes;
+};
+
+static size_t ckpt_f_bytes(const lb_ctx* c) {
+    return is_mc(c) ? (size_t)c->N * 10 * sizeof(float) : (size_t)c->N * 27 * c->fsize;
+}
+
+static char* ckpt_f_ptr(const lb_ctx* c) {
+    if (!is_mc(c)) return static_cast<char*>(c->f);
+    return static_cast<char*>(c->f) + (size_t)(c->t & 1) * (size_t)c->N * 10 * sizeof(float);
+}
+
+size_t lb_state_bytes(const lb_ctx* c) {
+    if (!c) return 0;
+    return sizeof(CkptHeader) + sizeof(DevState) + ckpt_f_bytes(c) + (size_t)c->N * 7 * sizeof(float);
+}
+
+int lb_save(lb_ctx* c, void* buf, size_t bytes) {
+    if (!c || !buf) return fail(LB_EINVAL, "lb_save: NULL argument");
+    if (!c->initialized) return fail(LB_ESTATE, "lb_save before lb_init");
+    if (bytes < lb_state_bytes(c)) return fail(LB_EINVAL, "lb_save: buffer of %zu bytes < %zu", bytes, lb_state_bytes(c));
+    CkptHeader h;
+    memcpy(h.magic, "LBGBCKP1", 8);
+    h.nx = c->nx; h.ny = c->ny; h.nz = c->nz; h.storage = c->storage;
+    h.t = c->t;
+    h.f_bytes = (long long)ckpt_f_bytes(c);
+    h.g_bytes = (long long)c->N * 7 * (long long)sizeof(float);
+    char* p = static_cast<char*>(buf);
+    memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    LB_CUDA(cudaMemcpyAsync(p, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    p += sizeof(DevState);
+    LB_CUDA(cudaMemcpyAsync(p, ckpt_f_ptr(c), (size_t)h.f_bytes, cudaMemcpyDeviceToHost, c->stream));
+    p += h.f_bytes;
+    LB_CUDA(cudaMemcpyAsync(p, c->g[c->t & 1], (size_t)h.g_bytes, cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+int lb_load(lb_ctx* c, const void* buf, size_t bytes) {
+    if (!c || !buf) return fail(LB_EINVAL, "lb_load: NULL argument");
+    if (bytes < sizeof(CkptHeader)) return fail(LB_EINVAL, "lb_load: %zu bytes hold no checkpoint", bytes);
+    CkptHeader h;
+    memcpy(&h, buf, sizeof(h));
+    if (memcmp(h.magic, "LBGBCKP1", 8) != 0) return fail(LB_EINVAL, "lb_load: not a checkpoint of this library");
+    if (h.nx != c->nx || h.ny != c->ny || h.nz != c->nz || h.storage != c->storage)
+        return fail(LB_EINVAL, "lb_load: checkpoint of a %dx%dx%d box in storage %d, context is %dx%dx%d in %d", h.nx,
+                    h.ny, h.nz, h.storage, c->nx, c->ny, c->nz, c->storage);
+    if (h.t < 0 || bytes < lb_state_bytes(c) || h.f_bytes != (long long)ckpt_f_bytes(c) ||
+        h.g_bytes != (long long)c->N * 7 * (long long)sizeof(float))
+        return fail(LB_EINVAL, "lb_load: truncated or inconsistent checkpoint");
+    c->t = h.t;  // selects the buffers the state goes to
+    const char* p = static_cast<const char*>(buf) + sizeof(h);
+    LB_CUDA(cudaMemcpyAsync(c->st, p, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
+    p += sizeof(DevState);
+    LB_CUDA(cudaMemcpyAsync(ckpt_f_ptr(c), p, (size_t)h.f_bytes, cudaMemcpyHostToDevice, c->stream));
+    p += h.f_bytes;
+    LB_CUDA(cudaMemcpyAsync(c->g[c->t & 1], p, (size_t)h.g_bytes, cudaMemcpyHostToDevice, c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    c->initialized = true;
+    return LB_OK;
+}
+
 double lb_bytes_per_site(const lb_ctx* c) {
     if (!c) return 0.0;
     if (is_mc(c)) return 10.0 * 2.0 * 4.0 + 7.0 * 2.0 * 4.0;

@@ -41,7 +41,7 @@ EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_step", "lb_moments", "lb
            "lb_field_stats_static", "lb_batch_create", "lb_batch_set_stream", "lb_batch_init",
            "lb_batch_step", "lb_batch_moments", "lb_batch_diagnostics", "lb_batch_set_tile", "lb_batch_get_tile",
            "lb_batch_tune", "lb_batch_sites", "lb_batch_time", "lb_batch_destroy", "lb_velocity_statistics",
-           "lb_spectrum"]
+           "lb_spectrum", "lb_state_bytes", "lb_save", "lb_load"]
 
 
 def _load():
@@ -93,6 +93,10 @@ def _load():
     lib.lb_batch_destroy.restype = None
     lib.lb_velocity_statistics.argtypes = [vp, i, i, i, i, i, d, d, vp, dp_, ctypes.POINTER(ctypes.c_ulonglong)]
     lib.lb_spectrum.argtypes = [vp, i, i, i, vp, dp_]
+    lib.lb_state_bytes.argtypes = [vp]
+    lib.lb_state_bytes.restype = ctypes.c_size_t
+    lib.lb_save.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.lb_load.argtypes = [vp, vp, ctypes.c_size_t]
     return lib
 
 
@@ -285,6 +289,17 @@ class Box:
         ms, n = ctypes.c_double(), ctypes.c_longlong()
         _check(_lib.lb_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+    def save(self) -> np.ndarray:
+        """Checkpoint of the current state (lb_save) as a uint8 array."""
+        buf = np.empty(int(_lib.lb_state_bytes(self._h)), dtype=np.uint8)
+        _check(_lib.lb_save(self._h, ctypes.c_void_p(buf.ctypes.data), buf.nbytes))
+        return buf
+
+    def load(self, buf: np.ndarray):
+        """Restore a checkpoint written by save() (lb_load)."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(_lib.lb_load(self._h, ctypes.c_void_p(buf.ctypes.data), buf.nbytes))
 
     def close(self):
         if self._h is not None and self._h.value:
