@@ -419,6 +419,10 @@ int lb_create(int nx, int ny, int nz, double tau, double M, double W, double sig
     if (rc == LB_OK && fz.kind == LB_FORCE_ABC) {
         const int L = 2 * (nx + ny + nz);
         float* h = (float*)malloc((size_t)L * sizeof(float));
+        if (!h) {
+            lb_destroy(c);
+            return fail(LB_ENOMEM, "host table of %d floats", L);
+        }
         int o = 0;
         const int ns[3] = {nx, ny, nz};
         for (int ax = 0; ax < 3; ++ax) {
