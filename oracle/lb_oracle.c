@@ -18,7 +18,11 @@
  *   - hydrodynamics: D3Q27, pressure-based equilibrium (Sec. 2.2), Guo force
  *     (Eq. 6), push form of the collision (Eq. 7) with the non-equilibrium part
  *     rebuilt from the second-order Hermite coefficient (Eq. 8);
- *   - FP64 diagnostics and the linear-forcing amplitude controller.
+ *   - FP64 diagnostics and the linear-forcing amplitude controller;
+ *   - optional (orc_set_density): density and viscosity contrasts (Sec. 2.3),
+ *     mixture density rho(phi) and relaxation time tau(phi) linear in phi, the
+ *     pressure force F^p and the viscous correction F^nu added to the total
+ *     force, which enters the velocity, the source and a2 as F/rho.
  *
  * Every stage is a separate loop over all sites writing a full field, in the
  * order of the method.  Two copies of each population set are kept; streaming
@@ -36,7 +40,13 @@
  *   - the regularized non-equilibrium is w_i H_i:a2/(2 cs^4) (the printed form
  *     omits w_i and the trace part of H_i);
  *   - u = sum_i f_i c_i + F/2 (the printed sum of S_i vanishes identically);
- *   - linear forcing F = A u, A_{t+1} = [eps_t + (K_target-K_t)/T_relax]/(2K_t).
+ *   - linear forcing F = A u, A_{t+1} = [eps_t + (K_target-K_t)/T_relax]/(2K_t);
+ *   - density contrasts: F^p = -(p* - 1) cs^2 grad rho (p* measured from its
+ *     rest value 1, which the equilibrium here carries); F^nu with the
+ *     coefficient nu omega / cs^2 = 1 - omega/2 and f - f^eq taken from the
+ *     pre-collision populations, f^eq at the velocity without F^nu's own
+ *     half-force; tau (so nu) linear in phi; the body force is a force density
+ *     (acceleration F/rho); eps sums each site's own nu.
  */
 #include "lb_oracle.h"
 
@@ -107,6 +117,11 @@ struct orc_state {
     double *phi, *grad, *nrm, *kappa;  /* phase field and its derivatives */
     double *Fs, *rho, *mom, *Pi;       /* surface force, hydrodynamic moments */
     double *u, *F, *a2;                /* velocity, total force, Hermite coeff. */
+
+    /* variable density and viscosity (Sec. 2.3), off unless orc_set_density */
+    int vd;
+    double rho_l, rho_g, tau_l, tau_g; /* of the phi = 1 and phi = 0 phases */
+    double* om;                        /* per-site relaxation rate 1/tau(phi) */
 };
 
 static int g_threads = 0;
@@ -183,6 +198,7 @@ void orc_destroy(orc_state* s) {
     free(s->phi); free(s->grad); free(s->nrm); free(s->kappa);
     free(s->Fs); free(s->rho); free(s->mom); free(s->Pi);
     free(s->u); free(s->F); free(s->a2);
+    free(s->om);
     free(s);
 }
 
@@ -381,11 +397,68 @@ static void external_force(const orc_state* s, int x, int y, int z, double Fe[3]
     }
 }
 
+/* Variable density and viscosity (Sec. 2.3), per site:
+ *   rho = rho_g + phi (rho_l - rho_g), grad rho = (rho_l - rho_g) grad phi,
+ *   tau = tau_g + phi (tau_l - tau_g) (linear in tau, so in nu), omega = 1/tau;
+ *   F^p = -(p* - 1) cs^2 grad rho, the pressure p* measured from its rest value 1
+ *         (the equilibrium carries p* = 1 at rest);
+ *   u0  = (m + (F^s + F^ext + F^p)/(2 rho)) / (1 - A/2);
+ *   F^nu_a = -(nu omega / cs^2) sum_b [Pi_ab - (p* cs^2 d_ab + u0_a u0_b)] d_b rho,
+ *          nu omega / cs^2 = (tau - 1/2) / tau = 1 - omega/2; Pi the second
+ *          moment of the pre-collision f, the equilibrium taken at u0 (before
+ *          F^nu's own half-force);
+ *   u = (m + F/(2 rho)) / (1 - A/2), F = F^s + F^ext + F^p + F^nu,
+ * and the source, the Hermite coefficient and the collision see the
+ * acceleration F/rho + A u.  With rho_l = rho_g = 1 and tau_l = tau_g every
+ * added term is an exact zero and these are the density-ratio-1 values. */
+static void velocity_force_vd(orc_state* s, double A) {
+    long long N = s->N;
+    const double dr = s->rho_l - s->rho_g, dt = s->tau_l - s->tau_g;
+#pragma omp parallel for schedule(static) num_threads(orc_threads())
+    for (int z = 0; z < s->nz; ++z)
+        for (int y = 0; y < s->ny; ++y)
+            for (int x = 0; x < s->nx; ++x) {
+                long long i = site(s, x, y, z);
+                const double ph = s->phi[i];
+                const double rho = s->rho_g + ph * dr;
+                const double om = 1.0 / (s->tau_g + ph * dt);
+                const double pp = s->rho[i] - 1.0;
+                double Fe[3], grho[3], Fo[3], u0[3];
+                external_force(s, x, y, z, Fe);
+                for (int a = 0; a < 3; ++a) {
+                    grho[a] = dr * s->grad[a * N + i];
+                    Fo[a] = s->Fs[a * N + i] + Fe[a] - pp * CS2 * grho[a];
+                    u0[a] = (s->mom[a * N + i] + 0.5 * Fo[a] / rho) / (1 - 0.5 * A);
+                }
+                /* Pi - Pi^eq at u0; Pi is stored xx, yy, zz, xy, xz, yz */
+                const double p = s->rho[i];
+                double Pn[3][3];
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) {
+                        const int k = a == b ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5));
+                        Pn[a][b] = s->Pi[k * N + i] - ((a == b ? p * CS2 : 0.0) + u0[a] * u0[b]);
+                    }
+                for (int a = 0; a < 3; ++a) {
+                    double Fnu = 0;
+                    for (int b = 0; b < 3; ++b) Fnu += Pn[a][b] * grho[b];
+                    const double Fa = Fo[a] - (1 - 0.5 * om) * Fnu;
+                    const double ua = (s->mom[a * N + i] + 0.5 * Fa / rho) / (1 - 0.5 * A);
+                    s->u[a * N + i] = ua;
+                    s->F[a * N + i] = Fa / rho + A * ua;
+                }
+                s->om[i] = om;
+            }
+}
+
 /* u = sum f c + F/2 with F = F^s + F^ext + A u (linear forcing solved in closed
  * form: u = (m + (F^s + F^ext)/2) / (1 - A/2)). */
 static void stage_velocity_force(orc_state* s) {
     long long N = s->N;
     double A = s->force_kind == ORC_FORCE_LINEAR ? s->A : 0.0;
+    if (s->vd) {
+        velocity_force_vd(s, A);
+        return;
+    }
 #pragma omp parallel for schedule(static) num_threads(orc_threads())
     for (int z = 0; z < s->nz; ++z)
         for (int y = 0; y < s->ny; ++y)
@@ -447,11 +520,12 @@ static void stage_collide_stream_hydro(orc_state* s) {
                 } else {
                     for (int i = 0; i < 27; ++i) fneq[i] = s->f[i * N + k] - feq[i] + 0.5 * S[i];
                 }
+                const double om = s->vd ? s->om[k] : s->omega;
                 for (int i = 0; i < 27; ++i) {
                     const int* c = C27[i];
                     long long dst = site(s, wrap(x + c[0], s->nx), wrap(y + c[1], s->ny),
                                          wrap(z + c[2], s->nz));
-                    s->fn[i * N + dst] = feq[i] + (1 - s->omega) * fneq[i] + 0.5 * S[i];
+                    s->fn[i * N + dst] = feq[i] + (1 - om) * fneq[i] + 0.5 * S[i];
                 }
             }
     double* t = s->f; s->f = s->fn; s->fn = t;
@@ -487,6 +561,7 @@ static void stage_diagnostics(orc_state* s) {
     long long N = s->N;
     double Phi = 0, K = 0, SS = 0, umax = 0;
     double scale = 1.0 / (2 * CS2 * s->tau);
+    const double nu_g = s->vd ? CS2 * (s->tau_g - 0.5) : s->nu;
     for (long long x = 0; x < N; ++x) {
         Phi += s->phi[x];
         double u2 = s->u[x] * s->u[x] + s->u[N + x] * s->u[N + x] + s->u[2 * N + x] * s->u[2 * N + x];
@@ -496,14 +571,19 @@ static void stage_diagnostics(orc_state* s) {
         double ss = 0;
         double A[6];
         for (int q = 0; q < 6; ++q) A[q] = s->a2[q * N + x];
+        /* variable viscosity: each site's own tau in S and nu_s in the sum,
+         * eps = 2 nu_g sum (nu_s / nu_g) S:S (exactly the single-viscosity sum
+         * when tau_l = tau_g = tau) */
+        const double tx = s->vd ? s->tau_g + s->phi[x] * (s->tau_l - s->tau_g) : s->tau;
+        const double sc = s->vd ? 1.0 / (2 * CS2 * tx) : scale;
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) {
-                double Sab = -scale * sym(A, a, b);
+                double Sab = -sc * sym(A, a, b);
                 ss += Sab * Sab;
             }
-        SS += ss;
+        SS += s->vd ? (CS2 * (tx - 0.5)) / nu_g * ss : ss;
     }
-    double eps = 2 * s->nu * SS;
+    double eps = 2 * nu_g * SS;
     double Anext = 0;
     if (s->force_kind == ORC_FORCE_LINEAR && K > 0)
         Anext = (eps + (s->K_target - K) / s->T_relax) / (2 * K);
@@ -597,6 +677,17 @@ int orc_interface(int nx, int ny, int nz, double W, double sigma, const double* 
 
 void orc_diagnostics(const orc_state* s, double out[5]) {
     for (int q = 0; q < 5; ++q) out[q] = s->diag[q];
+}
+
+int orc_set_density(orc_state* s, double rho_l, double rho_g, double tau_l, double tau_g) {
+    if (!s || !(rho_l > 0) || !(rho_g > 0) || !(tau_l > 0.5) || !(tau_g > 0.5)) return -1;
+    if (!s->om) {
+        s->om = (double*)calloc((size_t)s->N, sizeof(double));
+        if (!s->om) return -1;
+    }
+    s->vd = 1;
+    s->rho_l = rho_l; s->rho_g = rho_g; s->tau_l = tau_l; s->tau_g = tau_g;
+    return 0;
 }
 
 void orc_get_populations(const orc_state* s, double* f, double* g) {

@@ -42,6 +42,13 @@ void orc_moments(orc_state* s, double* rho, double* u, double* phi);
 void orc_diagnostics(const orc_state* s, double out[5]);
 long long orc_time(const orc_state* s);
 
+/* Variable density and viscosity (Sec. 2.3): rho and tau of the phi = 1 and
+ * phi = 0 phases, interpolated linearly in phi; adds the pressure and viscous
+ * forces F^p, F^nu and divides the force by rho in the source.  rho_l = rho_g
+ * = 1 with tau_l = tau_g = tau reproduces the density-ratio-1 step exactly.
+ * Returns -1 on bad input. */
+int  orc_set_density(orc_state* s, double rho_l, double rho_g, double tau_l, double tau_g);
+
 /* Raw populations: f is 27N in the oracle's own direction order (see
  * orc_lattice27), g is 7N in the order of orc_lattice7. */
 void orc_get_populations(const orc_state* s, double* f, double* g);

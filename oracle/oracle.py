@@ -49,6 +49,7 @@ def _load():
             lib.orc_init.argtypes = [ctypes.c_void_p, _dp, _dp]
             lib.orc_init.restype = ctypes.c_int
             lib.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            lib.orc_set_density.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 4
             lib.orc_step.restype = ctypes.c_int
             lib.orc_moments.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
             lib.orc_diagnostics.argtypes = [ctypes.c_void_p, _dp]
@@ -184,6 +185,12 @@ class Oracle:
         u = _f64(u).reshape((3,) + self.shape)
         if self._lib.orc_init(self._h, _ptr(phi), _ptr(u)) != 0:
             raise RuntimeError("orc_init failed")
+
+    def set_density(self, rho_l, rho_g, tau_l, tau_g):
+        """Variable density and viscosity (Sec. 2.3): rho and tau of the phi = 1 and
+        phi = 0 phases, linear in phi in between."""
+        if self._lib.orc_set_density(self._h, float(rho_l), float(rho_g), float(tau_l), float(tau_g)) != 0:
+            raise ValueError("oracle rejected the density parameters")
 
     def step(self, n: int = 1):
         if self._lib.orc_step(self._h, int(n)) != 0:
