@@ -12,6 +12,9 @@ the measured HBM bandwidth reached by the fused kernel.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                        [--storage f32|f16|bf16|moments] [--edge E]
+                       [--density RHO_L RHO_G TAU_L TAU_G]
+--density runs the same box with density and viscosity contrasts (Sec. 2.3):
+the bubbles become the gas (phi = 0 inside, phi flipped), the liquid phi = 1.
 Under torchrun (N > 1) every rank advances its own replica box (weak scaling,
 no collective on the data path); value = sum of sites*steps over ranks divided
 by the slowest rank's time.
@@ -162,15 +165,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline_sample():
-    """Time the oracle (as it stands) on a bounded sample of the workload."""
+def cpu_baseline_sample(density=None):
+    """Time the oracle (as it stands) on a bounded sample of the workload (with the
+    density contrasts and flipped phase field when `density` is given)."""
     import oracle
 
     oracle.build()
     w, _ = workload(SAMPLE_EDGE)
     n = SAMPLE_EDGE
     o = oracle.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma, force_kind=oracle.FORCE_LINEAR, T_relax=w.T_relax)
-    o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
+    phi = w.phi.astype(np.float64)
+    if density:
+        o.set_density(*density)
+        phi = (1.0 - w.phi).astype(np.float64)
+    o.init(phi, w.u.astype(np.float64))
     o.step(1)  # first touch of the arrays
     t0 = time.perf_counter()
     o.step(SAMPLE_STEPS)
@@ -179,7 +187,8 @@ def cpu_baseline_sample():
     value = n ** 3 * SAMPLE_STEPS / dt / 1e6
     return {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
             "sample": f"{n}^3 box of the same recipe ({SAMPLE_BUBBLES} bubbles R=10, u_rms 0.02, tau 0.51, "
-                      f"linear forcing), {SAMPLE_STEPS} FP64 oracle steps after 1 untimed step, "
+                      f"linear forcing{', density contrasts' if density else ''}), "
+                      f"{SAMPLE_STEPS} FP64 oracle steps after 1 untimed step, "
                       f"{dt:.1f} s"}
 
 
@@ -302,6 +311,8 @@ def main():
                     help="hit: one 256^3 bubbly HIT box (default); ensemble: the 512-box droplet batch")
     ap.add_argument("--boxes", type=int, default=512)
     ap.add_argument("--preset", choices=sorted(PRESETS), help="bubbly HIT preset (overrides --edge)")
+    ap.add_argument("--density", type=float, nargs=4, metavar=("RHO_L", "RHO_G", "TAU_L", "TAU_G"),
+                    help="density and viscosity contrasts: gas bubbles (phi = 0) in the liquid (phi = 1)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -346,6 +357,8 @@ def main():
     force = lbgb.Force(kind=lbgb.LB_FORCE_LINEAR, T_relax=w.T_relax)
     stream = torch.cuda.Stream()
     box = lbgb.Box(n, n, n, w.tau, w.M, w.W, w.sigma, force=force, storage=args.storage, stream=stream)
+    if args.density:
+        box.set_density(*args.density)
     if args.tile:
         box.set_tile(*args.tile)
     elif not args.no_tune:
@@ -353,6 +366,8 @@ def main():
         box.tune(8)
     ty, zc = box.tile()
     phi_d = w.phi if torch.is_tensor(w.phi) else torch.from_numpy(w.phi).cuda()
+    if args.density:
+        phi_d = 1.0 - phi_d  # gas bubbles: phi = 0 inside
     u_d = w.u if torch.is_tensor(w.u) else torch.from_numpy(w.u).cuda()
     box.init(phi_d, u_d)
     # clock sampling starts before the warm-up so it is running throughout the timed region
@@ -383,7 +398,7 @@ def main():
     value, t_max = whole_job(ms, N, args.steps, world, pg)
 
     # ---- end to end through the public API with pinned host buffers
-    phi_h = (phi_d.cpu() if torch.is_tensor(w.phi) else torch.from_numpy(w.phi)).pin_memory()
+    phi_h = phi_d.cpu().pin_memory()
     u_h = (u_d.cpu() if torch.is_tensor(w.u) else torch.from_numpy(w.u)).pin_memory()
     del phi_d, u_d
     rho_o = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
@@ -410,12 +425,13 @@ def main():
         kern_avg_s = kern_ms / max(kern_n, 1) * 1e-3
         achieved = bps * N / kern_avg_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": measured_traffic(args.storage, N, [32, ty, zc]), "kernel": "fused_step_kernel", "bytes_per_site": bps,
+                "traffic": measured_traffic(args.storage + ("+density" if args.density else ""), N, [32, ty, zc]),
+                "kernel": "fused_step_kernel" + (" (VD)" if args.density else ""), "bytes_per_site": bps,
                 "kernel_ms_avg": kern_avg_s * 1e3, "peak_source": peak_kind}
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             try:
-                cpu = cpu_baseline_sample()
+                cpu = cpu_baseline_sample(args.density)
             except Exception as ex:  # report, do not fail the benchmark line
                 cpu = {"error": str(ex)}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -423,7 +439,9 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"{n}^3 periodic bubbly forced HIT, {nb} bubbles R="
                                        f"{PRESETS[args.preset][2] if args.preset else 10.0:g}, W=3, sigma=0.01, "
-                                       f"tau={w.tau}, M=0.1, u_rms=0.02, linear forcing",
+                                       f"tau={w.tau}, M=0.1, u_rms=0.02, linear forcing"
+                                       + (", gas bubbles (phi = 0) with rho_l, rho_g, tau_l, tau_g = "
+                                          + ", ".join(f"{v:g}" for v in args.density) if args.density else ""),
                            "edge": n, "storage": args.storage, "tile": [32, ty, zc],
                            "l2": "inputs larger than L2 (populations %.2f GB), no flush" % (bps * N / 2 / 1e9),
                            "parallelism": f"replicas x{world}"},

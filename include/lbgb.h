@@ -117,6 +117,30 @@ int lb_set_stream(lb_ctx* ctx, void* stream);
  */
 int lb_init(lb_ctx* ctx, const float* phi, const float* u);
 
+/*
+ * lb_set_density -- density and viscosity contrasts (Sec. 2.3, after Fakhari
+ * et al. 2017).  From the next step on, the mixture density and the relaxation
+ * time follow phi linearly,
+ *   rho = rho_g + phi (rho_l - rho_g),  tau = tau_g + phi (tau_l - tau_g),
+ * (phi = 1 is the liquid, phi = 0 the gas; tau of lb_create is no longer used)
+ * and the total force F = F^s + F^ext + F^p + F^nu enters the velocity, the
+ * Guo source and a2 as the acceleration F/rho, with
+ *   F^p  = -(p* - 1) cs^2 grad rho   (the pressure measured from its rest value),
+ *   F^nu = -(1 - omega/2) [Pi - Pi^eq] grad rho,  omega = 1/tau of the site,
+ * Pi the second moment of the pre-collision populations and Pi^eq that of the
+ * equilibrium at the velocity without F^nu's own half-force.  The external
+ * force of lb_force is a force density.  eps in lb_diagnostics sums each
+ * site's own nu.  lb_moments still returns p* as rho; the pressure is
+ * p = p* rho(phi) cs^2.  Put the denser phase at phi = 1: the phase-field step
+ * overshoots phi slightly above 1 but not below 0, and an overshoot into a light
+ * phase at phi = 1 drives rho(phi) towards 0 (such runs blow up within tens of
+ * steps at ratio 10).  Every storage supports it; it stays on for the life
+ * of the context (a checkpoint holds the state, not these parameters: set them
+ * again on the context that loads it).
+ * Errors: LB_EINVAL unless rho_l, rho_g > 0 and tau_l, tau_g > 1/2 (finite).
+ */
+int lb_set_density(lb_ctx* ctx, double rho_l, double rho_g, double tau_l, double tau_g);
+
 /* lb_step -- advance n >= 0 full time steps (steps 1-13), asynchronously.
  * Runs of two or more steps replay a captured CUDA graph. */
 int lb_step(lb_ctx* ctx, int n);
@@ -157,7 +181,8 @@ int lb_get_tile(const lb_ctx* ctx, int* ty, int* zc);
  * the context uninitialised; after lb_init it times on a scratch box with this
  * box's nx, ny, storage and min(nz, 128) planes, allocated and freed here,
  * and leaves the state untouched.  Results are cached per (device name, nx,
- * ny, nz, storage) in the file named by LBGB_TUNE_CACHE, if set.
+ * ny, nz, storage, density contrasts on or off) in the file named by
+ * LBGB_TUNE_CACHE, if set.
  */
 int lb_tune(lb_ctx* ctx, int steps);
 

@@ -48,7 +48,8 @@ int fail(int code, const char* fmt, ...) {
 struct FinalizeArgs {
     int mode;        // MODE_STEP or MODE_INIT
     int force_kind;
-    double nu, tau, T_relax, K_target_param;
+    double eps_per_aa;  // eps = eps_per_aa * (sum of the per-site a2:a2 partials)
+    double T_relax, K_target_param;
 };
 
 // One block: deterministic FP64 sum of the per-block partials, then the
@@ -76,9 +77,9 @@ __global__ void __launch_bounds__(256) finalize_kernel(const double* __restrict_
             st->mass = 0.0;
             st->flags = bad ? 1 : 0;
         } else {
-            // eps = 2 nu sum S:S, S = -a2/(2 cs^2 tau) = -(3/(2 tau)) a2
-            const double s = 1.5 / fa.tau;
-            const double eps = 2.0 * fa.nu * s * s * v2;
+            // eps = 2 nu sum S:S, S = -a2/(2 cs^2 tau) = -(3/(2 tau)) a2 (with density
+            // contrasts the partials already carry each site's 2 nu (3/(2 tau))^2)
+            const double eps = fa.eps_per_aa * v2;
             double An = 0.0;
             if (fa.force_kind == FK_LINEAR && K > 0) An = (eps + (st->K_target - K) / fa.T_relax) / (2.0 * K);
             st->diag[0] = Phi; st->diag[1] = K; st->diag[2] = eps; st->diag[3] = umax; st->diag[4] = An;
@@ -126,6 +127,9 @@ struct lb_ctx {
     cudaGraphExec_t graph = nullptr;  // two steps starting at even parity
     int graph_ty = 0, graph_zc = 0;
 
+    bool vd = false;  // density and viscosity contrasts (lb_set_density)
+    double rho_l = 1.0, rho_g = 1.0, tau_l = 1.0, tau_g = 1.0;
+
     bool timing = false;                       // event pairs around fused launches
     std::vector<cudaEvent_t> ev_start, ev_stop;
     size_t ev_used = 0;
@@ -159,6 +163,12 @@ StepArgs base_args(const lb_ctx* c) {
     a.abc = c->abc;
     a.st = c->st;
     a.partials = c->partials;
+    if (c->vd) {
+        a.rho_g = (float)c->rho_g;
+        a.drho = (float)(c->rho_l - c->rho_g);
+        a.tau_g = (float)c->tau_g;
+        a.dtau = (float)(c->tau_l - c->tau_g);
+    }
     return a;
 }
 
@@ -184,6 +194,15 @@ cudaError_t launch_any(const lb_ctx* c, int mode, int parity, int ty, dim3 grid,
                        cudaStream_t s) {
     // float4 phase-A loads need 16-byte aligned rows: nx % 4 == 0 (planes then start aligned too)
     const bool vec = (c->nx % 4) == 0;
+    if (c->vd && mode != MODE_INIT) {
+        switch (c->storage) {
+            case LB_F32_MOMENTS: return launch_fused_vd<float, true>(mode, parity, ty, vec, grid, a, s);
+            case LB_F32: return launch_fused_vd<float, false>(mode, parity, ty, vec, grid, a, s);
+            case LB_F16_SHIFTED: return launch_fused_vd<__half, false>(mode, parity, ty, vec, grid, a, s);
+            case LB_BF16_SHIFTED: return launch_fused_vd<__nv_bfloat16, false>(mode, parity, ty, vec, grid, a, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (c->storage) {
         case LB_F32_MOMENTS: return launch_fused_mc(mode, parity, ty, vec, grid, a, s);
         case LB_F32: return launch_fused<float>(mode, parity, ty, vec, grid, a, s);
@@ -197,8 +216,12 @@ FinalizeArgs fin_args(const lb_ctx* c, int mode) {
     FinalizeArgs fa;
     fa.mode = mode;
     fa.force_kind = c->force.kind;
-    fa.tau = c->tau;
-    fa.nu = (c->tau - 0.5) / 3.0;
+    if (c->vd) {
+        fa.eps_per_aa = 1.0;
+    } else {
+        const double nu = (c->tau - 0.5) / 3.0, s = 1.5 / c->tau;
+        fa.eps_per_aa = 2.0 * nu * s * s;
+    }
     fa.T_relax = c->force.T_relax;
     fa.K_target_param = c->force.K_target;
     return fa;
@@ -298,10 +321,15 @@ int tune_chunks(const lb_ctx* c, int ty, int zcs[6]) {
     const bool vec = (c->nx % 4) == 0;
     int per_sm = 0;
     switch (c->storage) {
-        case LB_F32: per_sm = fused_blocks_per_sm<float>(ty, vec); break;
-        case LB_F16_SHIFTED: per_sm = fused_blocks_per_sm<__half>(ty, vec); break;
-        case LB_BF16_SHIFTED: per_sm = fused_blocks_per_sm<__nv_bfloat16>(ty, vec); break;
-        case LB_F32_MOMENTS: per_sm = fused_mc_blocks_per_sm(ty, vec); break;
+        case LB_F32: per_sm = c->vd ? fused_vd_blocks_per_sm<float, false>(ty, vec) : fused_blocks_per_sm<float>(ty, vec); break;
+        case LB_F16_SHIFTED:
+            per_sm = c->vd ? fused_vd_blocks_per_sm<__half, false>(ty, vec) : fused_blocks_per_sm<__half>(ty, vec);
+            break;
+        case LB_BF16_SHIFTED:
+            per_sm = c->vd ? fused_vd_blocks_per_sm<__nv_bfloat16, false>(ty, vec)
+                           : fused_blocks_per_sm<__nv_bfloat16>(ty, vec);
+            break;
+        case LB_F32_MOMENTS: per_sm = c->vd ? fused_vd_blocks_per_sm<float, true>(ty, vec) : fused_mc_blocks_per_sm(ty, vec); break;
     }
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
@@ -566,6 +594,18 @@ long long lb_time(const lb_ctx* c) { return c ? c->t : -1; }
 
 long long lb_launch_count(const lb_ctx* c) { return c ? c->launches : -1; }
 
+int lb_set_density(lb_ctx* c, double rho_l, double rho_g, double tau_l, double tau_g) {
+    if (!c) return fail(LB_EINVAL, "ctx is NULL");
+    if (!(rho_l > 0) || !(rho_g > 0) || !(tau_l > 0.5) || !(tau_g > 0.5) || !isfinite(rho_l) || !isfinite(rho_g) ||
+        !isfinite(tau_l) || !isfinite(tau_g))
+        return fail(LB_EINVAL, "lb_set_density: need rho > 0 and tau > 1/2, got rho %g, %g, tau %g, %g", rho_l, rho_g,
+                    tau_l, tau_g);
+    c->vd = true;
+    c->rho_l = rho_l; c->rho_g = rho_g; c->tau_l = tau_l; c->tau_g = tau_g;
+    drop_graph(c);  // the captured launches carry the old kernel and arguments
+    return LB_OK;
+}
+
 int lb_set_timing(lb_ctx* c, int on) {
     if (!c) return fail(LB_EINVAL, "ctx is NULL");
     c->timing = on != 0;
@@ -691,7 +731,7 @@ int lb_tune(lb_ctx* c, int steps) {
         if (*p == ' ') *p = '_';
     const char* cache = getenv("LBGB_TUNE_CACHE");
     char key[512];
-    snprintf(key, sizeof(key), "%s %d %d %d %d", dev_name, c->nx, c->ny, c->nz, c->storage);
+    snprintf(key, sizeof(key), "%s %d %d %d %d%s", dev_name, c->nx, c->ny, c->nz, c->storage, c->vd ? "vd" : "");
     if (cache) {
         FILE* fp = fopen(cache, "r");
         if (fp) {
@@ -729,6 +769,7 @@ int lb_tune(lb_ctx* c, int steps) {
         rc = lb_create(c->nx, c->ny, nzt, c->tau, c->M, c->W, c->sigma, &c->force, c->storage, &s);
         if (rc) return rc;
         lb_set_stream(s, c->stream);
+        if (c->vd) lb_set_density(s, c->rho_l, c->rho_g, c->tau_l, c->tau_g);
         cudaError_t e = cudaMalloc(&z, (size_t)s->N * 4 * sizeof(float));
         if (e != cudaSuccess) {
             lb_destroy(s);

@@ -85,6 +85,9 @@ struct StepArgs {
     // of the post-collision polynomial f*_i/w_i - 1 of each site (see quad_poly27)
     const float* cin[10];   // at t (written by step t-1, or by INIT at t = 0)
     float* cout[10];        // at t+1 (INIT: at 0)
+    // density and viscosity contrasts (kernels with VD = true): rho and tau
+    // linear in phi, rho = rho_g + phi drho, tau = tau_g + phi dtau
+    float rho_g, drho, tau_g, dtau;
 };
 
 // ---------------------------------------------------------- storage codecs
@@ -321,6 +324,41 @@ __host__ __device__ __forceinline__ void collide_site(float pp, float m0, float 
     quad_poly27(e0, Pp, Pm, Xxy, Xxz, Xyz, v);
 }
 
+// Density and viscosity contrasts (Sec. 2.3), per site, from phi, grad phi,
+// the shifted moments (p' = p* - 1, m, P' = Pi - I/3) and the force density
+// F = F^s + F^ext:
+//   rho = rho_g + phi drho, tau = tau_g + phi dtau, omega = 1/tau;
+//   F^p = -p' cs^2 grad rho (the pressure measured from its rest value);
+//   u0 = (m + F'/(2 rho)) / (1 - A/2), F' = F + F^p;
+//   F^nu = -(nu omega / cs^2) (Pi - Pi^eq(u0)) grad rho, nu omega / cs^2 = 1 - omega/2,
+//          Pi - Pi^eq(u0) = P' - (p'/3) I - u0 u0;
+// returns the acceleration (F' + F^nu)/rho in F (which collide_coefs then
+// treats as the force of a unit-density fluid), omega, and the weight
+// 2 nu (3/(2 tau))^2 = 1.5 (1 - omega/2) omega that turns a2:a2 into the
+// site's share of eps.
+__host__ __device__ __forceinline__ void vd_force(float phi, float gp0, float gp1, float gp2, float pp, float m0,
+                                                  float m1, float m2, float P00, float P11, float P22, float P01,
+                                                  float P02, float P12, float A_lin, float rho_g, float drho,
+                                                  float tau_g, float dtau, float& F0, float& F1, float& F2,
+                                                  float& omega, float& aa_w) {
+    const float rho = fmaf(phi, drho, rho_g);
+    const float irho = 1.f / rho;
+    omega = 1.f / fmaf(phi, dtau, tau_g);
+    const float q0 = drho * gp0, q1 = drho * gp1, q2 = drho * gp2;  // grad rho
+    const float fp = pp * (-1.f / 3.f);
+    const float G0 = fmaf(fp, q0, F0), G1 = fmaf(fp, q1, F1), G2 = fmaf(fp, q2, F2);
+    const float h = 0.5f * irho, inv = 1.f / (1.f - 0.5f * A_lin);
+    const float v0 = fmaf(h, G0, m0) * inv, v1 = fmaf(h, G1, m1) * inv, v2 = fmaf(h, G2, m2) * inv;
+    const float p3 = pp * (1.f / 3.f);
+    const float n00 = P00 - p3 - v0 * v0, n11 = P11 - p3 - v1 * v1, n22 = P22 - p3 - v2 * v2;
+    const float n01 = P01 - v0 * v1, n02 = P02 - v0 * v2, n12 = P12 - v1 * v2;
+    const float c = 0.5f * omega - 1.f;  // -nu omega / cs^2
+    F0 = fmaf(c, fmaf(n00, q0, fmaf(n01, q1, n02 * q2)), G0) * irho;
+    F1 = fmaf(c, fmaf(n01, q0, fmaf(n11, q1, n12 * q2)), G1) * irho;
+    F2 = fmaf(c, fmaf(n02, q0, fmaf(n12, q1, n22 * q2)), G2) * irho;
+    aa_w = 1.5f * (1.f - 0.5f * omega) * omega;
+}
+
 // One pulled column of the moment-only storage: the three directions
 // (cx, cy, -1), (cx, cy, 0), (cx, cy, +1) of the post-collision polynomial of
 // a source site whose ten coefficients are read through ld(k), k in the order
@@ -377,7 +415,8 @@ __device__ __forceinline__ void pull_column(LD ld, float& vm, float& v0, float& 
 // f_i(x) = w_i (1 + v_i(x - c_i)) from the neighbours' coefficients.  With MC,
 // PAR = 0 evaluates the site's own coefficients (t = 0, where lb_init stored
 // those of f^eq) and PAR = 1 pulls; FT is float.
-template <class FT, int TY, int MODE, int PAR, bool VEC, bool MC = false>
+// VD adds the density and viscosity contrasts of Sec. 2.3 (see vd_force).
+template <class FT, int TY, int MODE, int PAR, bool VEC, bool MC = false, bool VD = false>
 __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 512 / (32 * TY)))
 fused_step_kernel(const StepArgs a) {
 #define TILE_BX blockIdx.x
@@ -469,6 +508,7 @@ batch_step_kernel(const __grid_constant__ BatchArgs b) {
             const BoxTileArgs<FT>& a = t;
             constexpr int MODE = MODE_STEP;
             constexpr bool MC = MC_;
+            constexpr bool VD = false;
 #define TILE_BX tbx
 #define TILE_BY tby
 #define TILE_BZ tbz
@@ -509,5 +549,13 @@ int batch_blocks_per_sm(int ty, bool vec);
 // vec selects the float4 phase-A loads (requires nx % 4 == 0).
 template <class FT>
 cudaError_t launch_fused(int mode, int parity, int ty, bool vec, dim3 grid, const StepArgs& a, cudaStream_t st);
+
+// The same kernels with the density and viscosity contrasts (VD = true), mode
+// STEP or MOMENTS, for the AA storage FT (MC = false) or the moment-only
+// storage (FT float, MC = true, parity = pull).  Defined in lbgb_step_vd_*.cu.
+template <class FT, bool MC>
+cudaError_t launch_fused_vd(int mode, int parity, int ty, bool vec, dim3 grid, const StepArgs& a, cudaStream_t st);
+template <class FT, bool MC>
+int fused_vd_blocks_per_sm(int ty, bool vec);
 
 }  // namespace lbgb

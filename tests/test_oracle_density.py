@@ -84,6 +84,30 @@ def test_laplace_law_at_a_density_contrast(orc, rho_l, rho_g):
     assert umax < 5e-5, umax
 
 
+# ------------------------------------------------------------ orientation
+def test_light_phase_at_phi_one_is_not_the_supported_orientation(orc):
+    """The conservative Allen-Cahn step overshoots phi above 1, never below 0 (its
+    advective flux 4 phi u vanishes only at phi = 0), so the lighter phase belongs
+    at phi = 0: the same gas bubbles with the gas at phi = 1 run away (rho(phi)
+    -> 0 in the overshoot) within 20 steps on the oracle, while the phi = 0
+    orientation stays bounded.  (The GPU tests and the benchmark follow this
+    convention.)"""
+    w = inputs.bubbly_hit(32, 1, 8.0, seed=2)
+    ranges = {}
+    for name, phi, dens in (("gas_at_0", 1.0 - w.phi.astype(np.float64), (1.0, 0.1, 0.51, 0.55)),
+                            ("gas_at_1", w.phi.astype(np.float64), (0.1, 1.0, 0.55, 0.51))):
+        o = orc.Oracle(32, 32, 32, w.tau, w.M, w.W, w.sigma, force_kind=orc.FORCE_LINEAR, T_relax=w.T_relax)
+        o.set_density(*dens)
+        o.init(phi, w.u.astype(np.float64))
+        o.step(30)
+        _, _, ph = o.moments()
+        fin = bool(np.isfinite(ph).all())
+        ranges[name] = (float(ph.min()) if fin else -np.inf, float(ph.max()) if fin else np.inf, fin)
+        o.close()
+    assert ranges["gas_at_0"][2] and -1e-3 < ranges["gas_at_0"][0] and ranges["gas_at_0"][1] < 1.02, ranges
+    assert ranges["gas_at_1"][1] > 1.1, ranges
+
+
 # -------------------------------------------------------------- layered shear
 def _phi_layers(x, nx, W, x0, x1):
     """tanh layers phi = 1 for x0 < x < x1 (periodic), evaluated at any x."""
