@@ -57,6 +57,17 @@ PRESETS = {
 }
 
 
+# The paper's two-component benchmark case (Sec. 4): one droplet of the heavier
+# phase at density contrast 100 in a lighter carrier, kinematic viscosity 0.005
+# (tau = 0.515) in both phases, 512^3 per GPU.  The radius, W, sigma and M are
+# not given: R = edge/4, W = 3, sigma = 0.01, M = 0.1, zero initial velocity.
+DROPLET_EDGE, DROPLET_TAU, DROPLET_DENSITY = 512, 0.515, (100.0, 1.0, 0.515, 0.515)
+
+
+def droplet_workload(edge: int):
+    return inputs.static_droplet(edge=edge, R=edge / 4.0, tau=DROPLET_TAU)
+
+
 def workload(edge: int):
     nb = max(1, round(64 * (edge / 256) ** 3))
     return inputs.bubbly_hit(edge, nb, 10.0, seed=2), nb
@@ -171,8 +182,21 @@ def cpu_baseline_sample(density=None):
     import oracle
 
     oracle.build()
-    w, _ = workload(SAMPLE_EDGE)
     n = SAMPLE_EDGE
+    if density == "droplet":
+        w = droplet_workload(n)
+        o = oracle.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma)
+        o.set_density(*DROPLET_DENSITY)
+        o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
+        o.step(1)
+        t0 = time.perf_counter()
+        o.step(SAMPLE_STEPS)
+        dt = time.perf_counter() - t0
+        o.close()
+        return {"value": n ** 3 * SAMPLE_STEPS / dt / 1e6, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                "sample": f"{n}^3 box of the same recipe (droplet R={n // 4}, density ratio 100, tau 0.515), "
+                          f"{SAMPLE_STEPS} FP64 oracle steps after 1 untimed step, {dt:.1f} s"}
+    w, _ = workload(SAMPLE_EDGE)
     o = oracle.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma, force_kind=oracle.FORCE_LINEAR, T_relax=w.T_relax)
     phi = w.phi.astype(np.float64)
     if density:
@@ -303,12 +327,13 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "moments"],
                     help="population storage: FP32/FP16/BF16 AA populations, or the moment-only coefficients")
-    ap.add_argument("--edge", type=int, default=256)
+    ap.add_argument("--edge", type=int, default=None, help="box edge (default 256; 512 for --workload droplet)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--tile", type=int, nargs=2, metavar=("TY", "ZC"), help="fixed launch shape (skips tuning)")
-    ap.add_argument("--workload", default="hit", choices=["hit", "ensemble"],
-                    help="hit: one 256^3 bubbly HIT box (default); ensemble: the 512-box droplet batch")
+    ap.add_argument("--workload", default="hit", choices=["hit", "ensemble", "droplet"],
+                    help="hit: one 256^3 bubbly HIT box (default); ensemble: the 512-box droplet batch; "
+                         "droplet: the paper's two-component benchmark (512^3, one droplet, density ratio 100)")
     ap.add_argument("--boxes", type=int, default=512)
     ap.add_argument("--preset", choices=sorted(PRESETS), help="bubbly HIT preset (overrides --edge)")
     ap.add_argument("--density", type=float, nargs=4, metavar=("RHO_L", "RHO_G", "TAU_L", "TAU_G"),
@@ -346,15 +371,21 @@ def main():
     barrier()
     from paper_2505_01126_gb300 import lbgb
 
-    if args.preset:
+    droplet = args.workload == "droplet"
+    if droplet:
+        args.edge = args.edge or DROPLET_EDGE
+        args.density = DROPLET_DENSITY
+        w, nb = droplet_workload(args.edge), 0
+    elif args.preset:
         w, nb = preset_workload(args.preset)
         args.edge = w.n[0]
         torch.cuda.empty_cache()  # the generator's FFT scratch goes back before the box is allocated
     else:
+        args.edge = args.edge or 256
         w, nb = workload(args.edge)
     n = args.edge
     N = n ** 3
-    force = lbgb.Force(kind=lbgb.LB_FORCE_LINEAR, T_relax=w.T_relax)
+    force = None if droplet else lbgb.Force(kind=lbgb.LB_FORCE_LINEAR, T_relax=w.T_relax)
     stream = torch.cuda.Stream()
     box = lbgb.Box(n, n, n, w.tau, w.M, w.W, w.sigma, force=force, storage=args.storage, stream=stream)
     if args.density:
@@ -366,7 +397,7 @@ def main():
         box.tune(8)
     ty, zc = box.tile()
     phi_d = w.phi if torch.is_tensor(w.phi) else torch.from_numpy(w.phi).cuda()
-    if args.density:
+    if args.density and not droplet:
         phi_d = 1.0 - phi_d  # gas bubbles: phi = 0 inside
     u_d = w.u if torch.is_tensor(w.u) else torch.from_numpy(w.u).cuda()
     box.init(phi_d, u_d)
@@ -431,17 +462,21 @@ def main():
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             try:
-                cpu = cpu_baseline_sample(args.density)
+                cpu = cpu_baseline_sample("droplet" if droplet else args.density)
             except Exception as ex:  # report, do not fail the benchmark line
                 cpu = {"error": str(ex)}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"{n}^3 periodic bubbly forced HIT, {nb} bubbles R="
-                                       f"{PRESETS[args.preset][2] if args.preset else 10.0:g}, W=3, sigma=0.01, "
-                                       f"tau={w.tau}, M=0.1, u_rms=0.02, linear forcing"
-                                       + (", gas bubbles (phi = 0) with rho_l, rho_g, tau_l, tau_g = "
-                                          + ", ".join(f"{v:g}" for v in args.density) if args.density else ""),
+                "config": {"workload": (f"{n}^3 periodic box, one droplet R={n / 4:g} of the heavier phase, "
+                                        f"density ratio 100, nu=0.005 (tau={w.tau}) in both phases, W=3, "
+                                        f"sigma=0.01, M=0.1, zero initial velocity, no forcing (the paper's "
+                                        f"two-component benchmark case)") if droplet else
+                                       (f"{n}^3 periodic bubbly forced HIT, {nb} bubbles R="
+                                        f"{PRESETS[args.preset][2] if args.preset else 10.0:g}, W=3, sigma=0.01, "
+                                        f"tau={w.tau}, M=0.1, u_rms=0.02, linear forcing"
+                                        + (", gas bubbles (phi = 0) with rho_l, rho_g, tau_l, tau_g = "
+                                           + ", ".join(f"{v:g}" for v in args.density) if args.density else "")),
                            "edge": n, "storage": args.storage, "tile": [32, ty, zc],
                            "l2": "inputs larger than L2 (populations %.2f GB), no flush" % (bps * N / 2 / 1e9),
                            "parallelism": f"replicas x{world}"},
@@ -450,6 +485,10 @@ def main():
                         "note": "lb_init from pinned host fields, K x (lb_step(1) + lb_diagnostics), "
                                 "lb_moments to pinned host"},
                 "clocks": clk, "gpu_launches": launches,
+                **({"paper_context": {"value": 105480.0 / 64, "unit": "MLUPS per GPU",
+                                      "what": "two-component weak scaling, 512^3 per GPU: 105.48 GLUPS on 64 "
+                                              "A100 (Leonardo) divided by 64; derived, not printed"}}
+                   if droplet else {}),
                 "diagnostics": {"Phi": diag[0], "K": diag[1], "eps": diag[2], "umax": diag[3], "A": diag[4]}}
         print(json.dumps(line), flush=True)
     box.close()

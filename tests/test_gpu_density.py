@@ -309,3 +309,61 @@ def test_gas_bubbles_64_stay_finite_for_400_steps(lbgb):
     assert np.isfinite(d).all()
     assert abs(d[0] - d0[0]) <= 1e-4 * abs(d0[0])
     assert d[3] < 0.2
+
+
+def test_paper_droplet_case_256_full_parity(lbgb, orc):
+    """The paper's two-component benchmark recipe (one heavier droplet, density
+    ratio 100, nu = 0.005 in both phases) at 256^3 with R = 64, in the tuned
+    launch shape: 2 steps, every site compared with the oracle."""
+    import bench
+
+    n = 256
+    w = bench.droplet_workload(n)
+    dens = bench.DROPLET_DENSITY
+    b = lbgb.Box(n, n, n, w.tau, w.M, w.W, w.sigma)
+    b.set_density(*dens)
+    b.tune(2)
+    b.init(w.phi, w.u)
+    b.step(2)
+    got = b.moments_numpy()
+    dg = b.diagnostics()
+    b.close()
+    o = orc.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma)
+    o.set_density(*dens)
+    o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
+    o.step(2)
+    want = o.moments()
+    do = o.diagnostics()
+    o.close()
+    e = max_err(got, want)
+    assert max(e) <= TOL, e
+    check_diagnostics(dg, do, n ** 3)
+
+
+def test_paper_droplet_case_512_properties(lbgb):
+    """The benchmark's own 512^3 box (R = 128) in the tuned launch shape, 20 steps:
+    finite, phase mass conserved to FP32 rounding, and the droplet's mirror
+    symmetries about the box centre kept to 1e-6 in every field (the tiles and
+    z-chunks of the launch do not break them)."""
+    import bench
+
+    n = 512
+    w = bench.droplet_workload(n)
+    b = lbgb.Box(n, n, n, w.tau, w.M, w.W, w.sigma)
+    b.set_density(*bench.DROPLET_DENSITY)
+    b.tune(2)
+    b.init(w.phi, w.u)
+    d0 = b.diagnostics()
+    b.step(20)
+    d = b.diagnostics()
+    rho, u, phi = b.moments_numpy()
+    b.close()
+    assert np.isfinite(d).all()
+    assert abs(d[0] - d0[0]) <= 1e-6 * d0[0]
+    for axis in range(3):
+        assert np.abs(phi - np.flip(phi, axis)).max() <= 1e-6
+        assert np.abs(rho - np.flip(rho, axis)).max() <= 1e-6
+        # u is odd under the mirror along its own axis, even along the others
+        for a in range(3):
+            s = -1.0 if a == 2 - axis else 1.0
+            assert np.abs(u[a] - s * np.flip(u[a], axis)).max() <= 1e-6
