@@ -22,7 +22,8 @@
  *   - optional (orc_set_density): density and viscosity contrasts (Sec. 2.3),
  *     mixture density rho(phi) and relaxation time tau(phi) linear in phi, the
  *     pressure force F^p and the viscous correction F^nu added to the total
- *     force, which enters the velocity, the source and a2 as F/rho.
+ *     force, which enters the velocity, the source and a2 as F/rho; optional
+ *     (orc_set_gravity) buoyancy (rho(phi) - rho_ref) g (Sec. 5.2).
  *
  * Every stage is a separate loop over all sites writing a full field, in the
  * order of the method.  Two copies of each population set are kept; streaming
@@ -46,7 +47,10 @@
  *     coefficient nu omega / cs^2 = 1 - omega/2 and f - f^eq taken from the
  *     pre-collision populations, f^eq at the velocity without F^nu's own
  *     half-force; tau (so nu) linear in phi; the body force is a force density
- *     (acceleration F/rho); eps sums each site's own nu.
+ *     (acceleration F/rho); eps sums each site's own nu;
+ *   - buoyancy: the paper does not say how the net force of gravity on a
+ *     periodic box is closed; here the caller gives a reference density, and
+ *     rho_ref = the mean density makes the total buoyancy force zero.
  */
 #include "lb_oracle.h"
 
@@ -122,6 +126,7 @@ struct orc_state {
     int vd;
     double rho_l, rho_g, tau_l, tau_g; /* of the phi = 1 and phi = 0 phases */
     double* om;                        /* per-site relaxation rate 1/tau(phi) */
+    double gb[3], rho_ref;             /* buoyancy (rho(phi) - rho_ref) g, off while g = 0 */
 };
 
 static int g_threads = 0;
@@ -402,12 +407,13 @@ static void external_force(const orc_state* s, int x, int y, int z, double Fe[3]
  *   tau = tau_g + phi (tau_l - tau_g) (linear in tau, so in nu), omega = 1/tau;
  *   F^p = -(p* - 1) cs^2 grad rho, the pressure p* measured from its rest value 1
  *         (the equilibrium carries p* = 1 at rest);
- *   u0  = (m + (F^s + F^ext + F^p)/(2 rho)) / (1 - A/2);
+ *   F^b = (rho - rho_ref) g, buoyancy (zero unless orc_set_gravity);
+ *   u0  = (m + (F^s + F^ext + F^b + F^p)/(2 rho)) / (1 - A/2);
  *   F^nu_a = -(nu omega / cs^2) sum_b [Pi_ab - (p* cs^2 d_ab + u0_a u0_b)] d_b rho,
  *          nu omega / cs^2 = (tau - 1/2) / tau = 1 - omega/2; Pi the second
  *          moment of the pre-collision f, the equilibrium taken at u0 (before
  *          F^nu's own half-force);
- *   u = (m + F/(2 rho)) / (1 - A/2), F = F^s + F^ext + F^p + F^nu,
+ *   u = (m + F/(2 rho)) / (1 - A/2), F = F^s + F^ext + F^b + F^p + F^nu,
  * and the source, the Hermite coefficient and the collision see the
  * acceleration F/rho + A u.  With rho_l = rho_g = 1 and tau_l = tau_g every
  * added term is an exact zero and these are the density-ratio-1 values. */
@@ -427,7 +433,7 @@ static void velocity_force_vd(orc_state* s, double A) {
                 external_force(s, x, y, z, Fe);
                 for (int a = 0; a < 3; ++a) {
                     grho[a] = dr * s->grad[a * N + i];
-                    Fo[a] = s->Fs[a * N + i] + Fe[a] - pp * CS2 * grho[a];
+                    Fo[a] = s->Fs[a * N + i] + Fe[a] + (rho - s->rho_ref) * s->gb[a] - pp * CS2 * grho[a];
                     u0[a] = (s->mom[a * N + i] + 0.5 * Fo[a] / rho) / (1 - 0.5 * A);
                 }
                 /* Pi - Pi^eq at u0; Pi is stored xx, yy, zz, xy, xz, yz */
@@ -687,6 +693,13 @@ int orc_set_density(orc_state* s, double rho_l, double rho_g, double tau_l, doub
     }
     s->vd = 1;
     s->rho_l = rho_l; s->rho_g = rho_g; s->tau_l = tau_l; s->tau_g = tau_g;
+    return 0;
+}
+
+int orc_set_gravity(orc_state* s, const double g[3], double rho_ref) {
+    if (!s || !s->vd || !g || !isfinite(g[0]) || !isfinite(g[1]) || !isfinite(g[2]) || !isfinite(rho_ref)) return -1;
+    for (int a = 0; a < 3; ++a) s->gb[a] = g[a];
+    s->rho_ref = rho_ref;
     return 0;
 }
 

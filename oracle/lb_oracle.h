@@ -49,6 +49,11 @@ long long orc_time(const orc_state* s);
  * Returns -1 on bad input. */
 int  orc_set_density(orc_state* s, double rho_l, double rho_g, double tau_l, double tau_g);
 
+/* Buoyancy (Sec. 5.2) with density contrasts on: adds (rho(phi) - rho_ref) g
+ * to the force density.  Returns -1 unless orc_set_density was called and the
+ * arguments are finite. */
+int  orc_set_gravity(orc_state* s, const double g[3], double rho_ref);
+
 /* Raw populations: f is 27N in the oracle's own direction order (see
  * orc_lattice27), g is 7N in the order of orc_lattice7. */
 void orc_get_populations(const orc_state* s, double* f, double* g);

@@ -50,6 +50,7 @@ def _load():
             lib.orc_init.restype = ctypes.c_int
             lib.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
             lib.orc_set_density.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 4
+            lib.orc_set_gravity.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double]
             lib.orc_step.restype = ctypes.c_int
             lib.orc_moments.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
             lib.orc_diagnostics.argtypes = [ctypes.c_void_p, _dp]
@@ -191,6 +192,12 @@ class Oracle:
         phi = 0 phases, linear in phi in between."""
         if self._lib.orc_set_density(self._h, float(rho_l), float(rho_g), float(tau_l), float(tau_g)) != 0:
             raise ValueError("oracle rejected the density parameters")
+
+    def set_gravity(self, g, rho_ref):
+        """Buoyancy (rho(phi) - rho_ref) g (needs set_density first)."""
+        gv = _f64(g)
+        if self._lib.orc_set_gravity(self._h, _ptr(gv), float(rho_ref)) != 0:
+            raise ValueError("oracle rejected the gravity parameters")
 
     def step(self, n: int = 1):
         if self._lib.orc_step(self._h, int(n)) != 0:
