@@ -12,9 +12,10 @@ the measured HBM bandwidth reached by the fused kernel.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                        [--storage f32|f16|bf16|moments] [--edge E]
-                       [--density RHO_L RHO_G TAU_L TAU_G]
+                       [--density RHO_L RHO_G TAU_L TAU_G] [--gravity GX,GY,GZ]
 --density runs the same box with density and viscosity contrasts (Sec. 2.3):
 the bubbles become the gas (phi = 0 inside, phi flipped), the liquid phi = 1.
+--gravity adds the buoyancy (rho(phi) - rho_ref) g with rho_ref the mean density.
 Under torchrun (N > 1) every rank advances its own replica box (weak scaling,
 no collective on the data path); value = sum of sites*steps over ranks divided
 by the slowest rank's time.
@@ -338,7 +339,11 @@ def main():
     ap.add_argument("--preset", choices=sorted(PRESETS), help="bubbly HIT preset (overrides --edge)")
     ap.add_argument("--density", type=float, nargs=4, metavar=("RHO_L", "RHO_G", "TAU_L", "TAU_G"),
                     help="density and viscosity contrasts: gas bubbles (phi = 0) in the liquid (phi = 1)")
+    ap.add_argument("--gravity", type=lambda v: tuple(float(x) for x in v.split(",")), metavar="GX,GY,GZ",
+                    help="buoyancy (rho(phi) - rho_ref) g, rho_ref the mean density (needs --density or droplet)")
     args = ap.parse_args()
+    if args.gravity is not None and len(args.gravity) != 3:
+        ap.error("--gravity takes three comma-separated components")
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -390,6 +395,15 @@ def main():
     box = lbgb.Box(n, n, n, w.tau, w.M, w.W, w.sigma, force=force, storage=args.storage, stream=stream)
     if args.density:
         box.set_density(*args.density)
+    rho_ref = None
+    if args.gravity:
+        if not args.density:
+            raise SystemExit("--gravity needs --density (or --workload droplet)")
+        phim = float(w.phi.double().mean()) if torch.is_tensor(w.phi) else float(w.phi.astype(np.float64).mean())
+        if not droplet:
+            phim = 1.0 - phim  # the flipped field of the gas-bubble case
+        rho_ref = args.density[1] + (args.density[0] - args.density[1]) * phim
+        box.set_gravity(args.gravity, rho_ref)
     if args.tile:
         box.set_tile(*args.tile)
     elif not args.no_tune:
@@ -476,7 +490,9 @@ def main():
                                         f"{PRESETS[args.preset][2] if args.preset else 10.0:g}, W=3, sigma=0.01, "
                                         f"tau={w.tau}, M=0.1, u_rms=0.02, linear forcing"
                                         + (", gas bubbles (phi = 0) with rho_l, rho_g, tau_l, tau_g = "
-                                           + ", ".join(f"{v:g}" for v in args.density) if args.density else "")),
+                                           + ", ".join(f"{v:g}" for v in args.density) if args.density else ""))
+                                       + (f", buoyancy g = ({', '.join(f'{v:g}' for v in args.gravity)}), "
+                                          f"rho_ref = {rho_ref:.6g} (mean density)" if args.gravity else ""),
                            "edge": n, "storage": args.storage, "tile": [32, ty, zc],
                            "l2": "inputs larger than L2 (populations %.2f GB), no flush" % (bps * N / 2 / 1e9),
                            "parallelism": f"replicas x{world}"},

@@ -129,6 +129,7 @@ struct lb_ctx {
 
     bool vd = false;  // density and viscosity contrasts (lb_set_density)
     double rho_l = 1.0, rho_g = 1.0, tau_l = 1.0, tau_g = 1.0;
+    double gb[3] = {0.0, 0.0, 0.0}, rho_ref = 0.0;  // buoyancy (lb_set_gravity)
 
     bool timing = false;                       // event pairs around fused launches
     std::vector<cudaEvent_t> ev_start, ev_stop;
@@ -168,6 +169,8 @@ StepArgs base_args(const lb_ctx* c) {
         a.drho = (float)(c->rho_l - c->rho_g);
         a.tau_g = (float)c->tau_g;
         a.dtau = (float)(c->tau_l - c->tau_g);
+        a.gb0 = (float)c->gb[0]; a.gb1 = (float)c->gb[1]; a.gb2 = (float)c->gb[2];
+        a.rho_ref = (float)c->rho_ref;
     }
     return a;
 }
@@ -606,6 +609,17 @@ int lb_set_density(lb_ctx* c, double rho_l, double rho_g, double tau_l, double t
     return LB_OK;
 }
 
+int lb_set_gravity(lb_ctx* c, double gx, double gy, double gz, double rho_ref) {
+    if (!c) return fail(LB_EINVAL, "ctx is NULL");
+    if (!c->vd) return fail(LB_ESTATE, "lb_set_gravity needs lb_set_density first");
+    if (!isfinite(gx) || !isfinite(gy) || !isfinite(gz) || !isfinite(rho_ref))
+        return fail(LB_EINVAL, "lb_set_gravity: non-finite argument");
+    c->gb[0] = gx; c->gb[1] = gy; c->gb[2] = gz;
+    c->rho_ref = rho_ref;
+    drop_graph(c);  // the captured launches carry the old arguments
+    return LB_OK;
+}
+
 int lb_set_timing(lb_ctx* c, int on) {
     if (!c) return fail(LB_EINVAL, "ctx is NULL");
     c->timing = on != 0;
@@ -769,7 +783,10 @@ int lb_tune(lb_ctx* c, int steps) {
         rc = lb_create(c->nx, c->ny, nzt, c->tau, c->M, c->W, c->sigma, &c->force, c->storage, &s);
         if (rc) return rc;
         lb_set_stream(s, c->stream);
-        if (c->vd) lb_set_density(s, c->rho_l, c->rho_g, c->tau_l, c->tau_g);
+        if (c->vd) {
+            lb_set_density(s, c->rho_l, c->rho_g, c->tau_l, c->tau_g);
+            lb_set_gravity(s, c->gb[0], c->gb[1], c->gb[2], c->rho_ref);
+        }
         cudaError_t e = cudaMalloc(&z, (size_t)s->N * 4 * sizeof(float));
         if (e != cudaSuccess) {
             lb_destroy(s);

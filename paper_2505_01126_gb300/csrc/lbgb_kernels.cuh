@@ -86,8 +86,10 @@ struct StepArgs {
     const float* cin[10];   // at t (written by step t-1, or by INIT at t = 0)
     float* cout[10];        // at t+1 (INIT: at 0)
     // density and viscosity contrasts (kernels with VD = true): rho and tau
-    // linear in phi, rho = rho_g + phi drho, tau = tau_g + phi dtau
+    // linear in phi, rho = rho_g + phi drho, tau = tau_g + phi dtau; buoyancy
+    // (rho - rho_ref) gb (gb = 0 without gravity)
     float rho_g, drho, tau_g, dtau;
+    float gb0, gb1, gb2, rho_ref;
 };
 
 // ---------------------------------------------------------- storage codecs
@@ -328,8 +330,9 @@ __host__ __device__ __forceinline__ void collide_site(float pp, float m0, float 
 // the shifted moments (p' = p* - 1, m, P' = Pi - I/3) and the force density
 // F = F^s + F^ext:
 //   rho = rho_g + phi drho, tau = tau_g + phi dtau, omega = 1/tau;
+//   F^b = (rho - rho_ref) gb, buoyancy (Sec. 5.2; zero when gb = 0);
 //   F^p = -p' cs^2 grad rho (the pressure measured from its rest value);
-//   u0 = (m + F'/(2 rho)) / (1 - A/2), F' = F + F^p;
+//   u0 = (m + F'/(2 rho)) / (1 - A/2), F' = F + F^b + F^p;
 //   F^nu = -(nu omega / cs^2) (Pi - Pi^eq(u0)) grad rho, nu omega / cs^2 = 1 - omega/2,
 //          Pi - Pi^eq(u0) = P' - (p'/3) I - u0 u0;
 // returns the acceleration (F' + F^nu)/rho in F (which collide_coefs then
@@ -339,14 +342,17 @@ __host__ __device__ __forceinline__ void collide_site(float pp, float m0, float 
 __host__ __device__ __forceinline__ void vd_force(float phi, float gp0, float gp1, float gp2, float pp, float m0,
                                                   float m1, float m2, float P00, float P11, float P22, float P01,
                                                   float P02, float P12, float A_lin, float rho_g, float drho,
-                                                  float tau_g, float dtau, float& F0, float& F1, float& F2,
-                                                  float& omega, float& aa_w) {
+                                                  float tau_g, float dtau, float gb0, float gb1, float gb2,
+                                                  float rho_ref, float& F0, float& F1, float& F2, float& omega,
+                                                  float& aa_w) {
     const float rho = fmaf(phi, drho, rho_g);
     const float irho = 1.f / rho;
     omega = 1.f / fmaf(phi, dtau, tau_g);
     const float q0 = drho * gp0, q1 = drho * gp1, q2 = drho * gp2;  // grad rho
+    const float br = rho - rho_ref;
     const float fp = pp * (-1.f / 3.f);
-    const float G0 = fmaf(fp, q0, F0), G1 = fmaf(fp, q1, F1), G2 = fmaf(fp, q2, F2);
+    const float G0 = fmaf(fp, q0, fmaf(br, gb0, F0)), G1 = fmaf(fp, q1, fmaf(br, gb1, F1));
+    const float G2 = fmaf(fp, q2, fmaf(br, gb2, F2));
     const float h = 0.5f * irho, inv = 1.f / (1.f - 0.5f * A_lin);
     const float v0 = fmaf(h, G0, m0) * inv, v1 = fmaf(h, G1, m1) * inv, v2 = fmaf(h, G2, m2) * inv;
     const float p3 = pp * (1.f / 3.f);

@@ -41,7 +41,7 @@ EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_step", "lb_moments", "lb
            "lb_field_stats_static", "lb_batch_create", "lb_batch_set_stream", "lb_batch_init",
            "lb_batch_step", "lb_batch_moments", "lb_batch_diagnostics", "lb_batch_set_tile", "lb_batch_get_tile",
            "lb_batch_tune", "lb_batch_sites", "lb_batch_time", "lb_batch_destroy", "lb_velocity_statistics",
-           "lb_spectrum", "lb_state_bytes", "lb_save", "lb_load", "lb_set_density"]
+           "lb_spectrum", "lb_state_bytes", "lb_save", "lb_load", "lb_set_density", "lb_set_gravity"]
 
 
 def _load():
@@ -97,6 +97,7 @@ def _load():
     lib.lb_state_bytes.restype = ctypes.c_size_t
     lib.lb_save.argtypes = [vp, vp, ctypes.c_size_t]
     lib.lb_set_density.argtypes = [vp, d, d, d, d]
+    lib.lb_set_gravity.argtypes = [vp, d, d, d, d]
     lib.lb_load.argtypes = [vp, vp, ctypes.c_size_t]
     return lib
 
@@ -238,6 +239,11 @@ class Box:
         """Density and viscosity contrasts (lb_set_density): rho and tau of the
         phi = 1 and phi = 0 phases, linear in phi in between."""
         _check(_lib.lb_set_density(self._h, float(rho_l), float(rho_g), float(tau_l), float(tau_g)))
+
+    def set_gravity(self, g, rho_ref: float):
+        """Buoyancy (rho(phi) - rho_ref) g (lb_set_gravity); needs set_density first."""
+        gx, gy, gz = (float(v) for v in g)
+        _check(_lib.lb_set_gravity(self._h, gx, gy, gz, float(rho_ref)))
 
     def moments(self, rho=None, u=None, phi=None):
         """Fill caller buffers (any may be None) with p*, u (forced velocity) and phi."""

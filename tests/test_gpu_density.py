@@ -367,3 +367,106 @@ def test_paper_droplet_case_512_properties(lbgb):
         for a in range(3):
             s = -1.0 if a == 2 - axis else 1.0
             assert np.abs(u[a] - s * np.flip(u[a], axis)).max() <= 1e-6
+
+
+# ---------------------------------------------------------------- buoyancy
+def _mean_rho(phi, rho_l, rho_g):
+    return float(rho_g + (rho_l - rho_g) * phi.astype(np.float64).mean())
+
+
+@pytest.mark.parametrize("storage", ["f32", "moments"])
+def test_buoyant_droplet_32(lbgb, orc, storage):
+    """A heavy droplet (ratio 10, tau 0.6 inside) sinking under gravity
+    (0, 0, -1e-5) with rho_ref the mean density: 50 steps against the oracle."""
+    w = inputs.static_droplet()
+    dens = (10.0, 1.0, 0.6, 1.0)
+    rr = _mean_rho(w.phi, 10.0, 1.0)
+    b = lbgb.Box(32, 32, 32, w.tau, w.M, w.W, w.sigma, storage=storage)
+    b.set_density(*dens)
+    b.set_gravity((0.0, 0.0, -1e-5), rr)
+    b.init(w.phi, w.u)
+    b.step(50)
+    got = b.moments_numpy()
+    o = orc.Oracle(32, 32, 32, w.tau, w.M, w.W, w.sigma)
+    o.set_density(*dens)
+    o.set_gravity((0.0, 0.0, -1e-5), rr)
+    o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
+    o.step(50)
+    e = max_err(got, o.moments())
+    assert max(e) <= TOL, e
+    assert float(np.abs(got[1][2]).max()) > 1e-5  # the droplet does move
+    check_diagnostics(b.diagnostics(), o.diagnostics(), 32 ** 3)
+
+
+def test_buoyant_turbulence_64_heavy_droplets(lbgb, orc):
+    """64^3 forced turbulence with two heavy droplets (ratio 10) under gravity
+    along -y, linear forcing; 50 steps."""
+    w = inputs.bubbly_hit(64, 2, 10.0, seed=2)
+    dens = (10.0, 1.0, 0.55, 0.51)
+    rr = _mean_rho(w.phi, 10.0, 1.0)
+    force = dict(force_kind=3, T_relax=w.T_relax)
+    b = lbgb.Box(64, 64, 64, w.tau, w.M, w.W, w.sigma, force=_lb_force(lbgb, force))
+    b.set_density(*dens)
+    b.set_gravity((0.0, -2e-6, 0.0), rr)
+    b.init(w.phi, w.u)
+    b.step(50)
+    o = orc.Oracle(64, 64, 64, w.tau, w.M, w.W, w.sigma, **force)
+    o.set_density(*dens)
+    o.set_gravity((0.0, -2e-6, 0.0), rr)
+    o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
+    o.step(50)
+    e = max_err(b.moments_numpy(), o.moments())
+    assert max(e) <= TOL, e
+    check_diagnostics(b.diagnostics(), o.diagnostics(), 64 ** 3)
+
+
+def test_gravity_switched_on_mid_run(lbgb, orc):
+    shape = (12, 16, 40)
+    phi, u = smooth_fields(shape, 21)
+    dens = (10.0, 1.0, 0.7, 0.9)
+    rr = _mean_rho(phi, 10.0, 1.0)
+    b = lbgb.Box(40, 16, 12, 0.8, 0.1, 3.0, 0.01)
+    b.set_density(*dens)
+    b.init(phi, u)
+    b.step(10)
+    b.set_gravity((3e-6, 0.0, -1e-5), rr)
+    b.step(20)
+    o = orc.Oracle(40, 16, 12, 0.8, 0.1, 3.0, 0.01)
+    o.set_density(*dens)
+    o.init(phi.astype(np.float64), u.astype(np.float64))
+    o.step(10)
+    o.set_gravity((3e-6, 0.0, -1e-5), rr)
+    o.step(20)
+    e = max_err(b.moments_numpy(), o.moments())
+    assert max(e) <= TOL, e
+
+
+def test_counter_current_layers_on_the_device(lbgb):
+    """Gravity along layers at ratio 100 on the device: within 7% of the 1D
+    momentum equation with the force density (rho - rho_ref) g."""
+    nx, ny, W, x0, x1, g, T = 64, 4, 4.0, 16.0, 48.0, -1e-6, 3000
+    ph = _phi_layers(np.arange(nx, dtype=np.float64), nx, W, x0, x1)
+    phi = inputs.to_f32(np.broadcast_to(ph[None, None, :], (ny, ny, nx)))
+    rr = float((1.0 + ph * 99.0).mean())
+    b = lbgb.Box(nx, ny, ny, 1.0, 0.1, W, 0.0)
+    b.set_density(100.0, 1.0, 1.0, 1.0)
+    b.set_gravity((0.0, 0.0, g), rr)
+    b.init(phi, np.zeros((3, ny, ny, nx), np.float32))
+    b.step(T)
+    _, u, _ = b.moments_numpy()
+    ref = _shear_reference(nx, W, x0, x1, 100.0, 1.0, 1.0, 1.0, 0.0, T, force=lambda r: (r - rr) * g)
+    err = np.abs(u[2, 0, 0].astype(np.float64) - ref).max() / np.abs(ref).max()
+    assert err < 0.07, err
+
+
+def test_set_gravity_errors(lbgb):
+    b = lbgb.Box(8, 8, 8, 1.0, 0.1, 3.0, 0.01)
+    with pytest.raises(lbgb.LBError) as e:
+        b.set_gravity((0.0, 0.0, -1e-5), 1.0)
+    assert e.value.code == lbgb.LB_ESTATE
+    b.set_density(2.0, 1.0, 1.0, 1.0)
+    b.set_gravity((0.0, 0.0, -1e-5), 1.5)
+    with pytest.raises(lbgb.LBError) as e:
+        b.set_gravity((0.0, float("nan"), 0.0), 1.5)
+    assert e.value.code == lbgb.LB_EINVAL
+    b.close()
