@@ -23,4 +23,5 @@ from .oracle import (  # noqa: F401
     regularized_neq,
     set_threads,
     threads,
+    weno5_face,
 )

@@ -23,7 +23,10 @@
  *     mixture density rho(phi) and relaxation time tau(phi) linear in phi, the
  *     pressure force F^p and the viscous correction F^nu added to the total
  *     force, which enters the velocity, the source and a2 as F/rho; optional
- *     (orc_set_gravity) buoyancy (rho(phi) - rho_ref) g (Sec. 5.2).
+ *     (orc_set_gravity) buoyancy (rho(phi) - rho_ref) g (Sec. 5.2);
+ *   - optional (orc_set_phase_solver): Eq. 4 by finite differences, WENO-5
+ *     advection (Sec. 2.1.1) and the lattice stencils of Sec. 2.3, in place of
+ *     the D3Q7 model.
  *
  * Every stage is a separate loop over all sites writing a full field, in the
  * order of the method.  Two copies of each population set are kept; streaming
@@ -127,6 +130,11 @@ struct orc_state {
     double rho_l, rho_g, tau_l, tau_g; /* of the phi = 1 and phi = 0 phases */
     double* om;                        /* per-site relaxation rate 1/tau(phi) */
     double gb[3], rho_ref;             /* buoyancy (rho(phi) - rho_ref) g, off while g = 0 */
+
+    /* phase field by finite differences (Sec. 2.1.1: WENO-5 advection), off
+     * unless orc_set_phase_solver; phs is then the state and g is unused */
+    int fd;
+    double *phs, *ph1, *ph2, *rhs, *wv; /* state, RK3 stages, right-hand side, 3N work */
 };
 
 static int g_threads = 0;
@@ -204,6 +212,7 @@ void orc_destroy(orc_state* s) {
     free(s->Fs); free(s->rho); free(s->mom); free(s->Pi);
     free(s->u); free(s->F); free(s->a2);
     free(s->om);
+    free(s->phs); free(s->ph1); free(s->ph2); free(s->rhs); free(s->wv);
     free(s);
 }
 
@@ -313,9 +322,14 @@ void orc_gradient(int nx, int ny, int nz, const double* psi, double* grad) {
 
 /* ------------------------------------------------------------ step stages */
 
-/* phi = sum_i g_i (zeroth moment of the phase populations). */
+/* phi = sum_i g_i (zeroth moment of the phase populations); with the
+ * finite-difference phase solver phi is the stored field itself. */
 static void stage_phase_field(orc_state* s) {
     long long N = s->N;
+    if (s->fd) {
+        memcpy(s->phi, s->phs, (size_t)N * sizeof(double));
+        return;
+    }
 #pragma omp parallel for schedule(static) num_threads(orc_threads())
     for (long long x = 0; x < N; ++x) {
         double p = 0;
@@ -560,6 +574,118 @@ static void stage_collide_stream_phase(orc_state* s) {
     double* t = s->g; s->g = s->gn; s->gn = t;
 }
 
+/* ----------------------------------- phase field by finite differences
+ * Eq. 4 with the advection in flux form (reading: the printed u.grad phi
+ * equals div(phi u) for a solenoidal u; the flux form keeps sum phi exact):
+ *   d phi/dt = L(phi) = -div(phi u) + D lap(phi) - kappa_ace div(J),
+ *   J = max(phi (1 - phi), 0) n,  n = grad phi / max(|grad phi|, 1e-10),
+ * D = M and kappa_ace = 4M/W (the same constants as the D3Q7 model).  The
+ * derivatives of the diffusion and sharpening terms use the lattice stencils
+ * of Sec. 2.3: grad with (1/cs^2) sum_i w_i c_i Psi(x + c_i), and
+ * lap(Psi) = (2/cs^2) sum_i w_i (Psi(x + c_i) - Psi(x)).  The advective flux
+ * through the face between x and x + e_a is u_f phi_f with u_f the mean of
+ * the two sites' u_a and phi_f the WENO-5 reconstruction of Jiang and Shu
+ * (1996) from the five values upwind of the face (smoothness indicators,
+ * linear weights 1/10, 6/10, 3/10, epsilon 1e-6, squared).  Time: the
+ * three-stage strong-stability-preserving Runge-Kutta scheme of Shu and Osher
+ * with u held at its value of step 8 over the step (dt = 1). */
+
+/* WENO-5 value at the face between v0 and v1 for flow from v0 towards v1,
+ * from the values vm2, vm1, v0, v1, v2 along the flow. */
+static double weno5_face(double vm2, double vm1, double v0, double v1, double v2) {
+    const double q0 = (2 * vm2 - 7 * vm1 + 11 * v0) / 6;
+    const double q1 = (-vm1 + 5 * v0 + 2 * v1) / 6;
+    const double q2 = (2 * v0 + 5 * v1 - v2) / 6;
+    const double b0 = 13.0 / 12 * (vm2 - 2 * vm1 + v0) * (vm2 - 2 * vm1 + v0) +
+                      0.25 * (vm2 - 4 * vm1 + 3 * v0) * (vm2 - 4 * vm1 + 3 * v0);
+    const double b1 = 13.0 / 12 * (vm1 - 2 * v0 + v1) * (vm1 - 2 * v0 + v1) + 0.25 * (vm1 - v1) * (vm1 - v1);
+    const double b2 = 13.0 / 12 * (v0 - 2 * v1 + v2) * (v0 - 2 * v1 + v2) +
+                      0.25 * (3 * v0 - 4 * v1 + v2) * (3 * v0 - 4 * v1 + v2);
+    const double eps = 1e-6;
+    const double a0 = 0.1 / ((eps + b0) * (eps + b0));
+    const double a1 = 0.6 / ((eps + b1) * (eps + b1));
+    const double a2 = 0.3 / ((eps + b2) * (eps + b2));
+    return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+double orc_weno5_face(const double v[5]) { return weno5_face(v[0], v[1], v[2], v[3], v[4]); }
+
+/* L(ph) into out, u = s->u. */
+static void phase_rhs(orc_state* s, const double* ph, double* out) {
+    long long N = s->N;
+    const int nx = s->nx, ny = s->ny, nz = s->nz;
+    const double D = s->M, kap = isinf(s->W) ? 0.0 : 4.0 * s->M / s->W;
+    double* J = s->wv;
+    /* J = max(ph (1 - ph), 0) n */
+    orc_gradient(nx, ny, nz, ph, J);
+#pragma omp parallel for schedule(static) num_threads(orc_threads())
+    for (long long x = 0; x < N; ++x) {
+        double gx = J[x], gy = J[N + x], gz = J[2 * N + x];
+        double m = sqrt(gx * gx + gy * gy + gz * gz);
+        double d = m > NORMAL_GUARD ? m : NORMAL_GUARD;
+        double w = ph[x] * (1 - ph[x]);
+        if (w < 0) w = 0;
+        J[x] = w * gx / d;
+        J[N + x] = w * gy / d;
+        J[2 * N + x] = w * gz / d;
+    }
+#pragma omp parallel for schedule(static) num_threads(orc_threads())
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                long long k = site(s, x, y, z);
+                /* div J and lap(ph) with the lattice stencils */
+                double divJ = 0, lap = 0;
+                for (int i = 1; i < 27; ++i) {
+                    const int* c = C27[i];
+                    long long q = site(s, wrap(x + c[0], nx), wrap(y + c[1], ny), wrap(z + c[2], nz));
+                    for (int a = 0; a < 3; ++a) divJ += W27[i] * c[a] * J[a * N + q];
+                    lap += W27[i] * (ph[q] - ph[k]);
+                }
+                divJ /= CS2;
+                lap *= 2 / CS2;
+                /* advective flux differences, face by face */
+                double adv = 0;
+                for (int a = 0; a < 3; ++a) {
+                    const int n = a == 0 ? nx : (a == 1 ? ny : nz);
+                    const int p = a == 0 ? x : (a == 1 ? y : z);
+                    for (int side = 0; side < 2; ++side) {   /* faces p - 1/2 (side 0) and p + 1/2 */
+                        const int lo = p - 1 + side;         /* the face lies between lo and lo + 1 */
+                        double v[6];                         /* ph at lo - 2 .. lo + 3 along axis a */
+                        double ul = 0, ur = 0;
+                        for (int j = 0; j < 6; ++j) {
+                            int e[3] = {x, y, z};
+                            e[a] = wrap(lo - 2 + j, n);
+                            v[j] = ph[site(s, e[0], e[1], e[2])];
+                        }
+                        {
+                            int e[3] = {x, y, z};
+                            e[a] = wrap(lo, n);
+                            ul = s->u[a * N + site(s, e[0], e[1], e[2])];
+                            e[a] = wrap(lo + 1, n);
+                            ur = s->u[a * N + site(s, e[0], e[1], e[2])];
+                        }
+                        const double uf = 0.5 * (ul + ur);
+                        const double pf = uf >= 0 ? weno5_face(v[0], v[1], v[2], v[3], v[4])
+                                                  : weno5_face(v[5], v[4], v[3], v[2], v[1]);
+                        adv += (side ? 1.0 : -1.0) * uf * pf;
+                    }
+                }
+                out[k] = -adv + D * lap - kap * divJ;
+            }
+}
+
+static void stage_phase_fd(orc_state* s) {
+    long long N = s->N;
+    double *p0 = s->phs, *p1 = s->ph1, *p2 = s->ph2, *L = s->rhs;
+    phase_rhs(s, p0, L);
+    for (long long x = 0; x < N; ++x) p1[x] = p0[x] + L[x];
+    phase_rhs(s, p1, L);
+    for (long long x = 0; x < N; ++x) p2[x] = 0.75 * p0[x] + 0.25 * (p1[x] + L[x]);
+    phase_rhs(s, p2, L);
+    for (long long x = 0; x < N; ++x) p0[x] = p0[x] / 3 + 2.0 / 3 * (p2[x] + L[x]);
+}
+
 /* FP64 reductions: Phi = sum phi, K = 1/2 sum |u|^2, eps = 2 nu sum S:S with
  * S = -a2/(2 cs^2 tau) (the Chapman-Enskog estimate of Sec. 2.2), max|u|;
  * then the linear-forcing amplitude for the next step. */
@@ -620,7 +746,8 @@ int orc_step(orc_state* s, int n) {
         stage_hermite(s);
         stage_diagnostics(s);
         stage_collide_stream_hydro(s);
-        stage_collide_stream_phase(s);
+        if (s->fd) stage_phase_fd(s);
+        else stage_collide_stream_phase(s);
         s->t += 1;
     }
     return 0;
@@ -630,6 +757,7 @@ int orc_init(orc_state* s, const double* phi, const double* u) {
     if (!s || !phi || !u) return -1;
     long long N = s->N;
     memcpy(s->phi, phi, (size_t)N * sizeof(double));
+    if (s->fd) memcpy(s->phs, phi, (size_t)N * sizeof(double));
     orc_gradient(s->nx, s->ny, s->nz, s->phi, s->grad);
     stage_normal(s);
     for (long long x = 0; x < N; ++x) {
@@ -693,6 +821,21 @@ int orc_set_density(orc_state* s, double rho_l, double rho_g, double tau_l, doub
     }
     s->vd = 1;
     s->rho_l = rho_l; s->rho_g = rho_g; s->tau_l = tau_l; s->tau_g = tau_g;
+    return 0;
+}
+
+int orc_set_phase_solver(orc_state* s, int solver) {
+    if (!s || (solver != ORC_PHASE_LB && solver != ORC_PHASE_WENO5)) return -1;
+    if (solver == ORC_PHASE_WENO5 && !s->phs) {
+        long long N = s->N;
+        s->phs = (double*)calloc((size_t)N, sizeof(double));
+        s->ph1 = (double*)calloc((size_t)N, sizeof(double));
+        s->ph2 = (double*)calloc((size_t)N, sizeof(double));
+        s->rhs = (double*)calloc((size_t)N, sizeof(double));
+        s->wv = (double*)calloc((size_t)(3 * N), sizeof(double));
+        if (!s->phs || !s->ph1 || !s->ph2 || !s->rhs || !s->wv) return -1;
+    }
+    s->fd = solver == ORC_PHASE_WENO5;
     return 0;
 }
 

@@ -54,6 +54,17 @@ int  orc_set_density(orc_state* s, double rho_l, double rho_g, double tau_l, dou
  * arguments are finite. */
 int  orc_set_gravity(orc_state* s, const double g[3], double rho_ref);
 
+/* Phase-field solver: ORC_PHASE_LB (the D3Q7 model, default) or
+ * ORC_PHASE_WENO5 (Eq. 4 by finite differences with WENO-5 advection and
+ * SSP-RK3 in time).  Call before orc_init.  Returns -1 on bad input. */
+#define ORC_PHASE_LB 0
+#define ORC_PHASE_WENO5 1
+int  orc_set_phase_solver(orc_state* s, int solver);
+
+/* The WENO-5 face value of Jiang and Shu from the five values v[0..4] along
+ * the flow (the face lies between v[2] and v[3]). */
+double orc_weno5_face(const double v[5]);
+
 /* Raw populations: f is 27N in the oracle's own direction order (see
  * orc_lattice27), g is 7N in the order of orc_lattice7. */
 void orc_get_populations(const orc_state* s, double* f, double* g);

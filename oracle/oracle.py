@@ -51,6 +51,9 @@ def _load():
             lib.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
             lib.orc_set_density.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 4
             lib.orc_set_gravity.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double]
+            lib.orc_set_phase_solver.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            lib.orc_weno5_face.argtypes = [_dp]
+            lib.orc_weno5_face.restype = ctypes.c_double
             lib.orc_step.restype = ctypes.c_int
             lib.orc_moments.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
             lib.orc_diagnostics.argtypes = [ctypes.c_void_p, _dp]
@@ -128,6 +131,14 @@ def interface(phi: np.ndarray, W: float, sigma: float):
     return grad, nrm, kappa, Fs
 
 
+def weno5_face(v) -> float:
+    """WENO-5 face value (Jiang and Shu) from five values along the flow; the face
+    lies between v[2] and v[3]."""
+    a = _f64(v)
+    assert a.shape == (5,)
+    return float(_load().orc_weno5_face(_ptr(a)))
+
+
 def equilibrium(p: float, u) -> np.ndarray:
     out = np.zeros(27)
     _load().orc_equilibrium(float(p), _ptr(_f64(u)), _ptr(out))
@@ -192,6 +203,12 @@ class Oracle:
         phi = 0 phases, linear in phi in between."""
         if self._lib.orc_set_density(self._h, float(rho_l), float(rho_g), float(tau_l), float(tau_g)) != 0:
             raise ValueError("oracle rejected the density parameters")
+
+    def set_phase_solver(self, solver: str):
+        """"lb" (the D3Q7 model) or "weno5" (Eq. 4 by finite differences); before init."""
+        code = {"lb": 0, "weno5": 1}[solver]
+        if self._lib.orc_set_phase_solver(self._h, code) != 0:
+            raise ValueError("oracle rejected the phase solver")
 
     def set_gravity(self, g, rho_ref):
         """Buoyancy (rho(phi) - rho_ref) g (needs set_density first)."""
