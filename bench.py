@@ -13,9 +13,11 @@ the measured HBM bandwidth reached by the fused kernel.
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                        [--storage f32|f16|bf16|moments] [--edge E]
                        [--density RHO_L RHO_G TAU_L TAU_G] [--gravity GX,GY,GZ]
+                       [--phase lb|weno5]
 --density runs the same box with density and viscosity contrasts (Sec. 2.3):
 the bubbles become the gas (phi = 0 inside, phi flipped), the liquid phi = 1.
 --gravity adds the buoyancy (rho(phi) - rho_ref) g with rho_ref the mean density.
+--phase weno5 advances the phase field by finite differences (WENO-5, SSP-RK3).
 Under torchrun (N > 1) every rank advances its own replica box (weak scaling,
 no collective on the data path); value = sum of sites*steps over ranks divided
 by the slowest rank's time.
@@ -177,7 +179,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline_sample(density=None):
+def cpu_baseline_sample(density=None, phase="lb"):
     """Time the oracle (as it stands) on a bounded sample of the workload (with the
     density contrasts and flipped phase field when `density` is given)."""
     import oracle
@@ -187,6 +189,7 @@ def cpu_baseline_sample(density=None):
     if density == "droplet":
         w = droplet_workload(n)
         o = oracle.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma)
+        o.set_phase_solver(phase)
         o.set_density(*DROPLET_DENSITY)
         o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
         o.step(1)
@@ -199,6 +202,7 @@ def cpu_baseline_sample(density=None):
                           f"{SAMPLE_STEPS} FP64 oracle steps after 1 untimed step, {dt:.1f} s"}
     w, _ = workload(SAMPLE_EDGE)
     o = oracle.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma, force_kind=oracle.FORCE_LINEAR, T_relax=w.T_relax)
+    o.set_phase_solver(phase)
     phi = w.phi.astype(np.float64)
     if density:
         o.set_density(*density)
@@ -212,7 +216,8 @@ def cpu_baseline_sample(density=None):
     value = n ** 3 * SAMPLE_STEPS / dt / 1e6
     return {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
             "sample": f"{n}^3 box of the same recipe ({SAMPLE_BUBBLES} bubbles R=10, u_rms 0.02, tau 0.51, "
-                      f"linear forcing{', density contrasts' if density else ''}), "
+                      f"linear forcing{', density contrasts' if density else ''}"
+                      f"{', WENO-5 phase field' if phase != 'lb' else ''}), "
                       f"{SAMPLE_STEPS} FP64 oracle steps after 1 untimed step, "
                       f"{dt:.1f} s"}
 
@@ -339,6 +344,8 @@ def main():
     ap.add_argument("--preset", choices=sorted(PRESETS), help="bubbly HIT preset (overrides --edge)")
     ap.add_argument("--density", type=float, nargs=4, metavar=("RHO_L", "RHO_G", "TAU_L", "TAU_G"),
                     help="density and viscosity contrasts: gas bubbles (phi = 0) in the liquid (phi = 1)")
+    ap.add_argument("--phase", default="lb", choices=["lb", "weno5"],
+                    help="phase-field solver: the D3Q7 model (default) or WENO-5 finite differences")
     ap.add_argument("--gravity", type=lambda v: tuple(float(x) for x in v.split(",")), metavar="GX,GY,GZ",
                     help="buoyancy (rho(phi) - rho_ref) g, rho_ref the mean density (needs --density or droplet)")
     args = ap.parse_args()
@@ -393,6 +400,8 @@ def main():
     force = None if droplet else lbgb.Force(kind=lbgb.LB_FORCE_LINEAR, T_relax=w.T_relax)
     stream = torch.cuda.Stream()
     box = lbgb.Box(n, n, n, w.tau, w.M, w.W, w.sigma, force=force, storage=args.storage, stream=stream)
+    if args.phase != "lb":
+        box.set_phase_solver(args.phase)
     if args.density:
         box.set_density(*args.density)
     rho_ref = None
@@ -470,13 +479,19 @@ def main():
         kern_avg_s = kern_ms / max(kern_n, 1) * 1e-3
         achieved = bps * N / kern_avg_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": measured_traffic(args.storage + ("+density" if args.density else ""), N, [32, ty, zc]),
-                "kernel": "fused_step_kernel" + (" (VD)" if args.density else ""), "bytes_per_site": bps,
+                "traffic": measured_traffic(args.storage + ("+density" if args.density else "")
+                                            + ("+weno5" if args.phase != "lb" else ""), N, [32, ty, zc]),
+                "kernel": "fused_step_kernel" + (" (VD)" if args.density else "") + (" (PF)" if args.phase != "lb" else ""),
+                "bytes_per_site": bps,
                 "kernel_ms_avg": kern_avg_s * 1e3, "peak_source": peak_kind}
+        if args.phase != "lb":
+            # the three finite-difference stage kernels and the reduction, per step
+            roof["other_kernels_ms_per_step"] = t_max / args.steps - kern_avg_s * 1e3
+            roof["other_kernels_bytes_per_site"] = 3 * (4 + 12 + 4) + 2 * 4
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             try:
-                cpu = cpu_baseline_sample("droplet" if droplet else args.density)
+                cpu = cpu_baseline_sample("droplet" if droplet else args.density, args.phase)
             except Exception as ex:  # report, do not fail the benchmark line
                 cpu = {"error": str(ex)}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -492,7 +507,9 @@ def main():
                                         + (", gas bubbles (phi = 0) with rho_l, rho_g, tau_l, tau_g = "
                                            + ", ".join(f"{v:g}" for v in args.density) if args.density else ""))
                                        + (f", buoyancy g = ({', '.join(f'{v:g}' for v in args.gravity)}), "
-                                          f"rho_ref = {rho_ref:.6g} (mean density)" if args.gravity else ""),
+                                          f"rho_ref = {rho_ref:.6g} (mean density)" if args.gravity else "")
+                                       + (", phase field by WENO-5 finite differences (SSP-RK3)"
+                                          if args.phase != "lb" else ""),
                            "edge": n, "storage": args.storage, "tile": [32, ty, zc],
                            "l2": "inputs larger than L2 (populations %.2f GB), no flush" % (bps * N / 2 / 1e9),
                            "parallelism": f"replicas x{world}"},

@@ -142,6 +142,27 @@ int lb_init(lb_ctx* ctx, const float* phi, const float* u);
 int lb_set_density(lb_ctx* ctx, double rho_l, double rho_g, double tau_l, double tau_g);
 
 /*
+ * lb_set_phase_solver -- how the phase field advances (Sec. 2.1.1, Eq. 4):
+ *   LB_PHASE_LB     the D3Q7 lattice Boltzmann model (default);
+ *   LB_PHASE_WENO5  Eq. 4 by finite differences: the advection in flux form
+ *                   div(phi u) with WENO-5 face values (Jiang and Shu), the
+ *                   diffusion D lap(phi) and the sharpening
+ *                   -kappa div(max(phi (1 - phi), 0) n) with the lattice
+ *                   stencils of Sec. 2.3 (D = M, kappa = 4M/W), and the
+ *                   three-stage SSP Runge-Kutta scheme in time with u held at
+ *                   the step's forced velocity.
+ * With LB_PHASE_WENO5 phi is stored as one field (the D3Q7 buffers hold phi,
+ * the two Runge-Kutta stages and the velocity), each step launches the fused
+ * kernel (which reads phi and writes u), three stage kernels and the
+ * reduction.  Call before lb_init (LB_ESTATE after it, unless the solver does
+ * not change).  Every storage, density contrasts and checkpoints support it.
+ * Errors: LB_EINVAL for an unknown solver.
+ */
+#define LB_PHASE_LB 0
+#define LB_PHASE_WENO5 1
+int lb_set_phase_solver(lb_ctx* ctx, int solver);
+
+/*
  * lb_set_gravity -- buoyancy (the rising bubbles of Sec. 5.2) with density
  * contrasts on: from the next step the force density gains
  *   F^b = (rho(phi) - rho_ref) g,  g = (gx, gy, gz).
@@ -220,7 +241,8 @@ int lb_load(lb_ctx* ctx, const void* buf, size_t bytes);
 
 /* Algorithmic bytes moved per site per step by the fused kernel (population
  * reads and writes): 27*2*sizeof(f) + 7*2*sizeof(g), or 10*2*4 + 7*2*4 for
- * LB_F32_MOMENTS. */
+ * LB_F32_MOMENTS; with LB_PHASE_WENO5 the 7*2*4 of g become 4 + 3*4 (phi read,
+ * u written; the three stage kernels move 3*(4 + 3*4 + 4) + 2*4 = 68 more). */
 double lb_bytes_per_site(const lb_ctx* ctx);
 
 /* Free everything the context owns.  NULL is ignored. */

@@ -127,6 +127,7 @@ struct lb_ctx {
     cudaGraphExec_t graph = nullptr;  // two steps starting at even parity
     int graph_ty = 0, graph_zc = 0;
 
+    bool fd = false;  // phase field by finite differences (lb_set_phase_solver)
     bool vd = false;  // density and viscosity contrasts (lb_set_density)
     double rho_l = 1.0, rho_g = 1.0, tau_l = 1.0, tau_g = 1.0;
     double gb[3] = {0.0, 0.0, 0.0}, rho_ref = 0.0;  // buoyancy (lb_set_gravity)
@@ -176,11 +177,23 @@ StepArgs base_args(const lb_ctx* c) {
 }
 
 // D3Q7 plane pointers: read buffer `par`, write buffer par ^ 1 (and likewise
-// the coefficient buffers of the moment-only storage).
-void set_g(StepArgs& a, const lb_ctx* c, int par) {
-    for (int q = 0; q < 7; ++q) {
-        a.gin[q] = c->g[par] + (size_t)q * (size_t)c->N;
-        a.gout[q] = c->g[par ^ 1] + (size_t)q * (size_t)c->N;
+// the coefficient buffers of the moment-only storage).  With the
+// finite-difference phase field, g[0] holds phi (plane 0) and the two RK
+// stages (planes 1, 2), g[1] the velocity u (planes 0-2) the step writes; the
+// kernel reads phi from gin[0] and writes u to gout[0..2] (INIT: phi to gout[0]).
+float* g_plane(const lb_ctx* c, int buf, int q) { return c->g[buf] + (size_t)q * (size_t)c->N; }
+
+void set_g(StepArgs& a, const lb_ctx* c, int par, bool init = false) {
+    if (c->fd) {
+        for (int q = 0; q < 7; ++q) {
+            a.gin[q] = g_plane(c, 0, 0);
+            a.gout[q] = init ? g_plane(c, 0, 0) : g_plane(c, 1, q < 3 ? q : 0);
+        }
+    } else {
+        for (int q = 0; q < 7; ++q) {
+            a.gin[q] = g_plane(c, par, q);
+            a.gout[q] = g_plane(c, par ^ 1, q);
+        }
     }
     if (is_mc(c)) {
         float* C = static_cast<float*>(c->f);
@@ -197,13 +210,19 @@ cudaError_t launch_any(const lb_ctx* c, int mode, int parity, int ty, dim3 grid,
                        cudaStream_t s) {
     // float4 phase-A loads need 16-byte aligned rows: nx % 4 == 0 (planes then start aligned too)
     const bool vec = (c->nx % 4) == 0;
-    if (c->vd && mode != MODE_INIT) {
+    if (c->fd || (c->vd && mode != MODE_INIT)) {
+        const bool vd = c->vd && mode != MODE_INIT;
+#define LBGB_X(FT, MC)                                                                              \
+    (c->fd ? (vd ? launch_fused_x<FT, MC, true, true>(mode, parity, ty, vec, grid, a, s)            \
+                 : launch_fused_x<FT, MC, false, true>(mode, parity, ty, vec, grid, a, s))          \
+           : launch_fused_x<FT, MC, true, false>(mode, parity, ty, vec, grid, a, s))
         switch (c->storage) {
-            case LB_F32_MOMENTS: return launch_fused_vd<float, true>(mode, parity, ty, vec, grid, a, s);
-            case LB_F32: return launch_fused_vd<float, false>(mode, parity, ty, vec, grid, a, s);
-            case LB_F16_SHIFTED: return launch_fused_vd<__half, false>(mode, parity, ty, vec, grid, a, s);
-            case LB_BF16_SHIFTED: return launch_fused_vd<__nv_bfloat16, false>(mode, parity, ty, vec, grid, a, s);
+            case LB_F32_MOMENTS: return LBGB_X(float, true);
+            case LB_F32: return LBGB_X(float, false);
+            case LB_F16_SHIFTED: return LBGB_X(__half, false);
+            case LB_BF16_SHIFTED: return LBGB_X(__nv_bfloat16, false);
         }
+#undef LBGB_X
         return cudaErrorInvalidValue;
     }
     switch (c->storage) {
@@ -255,6 +274,16 @@ int enqueue_step(lb_ctx* c, int par, cudaStream_t s, bool first = false) {
     if (timed) {
         LB_CUDA(cudaEventRecord(c->ev_stop[c->ev_used], s));
         c->ev_used += 1;
+    }
+    if (c->fd) {
+        // Eq. 4 by finite differences, three RK stages on the u just written
+        const float D = (float)c->M, kap = isinf(c->W) ? 0.f : (float)(4.0 * c->M / c->W);
+        float *p0 = g_plane(c, 0, 0), *p1 = g_plane(c, 0, 1), *p2 = g_plane(c, 0, 2);
+        const float* u = g_plane(c, 1, 0);
+        LB_CUDA(launch_weno_stage(0, p0, p0, u, p1, c->nx, c->ny, c->nz, D, kap, s));
+        LB_CUDA(launch_weno_stage(1, p1, p0, u, p2, c->nx, c->ny, c->nz, D, kap, s));
+        LB_CUDA(launch_weno_stage(2, p2, p0, u, p0, c->nx, c->ny, c->nz, D, kap, s));
+        c->launches += 3;
     }
     finalize_kernel<<<1, 256, 0, s>>>(c->partials, (int)nblk, c->st, fin_args(c, MODE_STEP));
     LB_CUDA(cudaGetLastError());
@@ -323,17 +352,17 @@ int tune_chunks(const lb_ctx* c, int ty, int zcs[6]) {
     }
     const bool vec = (c->nx % 4) == 0;
     int per_sm = 0;
+#define LBGB_XO(FT, MC)                                                                                     \
+    (c->fd ? (c->vd ? fused_x_blocks_per_sm<FT, MC, true, true>(ty, vec) : fused_x_blocks_per_sm<FT, MC, false, true>(ty, vec)) \
+           : fused_x_blocks_per_sm<FT, MC, true, false>(ty, vec))
+    const bool x = c->fd || c->vd;
     switch (c->storage) {
-        case LB_F32: per_sm = c->vd ? fused_vd_blocks_per_sm<float, false>(ty, vec) : fused_blocks_per_sm<float>(ty, vec); break;
-        case LB_F16_SHIFTED:
-            per_sm = c->vd ? fused_vd_blocks_per_sm<__half, false>(ty, vec) : fused_blocks_per_sm<__half>(ty, vec);
-            break;
-        case LB_BF16_SHIFTED:
-            per_sm = c->vd ? fused_vd_blocks_per_sm<__nv_bfloat16, false>(ty, vec)
-                           : fused_blocks_per_sm<__nv_bfloat16>(ty, vec);
-            break;
-        case LB_F32_MOMENTS: per_sm = c->vd ? fused_vd_blocks_per_sm<float, true>(ty, vec) : fused_mc_blocks_per_sm(ty, vec); break;
+        case LB_F32: per_sm = x ? LBGB_XO(float, false) : fused_blocks_per_sm<float>(ty, vec); break;
+        case LB_F16_SHIFTED: per_sm = x ? LBGB_XO(__half, false) : fused_blocks_per_sm<__half>(ty, vec); break;
+        case LB_BF16_SHIFTED: per_sm = x ? LBGB_XO(__nv_bfloat16, false) : fused_blocks_per_sm<__nv_bfloat16>(ty, vec); break;
+        case LB_F32_MOMENTS: per_sm = x ? LBGB_XO(float, true) : fused_mc_blocks_per_sm(ty, vec); break;
     }
+#undef LBGB_XO
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
         cudaGetLastError();
@@ -505,7 +534,7 @@ int lb_init(lb_ctx* c, const float* phi, const float* u) {
     }
     StepArgs a = base_args(c);
     a.zc = c->nz < 32 ? c->nz : 32;
-    set_g(a, c, 1);  // writes buffer 0
+    set_g(a, c, 1, true);  // writes buffer 0 (finite-difference phase field: phi into g[0] plane 0)
     a.in_phi = dphi;
     a.in_u = du;
     const dim3 grid = grid_for(c, 8, a.zc);
@@ -609,6 +638,16 @@ int lb_set_density(lb_ctx* c, double rho_l, double rho_g, double tau_l, double t
     return LB_OK;
 }
 
+int lb_set_phase_solver(lb_ctx* c, int solver) {
+    if (!c) return fail(LB_EINVAL, "ctx is NULL");
+    if (solver != LB_PHASE_LB && solver != LB_PHASE_WENO5) return fail(LB_EINVAL, "unknown phase solver %d", solver);
+    if (c->initialized && (solver == LB_PHASE_WENO5) != c->fd)
+        return fail(LB_ESTATE, "lb_set_phase_solver after lb_init (the state is held differently)");
+    c->fd = solver == LB_PHASE_WENO5;
+    drop_graph(c);
+    return LB_OK;
+}
+
 int lb_set_gravity(lb_ctx* c, double gx, double gy, double gz, double rho_ref) {
     if (!c) return fail(LB_EINVAL, "ctx is NULL");
     if (!c->vd) return fail(LB_ESTATE, "lb_set_gravity needs lb_set_density first");
@@ -671,6 +710,10 @@ static size_t ckpt_f_bytes(const lb_ctx* c) {
     return is_mc(c) ? (size_t)c->N * 10 * sizeof(float) : (size_t)c->N * 27 * c->fsize;
 }
 
+// The D3Q7 buffer of time t, or (finite-difference phase field) the buffer
+// whose plane 0 holds phi.
+static float* g_state(const lb_ctx* c) { return c->fd ? c->g[0] : c->g[c->t & 1]; }
+
 static char* ckpt_f_ptr(const lb_ctx* c) {
     if (!is_mc(c)) return static_cast<char*>(c->f);
     return static_cast<char*>(c->f) + (size_t)(c->t & 1) * (size_t)c->N * 10 * sizeof(float);
@@ -698,7 +741,7 @@ int lb_save(lb_ctx* c, void* buf, size_t bytes) {
     p += sizeof(DevState);
     LB_CUDA(cudaMemcpyAsync(p, ckpt_f_ptr(c), (size_t)h.f_bytes, cudaMemcpyDeviceToHost, c->stream));
     p += h.f_bytes;
-    LB_CUDA(cudaMemcpyAsync(p, c->g[c->t & 1], (size_t)h.g_bytes, cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(cudaMemcpyAsync(p, g_state(c), (size_t)h.g_bytes, cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(cudaStreamSynchronize(c->stream));
     return LB_OK;
 }
@@ -721,7 +764,7 @@ int lb_load(lb_ctx* c, const void* buf, size_t bytes) {
     p += sizeof(DevState);
     LB_CUDA(cudaMemcpyAsync(ckpt_f_ptr(c), p, (size_t)h.f_bytes, cudaMemcpyHostToDevice, c->stream));
     p += h.f_bytes;
-    LB_CUDA(cudaMemcpyAsync(c->g[c->t & 1], p, (size_t)h.g_bytes, cudaMemcpyHostToDevice, c->stream));
+    LB_CUDA(cudaMemcpyAsync(g_state(c), p, (size_t)h.g_bytes, cudaMemcpyHostToDevice, c->stream));
     LB_CUDA(cudaStreamSynchronize(c->stream));
     c->initialized = true;
     return LB_OK;
@@ -729,8 +772,10 @@ int lb_load(lb_ctx* c, const void* buf, size_t bytes) {
 
 double lb_bytes_per_site(const lb_ctx* c) {
     if (!c) return 0.0;
-    if (is_mc(c)) return 10.0 * 2.0 * 4.0 + 7.0 * 2.0 * 4.0;
-    return 27.0 * 2.0 * (double)c->fsize + 7.0 * 2.0 * 4.0;
+    // phase part: D3Q7 read + write, or (finite-difference phase field) phi read + u written
+    const double ph = c->fd ? 4.0 + 3.0 * 4.0 : 7.0 * 2.0 * 4.0;
+    if (is_mc(c)) return 10.0 * 2.0 * 4.0 + ph;
+    return 27.0 * 2.0 * (double)c->fsize + ph;
 }
 
 int lb_tune(lb_ctx* c, int steps) {
@@ -745,7 +790,8 @@ int lb_tune(lb_ctx* c, int steps) {
         if (*p == ' ') *p = '_';
     const char* cache = getenv("LBGB_TUNE_CACHE");
     char key[512];
-    snprintf(key, sizeof(key), "%s %d %d %d %d%s", dev_name, c->nx, c->ny, c->nz, c->storage, c->vd ? "vd" : "");
+    snprintf(key, sizeof(key), "%s %d %d %d %d%s%s", dev_name, c->nx, c->ny, c->nz, c->storage, c->vd ? "vd" : "",
+             c->fd ? "fd" : "");
     if (cache) {
         FILE* fp = fopen(cache, "r");
         if (fp) {
@@ -783,6 +829,7 @@ int lb_tune(lb_ctx* c, int steps) {
         rc = lb_create(c->nx, c->ny, nzt, c->tau, c->M, c->W, c->sigma, &c->force, c->storage, &s);
         if (rc) return rc;
         lb_set_stream(s, c->stream);
+        if (c->fd) lb_set_phase_solver(s, LB_PHASE_WENO5);
         if (c->vd) {
             lb_set_density(s, c->rho_l, c->rho_g, c->tau_l, c->tau_g);
             lb_set_gravity(s, c->gb[0], c->gb[1], c->gb[2], c->rho_ref);

@@ -422,7 +422,10 @@ __device__ __forceinline__ void pull_column(LD ld, float& vm, float& v0, float& 
 // PAR = 0 evaluates the site's own coefficients (t = 0, where lb_init stored
 // those of f^eq) and PAR = 1 pulls; FT is float.
 // VD adds the density and viscosity contrasts of Sec. 2.3 (see vd_force).
-template <class FT, int TY, int MODE, int PAR, bool VEC, bool MC = false, bool VD = false>
+// PF: the phase field is a stored field (one plane, gin[0]) advanced by the
+// finite-difference step of lbgb_weno.cu; this kernel then reads phi from it
+// and writes u (gout[0..2]) instead of the D3Q7 update (INIT: copies phi).
+template <class FT, int TY, int MODE, int PAR, bool VEC, bool MC = false, bool VD = false, bool PF = false>
 __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 512 / (32 * TY)))
 fused_step_kernel(const StepArgs a) {
 #define TILE_BX blockIdx.x
@@ -515,6 +518,7 @@ batch_step_kernel(const __grid_constant__ BatchArgs b) {
             constexpr int MODE = MODE_STEP;
             constexpr bool MC = MC_;
             constexpr bool VD = false;
+            constexpr bool PF = false;
 #define TILE_BX tbx
 #define TILE_BY tby
 #define TILE_BZ tbz
@@ -556,12 +560,18 @@ int batch_blocks_per_sm(int ty, bool vec);
 template <class FT>
 cudaError_t launch_fused(int mode, int parity, int ty, bool vec, dim3 grid, const StepArgs& a, cudaStream_t st);
 
-// The same kernels with the density and viscosity contrasts (VD = true), mode
-// STEP or MOMENTS, for the AA storage FT (MC = false) or the moment-only
-// storage (FT float, MC = true, parity = pull).  Defined in lbgb_step_vd_*.cu.
-template <class FT, bool MC>
-cudaError_t launch_fused_vd(int mode, int parity, int ty, bool vec, dim3 grid, const StepArgs& a, cudaStream_t st);
-template <class FT, bool MC>
-int fused_vd_blocks_per_sm(int ty, bool vec);
+// The same kernels with the density and viscosity contrasts (VD) and/or the
+// phase field as a stored field (PF), mode STEP or MOMENTS (and INIT for PF
+// without VD), for the AA storage FT (MC = false) or the moment-only storage
+// (FT float, MC = true, parity = pull).  Defined in lbgb_step_{vd,fd,fdvd}_*.cu.
+template <class FT, bool MC, bool VD, bool PF>
+cudaError_t launch_fused_x(int mode, int parity, int ty, bool vec, dim3 grid, const StepArgs& a, cudaStream_t st);
+template <class FT, bool MC, bool VD, bool PF>
+int fused_x_blocks_per_sm(int ty, bool vec);
+
+// One stage (0, 1, 2) of the finite-difference phase step (lbgb_weno.cu):
+// reads pin (with halo), phin (own site), u (3 planes of N) and writes out.
+cudaError_t launch_weno_stage(int stage, const float* pin, const float* phin, const float* u, float* out, int nx,
+                              int ny, int nz, float D, float kap, cudaStream_t st);
 
 }  // namespace lbgb

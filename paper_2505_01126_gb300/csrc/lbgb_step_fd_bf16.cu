@@ -1,0 +1,6 @@
+// BF16 shifted population storage, finite-difference phase field.
+#define LBGB_FT __nv_bfloat16
+#define LBGB_MC false
+#define LBGB_VD false
+#define LBGB_PF true
+#include "lbgb_step_x_impl.cuh"

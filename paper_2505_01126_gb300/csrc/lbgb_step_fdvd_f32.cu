@@ -1,0 +1,6 @@
+// FP32 population storage, finite-difference phase field with density and viscosity contrasts.
+#define LBGB_FT float
+#define LBGB_MC false
+#define LBGB_VD true
+#define LBGB_PF true
+#include "lbgb_step_x_impl.cuh"

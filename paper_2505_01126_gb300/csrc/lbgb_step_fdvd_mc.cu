@@ -1,0 +1,6 @@
+// Moment-only storage, finite-difference phase field with density and viscosity contrasts.
+#define LBGB_FT float
+#define LBGB_MC true
+#define LBGB_VD true
+#define LBGB_PF true
+#include "lbgb_step_x_impl.cuh"

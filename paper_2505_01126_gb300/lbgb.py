@@ -41,7 +41,8 @@ EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_step", "lb_moments", "lb
            "lb_field_stats_static", "lb_batch_create", "lb_batch_set_stream", "lb_batch_init",
            "lb_batch_step", "lb_batch_moments", "lb_batch_diagnostics", "lb_batch_set_tile", "lb_batch_get_tile",
            "lb_batch_tune", "lb_batch_sites", "lb_batch_time", "lb_batch_destroy", "lb_velocity_statistics",
-           "lb_spectrum", "lb_state_bytes", "lb_save", "lb_load", "lb_set_density", "lb_set_gravity"]
+           "lb_spectrum", "lb_state_bytes", "lb_save", "lb_load", "lb_set_density", "lb_set_gravity",
+           "lb_set_phase_solver"]
 
 
 def _load():
@@ -98,6 +99,7 @@ def _load():
     lib.lb_save.argtypes = [vp, vp, ctypes.c_size_t]
     lib.lb_set_density.argtypes = [vp, d, d, d, d]
     lib.lb_set_gravity.argtypes = [vp, d, d, d, d]
+    lib.lb_set_phase_solver.argtypes = [vp, i]
     lib.lb_load.argtypes = [vp, vp, ctypes.c_size_t]
     return lib
 
@@ -234,6 +236,10 @@ class Box:
 
     def step(self, n: int = 1):
         _check(_lib.lb_step(self._h, int(n)))
+
+    def set_phase_solver(self, solver: str):
+        """"lb" (the D3Q7 model) or "weno5" (Eq. 4 by finite differences); before init."""
+        _check(_lib.lb_set_phase_solver(self._h, {"lb": 0, "weno5": 1}[solver]))
 
     def set_density(self, rho_l: float, rho_g: float, tau_l: float, tau_g: float):
         """Density and viscosity contrasts (lb_set_density): rho and tau of the

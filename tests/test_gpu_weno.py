@@ -1,0 +1,236 @@
+"""Parity of the CUDA path with the finite-difference phase field
+(lb_set_phase_solver(LB_PHASE_WENO5); accLB Sec. 2.1.1, Eq. 4 with WENO-5
+advection, Sec. 2.3 lattice stencils, SSP-RK3) with the FP64 oracle, through
+the C ABI.
+
+Bar: FP32 storage max|delta| <= 1e-5 in p*, u and phi after 50 steps; the
+moment-only storage equals the FP32 populations bit for bit; 16-bit storage
+states its error.  Cases: droplet, ragged and degenerate boxes (the WENO reach
+of 3 wraps several times around boxes of 1-5 sites), the three forcing kinds,
+forced turbulence with bubbles, density contrasts with buoyancy, checkpoints,
+the full 256^3 workload, translation of a smooth profile, and phase mass.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2505_01126_gb300 import inputs
+
+from test_gpu_parity import check_diagnostics, max_err, smooth_fields
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lbgb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_01126_gb300 import build
+
+    build.build()
+    from paper_2505_01126_gb300 import lbgb as mod
+
+    return mod
+
+
+def _lb_force(lbgb, force):
+    return lbgb.Force(kind=force.get("force_kind", 0), g=force.get("g", (0, 0, 0)), A=force.get("A_abc", 0.0),
+                      kf=force.get("kf", 0.0), K_target=force.get("K_target", 0.0),
+                      T_relax=force.get("T_relax", 100.0))
+
+
+def run_fd(lbgb, orc, shape, tau, M, W, sigma, phi, u, steps, force=None, storage="f32", tile=None, dens=None,
+           grav=None, oracle=True):
+    nz, ny, nx = shape
+    force = force or {}
+    b = lbgb.Box(nx, ny, nz, tau, M, W, sigma, force=_lb_force(lbgb, force), storage=storage)
+    b.set_phase_solver("weno5")
+    if dens:
+        b.set_density(*dens)
+    if grav:
+        b.set_gravity(*grav)
+    if tile is not None:
+        b.set_tile(*tile)
+    b.init(phi, u)
+    b.step(steps)
+    got = b.moments_numpy()
+    o = want = None
+    if oracle:
+        o = orc.Oracle(nx, ny, nz, tau, M, W, sigma, **force)
+        o.set_phase_solver("weno5")
+        if dens:
+            o.set_density(*dens)
+        if grav:
+            o.set_gravity(*grav)
+        o.init(phi.astype(np.float64), u.astype(np.float64))
+        o.step(steps)
+        want = o.moments()
+    return b, o, got, want
+
+
+def test_droplet_32_50_steps(lbgb, orc):
+    w = inputs.static_droplet()
+    b, o, got, want = run_fd(lbgb, orc, (32, 32, 32), w.tau, w.M, w.W, w.sigma, w.phi, w.u, 50)
+    e = max_err(got, want)
+    assert max(e) <= TOL, e
+    check_diagnostics(b.diagnostics(), o.diagnostics(), 32 ** 3)
+
+
+@pytest.mark.parametrize("shape", [(11, 13, 37), (5, 9, 70), (40, 3, 33), (2, 2, 2), (1, 1, 1), (3, 1, 5),
+                                   (7, 6, 5)])
+def test_ragged_and_degenerate_boxes(lbgb, orc, shape):
+    phi, u = smooth_fields(shape, sum(shape) + 11)
+    b, o, got, want = run_fd(lbgb, orc, shape, 0.7, 0.1, 3.0, 0.02, phi, u, 50)
+    e = max_err(got, want)
+    assert max(e) <= TOL, e
+
+
+@pytest.mark.parametrize("kind", ["const", "abc", "linear"])
+def test_forcing_kinds(lbgb, orc, kind):
+    shape = (12, 20, 36)
+    phi, u = smooth_fields(shape, 3)
+    force = {"const": dict(force_kind=1, g=(1e-5, -2e-5, 5e-6)),
+             "abc": dict(force_kind=2, A_abc=2e-5, kf=2 * math.pi / 12),
+             "linear": dict(force_kind=3, T_relax=20.0)}[kind]
+    b, o, got, want = run_fd(lbgb, orc, shape, 0.6, 0.1, 3.0, 0.01, phi, u, 50, force=force)
+    e = max_err(got, want)
+    assert max(e) <= TOL, e
+    dg, do = b.diagnostics(), o.diagnostics()
+    check_diagnostics(dg, do, int(np.prod(shape)))
+    if kind == "linear":
+        assert abs(dg[4] - do[4]) <= 1e-5 * abs(do[4]) + 1e-9
+
+
+def test_hit_64_two_bubbles(lbgb, orc):
+    w = inputs.bubbly_hit(64, 2, 10.0, seed=2)
+    force = dict(force_kind=3, T_relax=w.T_relax)
+    b, o, got, want = run_fd(lbgb, orc, (64, 64, 64), w.tau, w.M, w.W, w.sigma, w.phi, w.u, 50, force=force)
+    e = max_err(got, want)
+    assert max(e) <= TOL, e
+    check_diagnostics(b.diagnostics(), o.diagnostics(), 64 ** 3)
+
+
+def test_density_contrast_and_buoyancy(lbgb, orc):
+    """The finite-difference phase field with the Sec. 2.3 contrasts (heavy
+    droplet, ratio 10, tau 0.6 inside) sinking under gravity."""
+    w = inputs.static_droplet()
+    rr = float(1.0 + 9.0 * w.phi.astype(np.float64).mean())
+    b, o, got, want = run_fd(lbgb, orc, (32, 32, 32), w.tau, w.M, w.W, w.sigma, w.phi, w.u, 50,
+                             dens=(10.0, 1.0, 0.6, 1.0), grav=((0.0, 0.0, -1e-5), rr))
+    e = max_err(got, want)
+    assert max(e) <= TOL, e
+
+
+@pytest.mark.parametrize("tile", [(4, 8), (8, 16), (8, 5)])
+def test_moment_storage_equals_fp32_and_16bit_bounds(lbgb, orc, tile):
+    shape = (20, 24, 44)
+    phi, u = smooth_fields(shape, 17)
+    res = {}
+    for st in ("f32", "moments", "f16", "bf16"):
+        b, o, got, want = run_fd(lbgb, orc, shape, 0.7, 0.1, 3.0, 0.01, phi, u, 50, storage=st, tile=tile,
+                                 oracle=(st == "f32"))
+        res[st] = got
+        if st == "f32":
+            ref = want
+        b.close()
+    for a, c in zip(res["f32"], res["moments"]):
+        assert np.array_equal(a, c)
+    assert max(max_err(res["f32"], ref)) <= TOL
+    assert max(max_err(res["f16"], ref)) <= 2e-4, max_err(res["f16"], ref)
+    assert max(max_err(res["bf16"], ref)) <= 5e-3, max_err(res["bf16"], ref)
+
+
+@pytest.mark.parametrize("storage", ["f32", "moments"])
+def test_checkpoint_restart(lbgb, storage):
+    shape = (12, 16, 40)
+    phi, u = smooth_fields(shape, 9)
+    a = lbgb.Box(40, 16, 12, 0.8, 0.1, 3.0, 0.01, storage=storage)
+    a.set_phase_solver("weno5")
+    a.init(phi, u)
+    a.step(15)
+    buf = a.save()
+    a.step(20)
+    want = a.moments_numpy()
+    c = lbgb.Box(40, 16, 12, 0.8, 0.1, 3.0, 0.01, storage=storage)
+    c.set_phase_solver("weno5")
+    c.load(buf)
+    c.step(20)
+    for x, y in zip(c.moments_numpy(), want):
+        assert np.array_equal(x, y)
+
+
+def test_phase_solver_errors(lbgb):
+    b = lbgb.Box(8, 8, 8, 1.0, 0.1, 3.0, 0.01)
+    with pytest.raises(KeyError):
+        b.set_phase_solver("spectral")
+    b.set_phase_solver("weno5")
+    b.set_phase_solver("lb")
+    b.init(np.zeros((8, 8, 8), np.float32), np.zeros((3, 8, 8, 8), np.float32))
+    b.set_phase_solver("lb")  # no change: allowed
+    with pytest.raises(lbgb.LBError) as e:
+        b.set_phase_solver("weno5")
+    assert e.value.code == lbgb.LB_ESTATE
+    b.close()
+
+
+def test_uniform_flow_translates_a_smooth_profile(lbgb):
+    """phi = 0.5 + 0.2 sin(2 pi x / 64) carried by u = 0.05 once around the box
+    (no sharpening, D = 1e-7) on the device: back to itself within 1e-5 (the
+    oracle's scheme error is 1.9e-6; FP32 adds rounding over 1280 steps)."""
+    L = 64
+    x = np.arange(L)
+    ph = 0.5 + 0.2 * np.sin(2 * np.pi * x / L)
+    phi = inputs.to_f32(np.broadcast_to(ph[None, None, :], (2, 2, L)))
+    u = np.zeros((3, 2, 2, L), np.float32)
+    u[0] = 0.05
+    b = lbgb.Box(L, 2, 2, 0.8, 1e-7, float("inf"), 0.0)
+    b.set_phase_solver("weno5")
+    b.init(phi, u)
+    b.step(int(round(L / 0.05)))
+    _, uu, pt = b.moments_numpy()
+    assert np.abs(pt[0, 0].astype(np.float64) - ph).max() < 1e-5
+
+
+def test_full_size_256_one_step_each_parity(lbgb, orc):
+    """The benchmark workload with the finite-difference phase field, in the
+    tuned launch shape: 2 steps, every site compared with the oracle."""
+    w = inputs.bubbly_hit(256, 64, 10.0, seed=2)
+    n = 256
+    b = lbgb.Box(n, n, n, w.tau, w.M, w.W, w.sigma, force=lbgb.Force(kind=3, T_relax=w.T_relax))
+    b.set_phase_solver("weno5")
+    b.tune(2)
+    b.init(w.phi, w.u)
+    b.step(2)
+    got = b.moments_numpy()
+    dg = b.diagnostics()
+    b.close()
+    o = orc.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma, force_kind=3, T_relax=w.T_relax)
+    o.set_phase_solver("weno5")
+    o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
+    o.step(2)
+    want = o.moments()
+    do = o.diagnostics()
+    o.close()
+    e = max_err(got, want)
+    assert max(e) <= TOL, e
+    check_diagnostics(dg, do, n ** 3)
+
+
+def test_phase_mass_over_500_steps(lbgb):
+    """sum phi (FP64 reduction of FP32 phi) drifts by less than 1e-6 relative
+    over 500 steps of the 64^3 bubbly turbulence: every term is a flux
+    difference, so only rounding moves it."""
+    w = inputs.bubbly_hit(64, 2, 10.0, seed=2)
+    b = lbgb.Box(64, 64, 64, w.tau, w.M, w.W, w.sigma, force=lbgb.Force(kind=3, T_relax=w.T_relax))
+    b.set_phase_solver("weno5")
+    b.init(w.phi, w.u)
+    d0 = b.diagnostics()
+    b.step(500)
+    d = b.diagnostics()
+    assert np.isfinite(d).all()
+    assert abs(d[0] - d0[0]) <= 1e-6 * d0[0], (d0[0], d[0])
