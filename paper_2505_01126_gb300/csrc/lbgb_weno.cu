@@ -16,21 +16,26 @@
 //     form (1/72) sum over the transverse 3x3 with weights (1, 4, 1)^2 of the
 //     difference along the axis;
 //   - n = grad p / max(|grad p|, 1e-10).
-// A block takes a 32 x 4 x 4 tile: p on the tile with a halo of 3 (the WENO
+// A block takes a 32 x 8 x 8 tile: p on the tile with a halo of 3 (the WENO
 // reach; 2 would do for the stencils) in shared memory, J on the halo-1 ring,
-// then each thread forms L at two sites.  Every read of a stage is of the
-// previous stage's array or of phi_n at the thread's own site, so stage 2 may
-// write phi_n in place.
+// D lap - kappa div J in registers, then every face flux of the tile once (in
+// the space of J), then L and the stage combination at eight sites per
+// thread.  Every read of a stage is of the previous stage's array or of phi_n
+// at the thread's own site, so stage 2 may write phi_n in place.
 #include "lbgb_kernels.cuh"
 
 namespace lbgb {
 
 namespace {
 
-constexpr int WX = 32, WY = 4, WZ = 4, WH = 3;
-constexpr int SX = WX + 2 * WH, SY = WY + 2 * WH, SZ = WZ + 2 * WH;  // 38 x 10 x 10
-constexpr int JX = WX + 2, JY = WY + 2, JZ = WZ + 2;                 // 34 x 6 x 6
+constexpr int WX = 32, WY = 8, WZ = 8, WH = 3;
+constexpr int SX = WX + 2 * WH, SY = WY + 2 * WH, SZ = WZ + 2 * WH;  // 38 x 14 x 14
+constexpr int JX = WX + 2, JY = WY + 2, JZ = WZ + 2;                 // 34 x 10 x 10
 constexpr int WNT = 256;                                             // threads per block
+constexpr int SPT = WX * WY * WZ / WNT;                              // sites per thread
+// face fluxes, stored after div(J) is formed, in the space of J
+constexpr int NFX = WZ * WY * (WX + 1), NFY = WZ * (WY + 1) * WX, NFZ = (WZ + 1) * WY * WX;
+static_assert(NFX + NFY + NFZ <= 3 * JX * JY * JZ, "fluxes fit in the space of J");
 
 __device__ __forceinline__ float weno5(float vm2, float vm1, float v0, float v1, float v2) {
     const float q0 = (2.f * vm2 - 7.f * vm1 + 11.f * v0) * (1.f / 6.f);
@@ -44,23 +49,16 @@ __device__ __forceinline__ float weno5(float vm2, float vm1, float v0, float v1,
     const float b2 = (13.f / 12.f) * d2 * d2 + 0.25f * e2 * e2;
     // weights d_k / (eps + b_k)^2, normalised; multiplied through by the
     // product of the three denominators so that one division remains (each
-    // (eps + b)^2 lies in [1e-12, ~1e3], so the products stay normal in FP32)
+    // (eps + b)^2 lies in [1e-12, ~1e3], so the products stay normal in FP32,
+    // as the fast division needs)
     constexpr float eps = 1e-6f;
     const float t0 = (eps + b0) * (eps + b0), t1 = (eps + b1) * (eps + b1), t2 = (eps + b2) * (eps + b2);
     const float a0 = 0.1f * (t1 * t2), a1 = 0.6f * (t0 * t2), a2 = 0.3f * (t0 * t1);
-    return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+    return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
 }
 
 // Periodic wrap of v in [-n, 2n).
 __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
-
-// Flux u_f p_f through the face between p[2] and p[3] of the six values
-// p[0..5] along an axis, u_f = (ul + ur)/2.
-__device__ __forceinline__ float face_flux(const float (&p)[6], float ul, float ur) {
-    const float uf = 0.5f * (ul + ur);
-    const float pf = uf >= 0.f ? weno5(p[0], p[1], p[2], p[3], p[4]) : weno5(p[5], p[4], p[3], p[2], p[1]);
-    return uf * pf;
-}
 
 __global__ void __launch_bounds__(WNT) weno_stage_kernel(const float* __restrict__ pin, const float* phin,
                                                          const float* __restrict__ ux, const float* __restrict__ uy,
@@ -68,22 +66,26 @@ __global__ void __launch_bounds__(WNT) weno_stage_kernel(const float* __restrict
                                                          int nz, float D, float kap, int stage) {
     __shared__ float s_p[SZ][SY][SX];
     __shared__ float s_J[3][JZ][JY][JX];
+    float* s_F = &s_J[0][0][0][0];  // Fx, Fy, Fz after div(J)
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * WX, y0 = blockIdx.y * WY, z0 = blockIdx.z * WZ;
     const long long plane = (long long)nx * ny;
-
     // the tile and its halo span [x0 - WH, x0 + WX + WH - 1] with x0 < nx, within
     // [-n, 2n) unless the box is shorter than the tile plus its halo
     const bool small = nx < WX + WH || ny < WY + WH || nz < WZ + WH;
-    for (int i = tid; i < SX * SY * SZ; i += WNT) {
-        const int lx = i % SX, ly = (i / SX) % SY, lz = i / (SX * SY);
-        int gx, gy, gz;
-        if (small) {
-            gx = wrap_mod(x0 - WH + lx, nx); gy = wrap_mod(y0 - WH + ly, ny); gz = wrap_mod(z0 - WH + lz, nz);
-        } else {
-            gx = wrap1(x0 - WH + lx, nx); gy = wrap1(y0 - WH + ly, ny); gz = wrap1(z0 - WH + lz, nz);
-        }
-        s_p[lz][ly][lx] = __ldg(pin + gz * plane + (long long)gy * nx + gx);
+    auto wx = [&](int v) { return small ? wrap_mod(v, nx) : wrap1(v, nx); };
+    auto wy = [&](int v) { return small ? wrap_mod(v, ny) : wrap1(v, ny); };
+    auto wz = [&](int v) { return small ? wrap_mod(v, nz) : wrap1(v, nz); };
+
+    // a warp per halo row; a lane loads the columns lane and lane + 32 (< SX)
+    const int warp = tid >> 5, lane = tid & 31;
+    constexpr int NW = WNT / 32;
+    const int gxa = wx(x0 - WH + lane), gxb = lane + 32 < SX ? wx(x0 - WH + lane + 32) : 0;
+    for (int r = warp; r < SY * SZ; r += NW) {
+        const int ly = r % SY, lz = r / SY;
+        const float* row = pin + wz(z0 - WH + lz) * plane + (long long)wy(y0 - WH + ly) * nx;
+        s_p[lz][ly][lane] = __ldg(row + gxa);
+        if (lane + 32 < SX) s_p[lz][ly][lane + 32] = __ldg(row + gxb);
     }
     __syncthreads();
 
@@ -106,22 +108,22 @@ __global__ void __launch_bounds__(WNT) weno_stage_kernel(const float* __restrict
         gz *= 1.f / 72.f;
         const float m = sqrtf(gx * gx + gy * gy + gz * gz);
         const float p = s_p[cz][cy][cx];
-        const float w = fmaxf(p * (1.f - p), 0.f) / fmaxf(m, 1e-10f);
+        const float w = __fdividef(fmaxf(p * (1.f - p), 0.f), fmaxf(m, 1e-10f));
         s_J[0][jz][jy][jx] = w * gx;
         s_J[1][jz][jy][jx] = w * gy;
         s_J[2][jz][jy][jx] = w * gz;
     }
     __syncthreads();
 
-    for (int i = tid; i < WX * WY * WZ; i += WNT) {
+    // D lap(p) - kappa div(J) at this thread's sites (site i = tid + k WNT)
+    float Ld[SPT];
+#pragma unroll
+    for (int k = 0; k < SPT; ++k) {
+        const int i = tid + k * WNT;
         const int tx = i % WX, ty = (i / WX) % WY, tz = i / (WX * WY);
-        const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
-        if (gx >= nx || gy >= ny || gz >= nz) continue;
         const int cx = tx + WH, cy = ty + WH, cz = tz + WH;
         const int jx = tx + 1, jy = ty + 1, jz = tz + 1;
         const float p0 = s_p[cz][cy][cx];
-
-        // lap(p) and div(J), the 26 neighbours with weights (1, 4, 1)^3 / 216
         float lap = 0.f, dj = 0.f;
 #pragma unroll
         for (int c = -1; c <= 1; ++c)
@@ -138,44 +140,77 @@ __global__ void __launch_bounds__(WNT) weno_stage_kernel(const float* __restrict
                 dj = fmaf(wbc, s_J[1][jz + c][jy + 1][jx + b] - s_J[1][jz + c][jy - 1][jx + b], dj);
                 dj = fmaf(wbc, s_J[2][jz + 1][jy + c][jx + b] - s_J[2][jz - 1][jy + c][jx + b], dj);
             }
-        lap *= 1.f / 36.f;  // (2/cs^2) / 216
-        dj *= 1.f / 72.f;
+        // (2/cs^2) / 216 for lap, 1/72 for the divergence
+        Ld[k] = fmaf(D * (1.f / 36.f), lap, -kap * (1.f / 72.f) * dj);
+    }
+    __syncthreads();  // J is read; its space takes the face fluxes
 
-        // advective flux differences
-        const long long s = gz * plane + (long long)gy * nx + gx;
-        const int xm = gx == 0 ? nx - 1 : gx - 1, xp = gx == nx - 1 ? 0 : gx + 1;
-        const int ym = gy == 0 ? ny - 1 : gy - 1, yp = gy == ny - 1 ? 0 : gy + 1;
-        const int zm = gz == 0 ? nz - 1 : gz - 1, zp = gz == nz - 1 ? 0 : gz + 1;
-        const long long row = gz * plane + (long long)gy * nx;
-        const float u0 = __ldg(ux + s), uxm = __ldg(ux + row + xm), uxp = __ldg(ux + row + xp);
-        const float v0 = __ldg(uy + s), uym = __ldg(uy + gz * plane + (long long)ym * nx + gx);
-        const float uyp = __ldg(uy + gz * plane + (long long)yp * nx + gx);
-        const float w0 = __ldg(uz + s), uzm = __ldg(uz + zm * plane + (long long)gy * nx + gx);
-        const float uzp = __ldg(uz + zp * plane + (long long)gy * nx + gx);
-        float adv = 0.f;
-        {
-            float pl[6], pr[6];  // the six values around face x-1/2 and around x+1/2
+    // advective flux u_f p_f of every face of the tile, once: face f along an
+    // axis lies between local sites f - 1 and f.  A warp takes a row of faces
+    // (lane = the face's x, or its index along x for the x faces).
+    auto flux = [](const float (&v)[6], float ul, float ur) {
+        const float uf = 0.5f * (ul + ur);
+        // the five values upwind of the face, selected without a branch (a warp
+        // holds both signs of u in a flow)
+        const bool up = uf >= 0.f;
+        return uf * weno5(up ? v[0] : v[5], up ? v[1] : v[4], up ? v[2] : v[3], up ? v[3] : v[2], up ? v[4] : v[1]);
+    };
+    const int gxl = wx(x0 + lane), gxm = wx(x0 + lane - 1);  // this lane's site and its left neighbour
+    {
+        float* Fx = s_F;
+        for (int r = warp; r < WY * WZ; r += NW) {  // x faces: rows (y, z), faces f = lane and 32
+            const int ly = r % WY, lz = r / WY;
+            const float* urow = ux + wz(z0 + lz) * plane + (long long)wy(y0 + ly) * nx;
+            float v[6];
 #pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                pl[j] = s_p[cz][cy][cx - 3 + j];
-                pr[j] = s_p[cz][cy][cx - 2 + j];
-            }
-            adv += face_flux(pr, u0, uxp) - face_flux(pl, uxm, u0);
+            for (int j = 0; j < 6; ++j) v[j] = s_p[lz + WH][ly + WH][lane + j];
+            Fx[(lz * WY + ly) * (WX + 1) + lane] = flux(v, __ldg(urow + gxm), __ldg(urow + gxl));
+            if (lane == 0) {
 #pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                pl[j] = s_p[cz][cy - 3 + j][cx];
-                pr[j] = s_p[cz][cy - 2 + j][cx];
+                for (int j = 0; j < 6; ++j) v[j] = s_p[lz + WH][ly + WH][WX + j];
+                Fx[(lz * WY + ly) * (WX + 1) + WX] = flux(v, __ldg(urow + wx(x0 + WX - 1)), __ldg(urow + wx(x0 + WX)));
             }
-            adv += face_flux(pr, v0, uyp) - face_flux(pl, uym, v0);
-#pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                pl[j] = s_p[cz - 3 + j][cy][cx];
-                pr[j] = s_p[cz - 2 + j][cy][cx];
-            }
-            adv += face_flux(pr, w0, uzp) - face_flux(pl, uzm, w0);
         }
-        const float L = fmaf(D, lap, -fmaf(kap, dj, adv));
-        const float q = p0 + L;
+        float* Fy = s_F + NFX;
+        for (int r = warp; r < (WY + 1) * WZ; r += NW) {  // y faces: rows (f, z), lane = x
+            const int f = r % (WY + 1), lz = r / (WY + 1);
+            const long long zb = wz(z0 + lz) * plane;
+            float v[6];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) v[j] = s_p[lz + WH][f + j][lane + WH];
+            const float ul = __ldg(uy + zb + (long long)wy(y0 + f - 1) * nx + gxl);
+            const float ur = __ldg(uy + zb + (long long)wy(y0 + f) * nx + gxl);
+            Fy[(lz * (WY + 1) + f) * WX + lane] = flux(v, ul, ur);
+        }
+        float* Fz = s_F + NFX + NFY;
+        for (int r = warp; r < (WZ + 1) * WY; r += NW) {  // z faces: rows (y, f), lane = x
+            const int ly = r % WY, f = r / WY;
+            const long long yb = (long long)wy(y0 + ly) * nx + gxl;
+            float v[6];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) v[j] = s_p[f + j][ly + WH][lane + WH];
+            const float ul = __ldg(uz + wz(z0 + f - 1) * plane + yb);
+            const float ur = __ldg(uz + wz(z0 + f) * plane + yb);
+            Fz[(f * WY + ly) * WX + lane] = flux(v, ul, ur);
+        }
+    }
+    __syncthreads();
+
+#pragma unroll
+    for (int k = 0; k < SPT; ++k) {
+        const int i = tid + k * WNT;
+        const int tx = i % WX, ty = (i / WX) % WY, tz = i / (WX * WY);
+        const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
+        if (gx >= nx || gy >= ny || gz >= nz) continue;
+        const float* Fx = s_F;
+        const float* Fy = s_F + NFX;
+        const float* Fz = s_F + NFX + NFY;
+        const int ix = (tz * WY + ty) * (WX + 1) + tx;
+        const int iy = (tz * (WY + 1) + ty) * WX + tx;
+        const int iz = (tz * WY + ty) * WX + tx;
+        const float adv = (Fx[ix + 1] - Fx[ix]) + (Fy[iy + WX] - Fy[iy]) + (Fz[iz + WX * WY] - Fz[iz]);
+        const float q = s_p[tz + WH][ty + WH][tx + WH] + (Ld[k] - adv);
+        const long long s = gz * plane + (long long)gy * nx + gx;
         float r;
         // weights that sum to exactly 1 in FP32, so that a uniform field stays
         // uniform bit for bit (1/3 + 2/3 rounded separately would not)
