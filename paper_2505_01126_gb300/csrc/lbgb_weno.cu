@@ -16,26 +16,31 @@
 //     form (1/72) sum over the transverse 3x3 with weights (1, 4, 1)^2 of the
 //     difference along the axis;
 //   - n = grad p / max(|grad p|, 1e-10).
-// A block takes a 32 x 8 x 8 tile: p on the tile with a halo of 3 (the WENO
-// reach; 2 would do for the stencils) in shared memory, J on the halo-1 ring,
-// D lap - kappa div J in registers, then every face flux of the tile once (in
-// the space of J), then L and the stage combination at eight sites per
-// thread.  Every read of a stage is of the previous stage's array or of phi_n
-// at the thread's own site, so stage 2 may write phi_n in place.
+// Every read of a stage is of the previous stage's array or of phi_n at the
+// thread's own site, so stage 2 may write phi_n in place.
 #include "lbgb_kernels.cuh"
 
 namespace lbgb {
 
 namespace {
 
-constexpr int WX = 32, WY = 8, WZ = 8, WH = 3;
-constexpr int SX = WX + 2 * WH, SY = WY + 2 * WH, SZ = WZ + 2 * WH;  // 38 x 14 x 14
-constexpr int JX = WX + 2, JY = WY + 2, JZ = WZ + 2;                 // 34 x 10 x 10
-constexpr int WNT = 256;                                             // threads per block
-constexpr int SPT = WX * WY * WZ / WNT;                              // sites per thread
-// face fluxes, stored after div(J) is formed, in the space of J
-constexpr int NFX = WZ * WY * (WX + 1), NFY = WZ * (WY + 1) * WX, NFZ = (WZ + 1) * WY * WX;
-static_assert(NFX + NFY + NFZ <= 3 * JX * JY * JZ, "fluxes fit in the space of J");
+// A block takes a 32 x 8 column tile and marches over a z-chunk: phi planes
+// (with a halo of 3 in x and y) in a ring of 8, J planes (halo 1) in a ring
+// of 4.  Per plane z: J of plane z + 1; barrier; the x- and y-face fluxes of
+// plane z, each once, spread over the block (264 + 288 faces), and per thread
+// D lap - kappa div J and the flux through its column's upper z face (the
+// lower one carried from the plane below); barrier; the stage combination,
+// then the load of plane z + 4.
+constexpr int TX = 32, TY = 8, WH = 3;
+constexpr int PX = TX + 2 * WH, PY = TY + 2 * WH, NP = PX * PY;  // 38 x 14
+constexpr int QX = TX + 2, QY = TY + 2, NQ = QX * QY;            // 34 x 10
+constexpr int WNT = TX * TY;                                       // 256 threads
+constexpr int NPL = (NP + WNT - 1) / WNT;                          // phi elements per thread
+constexpr int NJL = (NQ + WNT - 1) / WNT;                          // J elements per thread
+constexpr int NFX = TY * (TX + 1), NFY = (TY + 1) * TX;            // faces per plane
+constexpr int NFL = (NFY + WNT - 1) / WNT;                         // faces per thread (>= x's)
+constexpr int PR = 8, JR = 4;                                      // ring sizes (powers of 2)
+static_assert(NFX <= NFL * WNT, "x faces fit the per-thread face slots");
 
 __device__ __forceinline__ float weno5(float vm2, float vm1, float v0, float v1, float v2) {
     const float q0 = (2.f * vm2 - 7.f * vm1 + 11.f * v0) * (1.f / 6.f);
@@ -57,170 +62,197 @@ __device__ __forceinline__ float weno5(float vm2, float vm1, float v0, float v1,
     return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
 }
 
-// Periodic wrap of v in [-n, 2n).
-__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+// Flux u_f p_f through the face between v[2] and v[3] of six values along an
+// axis, u_f = (ul + ur)/2; the five values upwind of the face are selected
+// without a branch (a warp holds both signs of u in a flow).
+__device__ __forceinline__ float face_flux(const float (&v)[6], float ul, float ur) {
+    const float uf = 0.5f * (ul + ur);
+    const bool up = uf >= 0.f;
+    return uf * weno5(up ? v[0] : v[5], up ? v[1] : v[4], up ? v[2] : v[3], up ? v[3] : v[2], up ? v[4] : v[1]);
+}
 
 __global__ void __launch_bounds__(WNT) weno_stage_kernel(const float* __restrict__ pin, const float* phin,
                                                          const float* __restrict__ ux, const float* __restrict__ uy,
                                                          const float* __restrict__ uz, float* out, int nx, int ny,
-                                                         int nz, float D, float kap, int stage) {
-    __shared__ float s_p[SZ][SY][SX];
-    __shared__ float s_J[3][JZ][JY][JX];
-    float* s_F = &s_J[0][0][0][0];  // Fx, Fy, Fz after div(J)
+                                                         int nz, int zc, float D, float kap, int stage) {
+    __shared__ float s_p[PR][PY][PX];
+    __shared__ float s_J[JR][3][QY][QX];
+    __shared__ float s_Fx[TY][TX + 1];
+    __shared__ float s_Fy[TY + 1][TX];
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * WX, y0 = blockIdx.y * WY, z0 = blockIdx.z * WZ;
+    const int lx = tid % TX, ly = tid / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
+    const int z1 = min(z0 + zc, nz);
     const long long plane = (long long)nx * ny;
-    // the tile and its halo span [x0 - WH, x0 + WX + WH - 1] with x0 < nx, within
-    // [-n, 2n) unless the box is shorter than the tile plus its halo
-    const bool small = nx < WX + WH || ny < WY + WH || nz < WZ + WH;
-    auto wx = [&](int v) { return small ? wrap_mod(v, nx) : wrap1(v, nx); };
-    auto wy = [&](int v) { return small ? wrap_mod(v, ny) : wrap1(v, ny); };
-    auto wz = [&](int v) { return small ? wrap_mod(v, nz) : wrap1(v, nz); };
 
-    // a warp per halo row; a lane loads the columns lane and lane + 32 (< SX)
-    const int warp = tid >> 5, lane = tid & 31;
-    constexpr int NW = WNT / 32;
-    const int gxa = wx(x0 - WH + lane), gxb = lane + 32 < SX ? wx(x0 - WH + lane + 32) : 0;
-    for (int r = warp; r < SY * SZ; r += NW) {
-        const int ly = r % SY, lz = r / SY;
-        const float* row = pin + wz(z0 - WH + lz) * plane + (long long)wy(y0 - WH + ly) * nx;
-        s_p[lz][ly][lane] = __ldg(row + gxa);
-        if (lane + 32 < SX) s_p[lz][ly][lane + 32] = __ldg(row + gxb);
-    }
-    __syncthreads();
-
-    // J on the halo-1 ring: site (jx, jy, jz) is s_p[jz + 2][jy + 2][jx + 2]
-    for (int i = tid; i < JX * JY * JZ; i += WNT) {
-        const int jx = i % JX, jy = (i / JX) % JY, jz = i / (JX * JY);
-        const int cx = jx + 2, cy = jy + 2, cz = jz + 2;
-        float gx = 0.f, gy = 0.f, gz = 0.f;
+    // fixed in-plane offsets: this thread's phi-plane elements, J elements,
+    // faces (left/right site of each), and its own column
+    int p_off[NPL], p_dst[NPL];
 #pragma unroll
-        for (int b = -1; b <= 1; ++b)
-#pragma unroll
-            for (int c = -1; c <= 1; ++c) {
-                const float wbc = (b == 0 ? 4.f : 1.f) * (c == 0 ? 4.f : 1.f);
-                gx = fmaf(wbc, s_p[cz + c][cy + b][cx + 1] - s_p[cz + c][cy + b][cx - 1], gx);
-                gy = fmaf(wbc, s_p[cz + c][cy + 1][cx + b] - s_p[cz + c][cy - 1][cx + b], gy);
-                gz = fmaf(wbc, s_p[cz + 1][cy + c][cx + b] - s_p[cz - 1][cy + c][cx + b], gz);
-            }
-        gx *= 1.f / 72.f;
-        gy *= 1.f / 72.f;
-        gz *= 1.f / 72.f;
-        const float m = sqrtf(gx * gx + gy * gy + gz * gz);
-        const float p = s_p[cz][cy][cx];
-        const float w = __fdividef(fmaxf(p * (1.f - p), 0.f), fmaxf(m, 1e-10f));
-        s_J[0][jz][jy][jx] = w * gx;
-        s_J[1][jz][jy][jx] = w * gy;
-        s_J[2][jz][jy][jx] = w * gz;
-    }
-    __syncthreads();
-
-    // D lap(p) - kappa div(J) at this thread's sites (site i = tid + k WNT)
-    float Ld[SPT];
-#pragma unroll
-    for (int k = 0; k < SPT; ++k) {
+    for (int k = 0; k < NPL; ++k) {
         const int i = tid + k * WNT;
-        const int tx = i % WX, ty = (i / WX) % WY, tz = i / (WX * WY);
-        const int cx = tx + WH, cy = ty + WH, cz = tz + WH;
-        const int jx = tx + 1, jy = ty + 1, jz = tz + 1;
-        const float p0 = s_p[cz][cy][cx];
-        float lap = 0.f, dj = 0.f;
+        p_dst[k] = i < NP ? i : -1;
+        const int py = i / PX, px = i - (i / PX) * PX;
+        p_off[k] = i < NP ? wrap_mod(y0 - WH + py, ny) * nx + wrap_mod(x0 - WH + px, nx) : 0;
+    }
+    int fx_i[NFL], fx_l[NFL], fx_r[NFL], fy_i[NFL], fy_l[NFL], fy_r[NFL];
 #pragma unroll
-        for (int c = -1; c <= 1; ++c)
+    for (int k = 0; k < NFL; ++k) {
+        const int i = tid + k * WNT;
+        fx_i[k] = i < NFX ? i : -1;  // x face f of row r: between x0 + f - 1 and x0 + f
+        const int r = i / (TX + 1), f = i - (i / (TX + 1)) * (TX + 1);
+        const int yr = wrap_mod(y0 + r, ny);
+        fx_l[k] = i < NFX ? yr * nx + wrap_mod(x0 + f - 1, nx) : 0;
+        fx_r[k] = i < NFX ? yr * nx + wrap_mod(x0 + f, nx) : 0;
+        fy_i[k] = i < NFY ? i : -1;  // y face f of column c: between y0 + f - 1 and y0 + f
+        const int fy = i / TX, c = i - (i / TX) * TX;
+        const int xc = wrap_mod(x0 + c, nx);
+        fy_l[k] = i < NFY ? wrap_mod(y0 + fy - 1, ny) * nx + xc : 0;
+        fy_r[k] = i < NFY ? wrap_mod(y0 + fy, ny) * nx + xc : 0;
+    }
+    const int own = wrap_mod(y0 + ly, ny) * nx + wrap_mod(x0 + lx, nx);
+    const bool active = x0 + lx < nx && y0 + ly < ny;
+
+    auto load_plane = [&](int zp) {
+        const float* src = pin + (long long)wrap_mod(zp, nz) * plane;
+        float* dst = &s_p[zp & (PR - 1)][0][0];
+#pragma unroll
+        for (int k = 0; k < NPL; ++k)
+            if (p_dst[k] >= 0) dst[p_dst[k]] = __ldg(src + p_off[k]);
+    };
+    // J of plane zp on the halo-1 ring, from phi planes zp - 1 .. zp + 1
+    auto make_J = [&](int zp) {
+        const float(*Pm)[PX] = s_p[(zp - 1) & (PR - 1)];
+        const float(*P0)[PX] = s_p[zp & (PR - 1)];
+        const float(*Pp)[PX] = s_p[(zp + 1) & (PR - 1)];
+#pragma unroll
+        for (int k = 0; k < NJL; ++k) {
+            const int i = tid + k * WNT;
+            if (i >= NQ) continue;
+            const int qy = i / QX, qx = i - (i / QX) * QX;
+            const int cy = qy + 2, cx = qx + 2;
+            float gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
             for (int b = -1; b <= 1; ++b) {
-                const float wbc = (b == 0 ? 4.f : 1.f) * (c == 0 ? 4.f : 1.f);
+                const float wb = b == 0 ? 4.f : 1.f;
+                // along x and y: transverse (y or x, z) weights, z from the three planes
+                gx = fmaf(wb, (Pm[cy + b][cx + 1] - Pm[cy + b][cx - 1]) + (Pp[cy + b][cx + 1] - Pp[cy + b][cx - 1]),
+                          gx);
+                gx = fmaf(4.f * wb, P0[cy + b][cx + 1] - P0[cy + b][cx - 1], gx);
+                gy = fmaf(wb, (Pm[cy + 1][cx + b] - Pm[cy - 1][cx + b]) + (Pp[cy + 1][cx + b] - Pp[cy - 1][cx + b]),
+                          gy);
+                gy = fmaf(4.f * wb, P0[cy + 1][cx + b] - P0[cy - 1][cx + b], gy);
 #pragma unroll
-                for (int a = -1; a <= 1; ++a) {
-                    if (a == 0 && b == 0 && c == 0) continue;
-                    const float wabc = wbc * (a == 0 ? 4.f : 1.f);
-                    lap = fmaf(wabc, s_p[cz + c][cy + b][cx + a] - p0, lap);
-                }
-                dj = fmaf(wbc, s_J[0][jz + c][jy + b][jx + 1] - s_J[0][jz + c][jy + b][jx - 1], dj);
-                dj = fmaf(wbc, s_J[1][jz + c][jy + 1][jx + b] - s_J[1][jz + c][jy - 1][jx + b], dj);
-                dj = fmaf(wbc, s_J[2][jz + 1][jy + c][jx + b] - s_J[2][jz - 1][jy + c][jx + b], dj);
+                for (int a = -1; a <= 1; ++a)
+                    gz = fmaf(wb * (a == 0 ? 4.f : 1.f), Pp[cy + b][cx + a] - Pm[cy + b][cx + a], gz);
             }
-        // (2/cs^2) / 216 for lap, 1/72 for the divergence
-        Ld[k] = fmaf(D * (1.f / 36.f), lap, -kap * (1.f / 72.f) * dj);
-    }
-    __syncthreads();  // J is read; its space takes the face fluxes
-
-    // advective flux u_f p_f of every face of the tile, once: face f along an
-    // axis lies between local sites f - 1 and f.  A warp takes a row of faces
-    // (lane = the face's x, or its index along x for the x faces).
-    auto flux = [](const float (&v)[6], float ul, float ur) {
-        const float uf = 0.5f * (ul + ur);
-        // the five values upwind of the face, selected without a branch (a warp
-        // holds both signs of u in a flow)
-        const bool up = uf >= 0.f;
-        return uf * weno5(up ? v[0] : v[5], up ? v[1] : v[4], up ? v[2] : v[3], up ? v[3] : v[2], up ? v[4] : v[1]);
+            gx *= 1.f / 72.f;
+            gy *= 1.f / 72.f;
+            gz *= 1.f / 72.f;
+            const float m = sqrtf(gx * gx + gy * gy + gz * gz);
+            const float p = P0[cy][cx];
+            const float w = __fdividef(fmaxf(p * (1.f - p), 0.f), fmaxf(m, 1e-10f));
+            s_J[zp & (JR - 1)][0][qy][qx] = w * gx;
+            s_J[zp & (JR - 1)][1][qy][qx] = w * gy;
+            s_J[zp & (JR - 1)][2][qy][qx] = w * gz;
+        }
     };
-    const int gxl = wx(x0 + lane), gxm = wx(x0 + lane - 1);  // this lane's site and its left neighbour
-    {
-        float* Fx = s_F;
-        for (int r = warp; r < WY * WZ; r += NW) {  // x faces: rows (y, z), faces f = lane and 32
-            const int ly = r % WY, lz = r / WY;
-            const float* urow = ux + wz(z0 + lz) * plane + (long long)wy(y0 + ly) * nx;
-            float v[6];
+    // flux through the z face zf + 1/2 of this thread's column
+    const int pcy = ly + WH, pcx = lx + WH;
+    auto z_flux = [&](int zf, float ul, float ur) {
+        float v[6];
 #pragma unroll
-            for (int j = 0; j < 6; ++j) v[j] = s_p[lz + WH][ly + WH][lane + j];
-            Fx[(lz * WY + ly) * (WX + 1) + lane] = flux(v, __ldg(urow + gxm), __ldg(urow + gxl));
-            if (lane == 0) {
+        for (int j = 0; j < 6; ++j) v[j] = s_p[(zf - 2 + j) & (PR - 1)][pcy][pcx];
+        return face_flux(v, ul, ur);
+    };
+
+    // prologue: phi planes z0 - 3 .. z0 + 3, J of z0 - 1 and z0, the z face below z0
+    for (int zp = z0 - WH; zp <= z0 + WH; ++zp) load_plane(zp);
+    __syncthreads();
+    make_J(z0 - 1);
+    make_J(z0);
+    float uzc = __ldg(uz + (long long)wrap_mod(z0, nz) * plane + own);  // uz of the current plane
+    float fzm = z_flux(z0 - 1, __ldg(uz + (long long)wrap_mod(z0 - 1, nz) * plane + own), uzc);
+
+    for (int z = z0; z < z1; ++z) {
+        make_J(z + 1);
+        __syncthreads();  // J of z + 1 and phi of z + 3 are in place
+
+        const long long zb = (long long)z * plane;  // z < nz
+        const float(*P0)[PX] = s_p[z & (PR - 1)];
+        // x and y faces of plane z
 #pragma unroll
-                for (int j = 0; j < 6; ++j) v[j] = s_p[lz + WH][ly + WH][WX + j];
-                Fx[(lz * WY + ly) * (WX + 1) + WX] = flux(v, __ldg(urow + wx(x0 + WX - 1)), __ldg(urow + wx(x0 + WX)));
+        for (int k = 0; k < NFL; ++k) {
+            if (fx_i[k] >= 0) {
+                const int r = fx_i[k] / (TX + 1), f = fx_i[k] - r * (TX + 1);
+                float v[6];
+#pragma unroll
+                for (int j = 0; j < 6; ++j) v[j] = P0[r + WH][f + j];
+                (&s_Fx[0][0])[fx_i[k]] = face_flux(v, __ldg(ux + zb + fx_l[k]), __ldg(ux + zb + fx_r[k]));
+            }
+            if (fy_i[k] >= 0) {
+                const int f = fy_i[k] / TX, c = fy_i[k] - f * TX;
+                float v[6];
+#pragma unroll
+                for (int j = 0; j < 6; ++j) v[j] = P0[f + j][c + WH];
+                (&s_Fy[0][0])[fy_i[k]] = face_flux(v, __ldg(uy + zb + fy_l[k]), __ldg(uy + zb + fy_r[k]));
             }
         }
-        float* Fy = s_F + NFX;
-        for (int r = warp; r < (WY + 1) * WZ; r += NW) {  // y faces: rows (f, z), lane = x
-            const int f = r % (WY + 1), lz = r / (WY + 1);
-            const long long zb = wz(z0 + lz) * plane;
-            float v[6];
+        // D lap(p) - kappa div(J) at (x, y, z), the 26 neighbours with weights (1, 4, 1)^3 / 216
+        float lap = 0.f, dj = 0.f;
+        {
+            const float p0 = P0[pcy][pcx];
+            const int jy = ly + 1, jx = lx + 1;
 #pragma unroll
-            for (int j = 0; j < 6; ++j) v[j] = s_p[lz + WH][f + j][lane + WH];
-            const float ul = __ldg(uy + zb + (long long)wy(y0 + f - 1) * nx + gxl);
-            const float ur = __ldg(uy + zb + (long long)wy(y0 + f) * nx + gxl);
-            Fy[(lz * (WY + 1) + f) * WX + lane] = flux(v, ul, ur);
-        }
-        float* Fz = s_F + NFX + NFY;
-        for (int r = warp; r < (WZ + 1) * WY; r += NW) {  // z faces: rows (y, f), lane = x
-            const int ly = r % WY, f = r / WY;
-            const long long yb = (long long)wy(y0 + ly) * nx + gxl;
-            float v[6];
+            for (int c = -1; c <= 1; ++c) {
+                const float(*P)[PX] = s_p[(z + c) & (PR - 1)];
+                const float(*J0)[QX] = s_J[(z + c) & (JR - 1)][0];
+                const float(*J1)[QX] = s_J[(z + c) & (JR - 1)][1];
 #pragma unroll
-            for (int j = 0; j < 6; ++j) v[j] = s_p[f + j][ly + WH][lane + WH];
-            const float ul = __ldg(uz + wz(z0 + f - 1) * plane + yb);
-            const float ur = __ldg(uz + wz(z0 + f) * plane + yb);
-            Fz[(f * WY + ly) * WX + lane] = flux(v, ul, ur);
+                for (int b = -1; b <= 1; ++b) {
+                    const float wbc = (b == 0 ? 4.f : 1.f) * (c == 0 ? 4.f : 1.f);
+#pragma unroll
+                    for (int a = -1; a <= 1; ++a) {
+                        if (a == 0 && b == 0 && c == 0) continue;
+                        lap = fmaf(wbc * (a == 0 ? 4.f : 1.f), P[pcy + b][pcx + a] - p0, lap);
+                    }
+                    dj = fmaf(wbc, J0[jy + b][jx + 1] - J0[jy + b][jx - 1], dj);
+                    dj = fmaf(wbc, J1[jy + 1][jx + b] - J1[jy - 1][jx + b], dj);
+                }
+            }
+            const float(*J2m)[QX] = s_J[(z - 1) & (JR - 1)][2];
+            const float(*J2p)[QX] = s_J[(z + 1) & (JR - 1)][2];
+#pragma unroll
+            for (int b = -1; b <= 1; ++b)
+#pragma unroll
+                for (int a = -1; a <= 1; ++a)
+                    dj = fmaf((b == 0 ? 4.f : 1.f) * (a == 0 ? 4.f : 1.f), J2p[jy + b][jx + a] - J2m[jy + b][jx + a],
+                              dj);
         }
-    }
-    __syncthreads();
+        // the upper z face of this column
+        const float uzn = __ldg(uz + (long long)wrap_mod(z + 1, nz) * plane + own);
+        const float fzp = z_flux(z, uzc, uzn);
+        __syncthreads();  // the plane's x and y face fluxes are in place
 
-#pragma unroll
-    for (int k = 0; k < SPT; ++k) {
-        const int i = tid + k * WNT;
-        const int tx = i % WX, ty = (i / WX) % WY, tz = i / (WX * WY);
-        const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
-        if (gx >= nx || gy >= ny || gz >= nz) continue;
-        const float* Fx = s_F;
-        const float* Fy = s_F + NFX;
-        const float* Fz = s_F + NFX + NFY;
-        const int ix = (tz * WY + ty) * (WX + 1) + tx;
-        const int iy = (tz * (WY + 1) + ty) * WX + tx;
-        const int iz = (tz * WY + ty) * WX + tx;
-        const float adv = (Fx[ix + 1] - Fx[ix]) + (Fy[iy + WX] - Fy[iy]) + (Fz[iz + WX * WY] - Fz[iz]);
-        const float q = s_p[tz + WH][ty + WH][tx + WH] + (Ld[k] - adv);
-        const long long s = gz * plane + (long long)gy * nx + gx;
-        float r;
-        // weights that sum to exactly 1 in FP32, so that a uniform field stays
-        // uniform bit for bit (1/3 + 2/3 rounded separately would not)
-        if (stage == 0) r = q;
-        else if (stage == 1) r = fmaf(0.75f, phin[s], 0.25f * q);
-        else {
-            const float pn = phin[s];
-            r = fmaf(2.f / 3.f, q - pn, pn);
+        const float adv = (s_Fx[ly][lx + 1] - s_Fx[ly][lx]) + (s_Fy[ly + 1][lx] - s_Fy[ly][lx]) + (fzp - fzm);
+        const float L = fmaf(D * (1.f / 36.f), lap, -kap * (1.f / 72.f) * dj) - adv;
+        if (active) {
+            const long long s = zb + own;
+            const float q = P0[pcy][pcx] + L;
+            float r;
+            // weights that sum to exactly 1 in FP32, so that a uniform field stays
+            // uniform bit for bit (1/3 + 2/3 rounded separately would not)
+            if (stage == 0) r = q;
+            else if (stage == 1) r = fmaf(0.75f, phin[s], 0.25f * q);
+            else {
+                const float pn = phin[s];
+                r = fmaf(2.f / 3.f, q - pn, pn);
+            }
+            out[s] = r;
         }
-        out[s] = r;
+        fzm = fzp;
+        uzc = uzn;
+        load_plane(z + 4);
     }
 }
 
@@ -229,8 +261,9 @@ __global__ void __launch_bounds__(WNT) weno_stage_kernel(const float* __restrict
 cudaError_t launch_weno_stage(int stage, const float* pin, const float* phin, const float* u, float* out, int nx,
                               int ny, int nz, float D, float kap, cudaStream_t st) {
     const long long N = (long long)nx * ny * nz;
-    const dim3 grid((unsigned)((nx + WX - 1) / WX), (unsigned)((ny + WY - 1) / WY), (unsigned)((nz + WZ - 1) / WZ));
-    weno_stage_kernel<<<grid, WNT, 0, st>>>(pin, phin, u, u + N, u + 2 * N, out, nx, ny, nz, D, kap, stage);
+    const int zc = nz < 32 ? nz : 32;
+    const dim3 grid((unsigned)((nx + TX - 1) / TX), (unsigned)((ny + TY - 1) / TY), (unsigned)((nz + zc - 1) / zc));
+    weno_stage_kernel<<<grid, WNT, 0, st>>>(pin, phin, u, u + N, u + 2 * N, out, nx, ny, nz, zc, D, kap, stage);
     return cudaGetLastError();
 }
 
