@@ -71,7 +71,7 @@ __device__ __forceinline__ float face_flux(const float (&v)[6], float ul, float 
     return uf * weno5(up ? v[0] : v[5], up ? v[1] : v[4], up ? v[2] : v[3], up ? v[3] : v[2], up ? v[4] : v[1]);
 }
 
-__global__ void __launch_bounds__(WNT) weno_stage_kernel(const float* __restrict__ pin, const float* phin,
+__global__ void __launch_bounds__(WNT, 4) weno_stage_kernel(const float* __restrict__ pin, const float* phin,
                                                          const float* __restrict__ ux, const float* __restrict__ uy,
                                                          const float* __restrict__ uz, float* out, int nx, int ny,
                                                          int nz, int zc, float D, float kap, int stage) {
