@@ -223,11 +223,14 @@ int lb_tune(lb_ctx* ctx, int steps);
 
 /*
  * Checkpoint / restart.  lb_save copies the complete state of time t to host
- * memory: a header (sizes, storage, t), the device state (forcing amplitude
- * and target, last diagnostics, non-finite flag), the populations of time t
- * (the AA array, or the moment-only coefficients the next step reads) and
- * the D3Q7 populations of time t.  lb_load restores it into a context of the
- * same sizes and storage (initialised or not), after which lb_step continues
+ * memory: a header (sizes, storage, phase solver, t), the device state
+ * (forcing amplitude and target, last diagnostics, non-finite flag), the
+ * populations of time t (the AA array, or the moment-only coefficients the
+ * next step reads) and the D3Q7 populations of time t (with LB_PHASE_WENO5:
+ * the buffer holding phi).  lb_load restores it into a context of the same
+ * sizes, storage and phase solver (initialised or not; density contrasts and
+ * gravity are settings, not state: set them as on the saving context), after
+ * which lb_step continues
  * exactly as the saved run would have: the results are bitwise those of an
  * uninterrupted run.  Both calls are synchronous on the context's stream.
  *   buf    host memory of at least lb_state_bytes(ctx) bytes (pinned memory

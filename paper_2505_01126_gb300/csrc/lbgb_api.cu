@@ -700,8 +700,10 @@ int lb_get_tile(const lb_ctx* c, int* ty, int* zc) {
 // array, or the coefficient buffer the next step reads), the D3Q7 buffer of
 // time t.
 struct CkptHeader {
-    char magic[8];  // "LBGBCKP1"
+    char magic[8];  // "LBGBCKP2"
     int nx, ny, nz, storage;
+    int phase;      // LB_PHASE_LB or LB_PHASE_WENO5: how the phase buffer is laid out
+    int reserved;
     long long t;
     long long f_bytes, g_bytes;
 };
@@ -729,8 +731,10 @@ int lb_save(lb_ctx* c, void* buf, size_t bytes) {
     if (!c->initialized) return fail(LB_ESTATE, "lb_save before lb_init");
     if (bytes < lb_state_bytes(c)) return fail(LB_EINVAL, "lb_save: buffer of %zu bytes < %zu", bytes, lb_state_bytes(c));
     CkptHeader h;
-    memcpy(h.magic, "LBGBCKP1", 8);
+    memcpy(h.magic, "LBGBCKP2", 8);
     h.nx = c->nx; h.ny = c->ny; h.nz = c->nz; h.storage = c->storage;
+    h.phase = c->fd ? LB_PHASE_WENO5 : LB_PHASE_LB;
+    h.reserved = 0;
     h.t = c->t;
     h.f_bytes = (long long)ckpt_f_bytes(c);
     h.g_bytes = (long long)c->N * 7 * (long long)sizeof(float);
@@ -751,7 +755,10 @@ int lb_load(lb_ctx* c, const void* buf, size_t bytes) {
     if (bytes < sizeof(CkptHeader)) return fail(LB_EINVAL, "lb_load: %zu bytes hold no checkpoint", bytes);
     CkptHeader h;
     memcpy(&h, buf, sizeof(h));
-    if (memcmp(h.magic, "LBGBCKP1", 8) != 0) return fail(LB_EINVAL, "lb_load: not a checkpoint of this library");
+    if (memcmp(h.magic, "LBGBCKP2", 8) != 0) return fail(LB_EINVAL, "lb_load: not a checkpoint of this library");
+    if (h.phase != (c->fd ? LB_PHASE_WENO5 : LB_PHASE_LB))
+        return fail(LB_EINVAL, "lb_load: checkpoint of phase solver %d, context uses %d", h.phase,
+                    c->fd ? LB_PHASE_WENO5 : LB_PHASE_LB);
     if (h.nx != c->nx || h.ny != c->ny || h.nz != c->nz || h.storage != c->storage)
         return fail(LB_EINVAL, "lb_load: checkpoint of a %dx%dx%d box in storage %d, context is %dx%dx%d in %d", h.nx,
                     h.ny, h.nz, h.storage, c->nx, c->ny, c->nz, c->storage);

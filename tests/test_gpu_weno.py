@@ -164,6 +164,22 @@ def test_checkpoint_restart(lbgb, storage):
         assert np.array_equal(x, y)
 
 
+def test_checkpoint_of_the_other_phase_solver_is_rejected(lbgb):
+    shape = (8, 8, 12)
+    phi, u = smooth_fields(shape, 4)
+    a = lbgb.Box(12, 8, 8, 0.8, 0.1, 3.0, 0.01)
+    a.set_phase_solver("weno5")
+    a.init(phi, u)
+    a.step(3)
+    buf = a.save()
+    c = lbgb.Box(12, 8, 8, 0.8, 0.1, 3.0, 0.01)
+    with pytest.raises(lbgb.LBError) as e:
+        c.load(buf)
+    assert e.value.code == lbgb.LB_EINVAL
+    a.close()
+    c.close()
+
+
 def test_phase_solver_errors(lbgb):
     b = lbgb.Box(8, 8, 8, 1.0, 0.1, 3.0, 0.01)
     with pytest.raises(KeyError):
