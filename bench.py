@@ -67,6 +67,19 @@ PRESETS = {
 DROPLET_EDGE, DROPLET_TAU, DROPLET_DENSITY = 512, 0.515, (100.0, 1.0, 0.515, 0.515)
 
 
+# Single-phase forced HIT (Sec. 5.1): ABC forcing, no interface (phi = 0
+# everywhere, sigma = 0), 512^3, the seeded solenoidal start of the bubbly
+# workload.  The paper gives neither the amplitude nor k_f: A = 2e-6,
+# k_f = 2 pi / edge (one forcing period per box), tau = 0.51.
+ABC_EDGE, ABC_TAU, ABC_A, ABC_SEED = 512, 0.51, 2e-6, 7
+
+
+def abc_workload(edge: int):
+    if edge >= 384:
+        return inputs.bubbly_hit_device(edge, 0, 1.0, seed=ABC_SEED, tau=ABC_TAU, sigma=0.0, force_kind=2)
+    return inputs.bubbly_hit(edge, 0, 1.0, seed=ABC_SEED, tau=ABC_TAU, sigma=0.0, force_kind=2)
+
+
 def droplet_workload(edge: int):
     return inputs.static_droplet(edge=edge, R=edge / 4.0, tau=DROPLET_TAU)
 
@@ -186,6 +199,20 @@ def cpu_baseline_sample(density=None, phase="lb"):
 
     oracle.build()
     n = SAMPLE_EDGE
+    if density == "abc":
+        w = abc_workload(n)
+        o = oracle.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma, force_kind=oracle.FORCE_ABC, A_abc=ABC_A,
+                          kf=2 * math.pi / n)
+        o.set_phase_solver(phase)
+        o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
+        o.step(1)
+        t0 = time.perf_counter()
+        o.step(SAMPLE_STEPS)
+        dt = time.perf_counter() - t0
+        o.close()
+        return {"value": n ** 3 * SAMPLE_STEPS / dt / 1e6, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                "sample": f"{n}^3 box of the same recipe (single phase, ABC forcing k_f = 2 pi/{n}), "
+                          f"{SAMPLE_STEPS} FP64 oracle steps after 1 untimed step, {dt:.1f} s"}
     if density == "droplet":
         w = droplet_workload(n)
         o = oracle.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma)
@@ -337,9 +364,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--tile", type=int, nargs=2, metavar=("TY", "ZC"), help="fixed launch shape (skips tuning)")
-    ap.add_argument("--workload", default="hit", choices=["hit", "ensemble", "droplet"],
+    ap.add_argument("--workload", default="hit", choices=["hit", "ensemble", "droplet", "abc"],
                     help="hit: one 256^3 bubbly HIT box (default); ensemble: the 512-box droplet batch; "
-                         "droplet: the paper's two-component benchmark (512^3, one droplet, density ratio 100)")
+                         "droplet: the paper's two-component benchmark (512^3, one droplet, density ratio 100); "
+                         "abc: single-phase ABC-forced HIT (512^3)")
     ap.add_argument("--boxes", type=int, default=512)
     ap.add_argument("--preset", choices=sorted(PRESETS), help="bubbly HIT preset (overrides --edge)")
     ap.add_argument("--density", type=float, nargs=4, metavar=("RHO_L", "RHO_G", "TAU_L", "TAU_G"),
@@ -384,7 +412,12 @@ def main():
     from paper_2505_01126_gb300 import lbgb
 
     droplet = args.workload == "droplet"
-    if droplet:
+    abc = args.workload == "abc"
+    if abc:
+        args.edge = args.edge or ABC_EDGE
+        w, nb = abc_workload(args.edge), 0
+        torch.cuda.empty_cache()
+    elif droplet:
         args.edge = args.edge or DROPLET_EDGE
         args.density = DROPLET_DENSITY
         w, nb = droplet_workload(args.edge), 0
@@ -397,7 +430,10 @@ def main():
         w, nb = workload(args.edge)
     n = args.edge
     N = n ** 3
-    force = None if droplet else lbgb.Force(kind=lbgb.LB_FORCE_LINEAR, T_relax=w.T_relax)
+    if abc:
+        force = lbgb.Force(kind=lbgb.LB_FORCE_ABC, A=ABC_A, kf=2 * math.pi / n)
+    else:
+        force = None if droplet else lbgb.Force(kind=lbgb.LB_FORCE_LINEAR, T_relax=w.T_relax)
     stream = torch.cuda.Stream()
     box = lbgb.Box(n, n, n, w.tau, w.M, w.W, w.sigma, force=force, storage=args.storage, stream=stream)
     if args.phase != "lb":
@@ -491,13 +527,17 @@ def main():
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             try:
-                cpu = cpu_baseline_sample("droplet" if droplet else args.density, args.phase)
+                cpu = cpu_baseline_sample("droplet" if droplet else ("abc" if abc else args.density), args.phase)
             except Exception as ex:  # report, do not fail the benchmark line
                 cpu = {"error": str(ex)}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": (f"{n}^3 periodic box, one droplet R={n / 4:g} of the heavier phase, "
+                "config": {"workload": (f"{n}^3 periodic single-phase forced HIT (phi = 0, sigma = 0), ABC forcing "
+                                        f"A = {ABC_A:g}, k_f = 2 pi/{n}, tau = {w.tau}, seeded solenoidal start "
+                                        f"u_rms = 0.02" + (", phase field by WENO-5 finite differences (SSP-RK3)"
+                                                           if args.phase != "lb" else "")) if abc else
+                                       (f"{n}^3 periodic box, one droplet R={n / 4:g} of the heavier phase, "
                                         f"density ratio 100, nu=0.005 (tau={w.tau}) in both phases, W=3, "
                                         f"sigma=0.01, M=0.1, zero initial velocity, no forcing (the paper's "
                                         f"two-component benchmark case)") if droplet else
@@ -522,6 +562,11 @@ def main():
                                       "what": "two-component weak scaling, 512^3 per GPU: 105.48 GLUPS on 64 "
                                               "A100 (Leonardo) divided by 64; derived, not printed"}}
                    if droplet else {}),
+                **({"paper_context": {"value": 154940.0 / 64, "unit": "MLUPS per GPU",
+                                      "what": "single-component weak scaling, 512^3 per GPU: 154.94 GLUPS on 64 "
+                                              "A100 (Leonardo) divided by 64; derived, not printed; that code has "
+                                              "no phase field, this step still carries one (phi = 0)"}}
+                   if abc else {}),
                 "diagnostics": {"Phi": diag[0], "K": diag[1], "eps": diag[2], "umax": diag[3], "A": diag[4]}}
         print(json.dumps(line), flush=True)
     box.close()

@@ -290,3 +290,16 @@ def test_full_size_256_one_step_each_parity(lbgb, orc):
     e = max_err(got, want)
     assert max(e) <= TOL, e
     check_diagnostics(dg, do, n ** 3)
+
+
+def test_single_phase_abc_hit(lbgb, orc):
+    """Single-phase forced turbulence (phi = 0, sigma = 0, ABC forcing; the
+    second workload of the benchmark, here at 48^3): 50 steps against the
+    oracle, and phi stays exactly 0."""
+    w = inputs.bubbly_hit(48, 0, 1.0, seed=7, tau=0.51, sigma=0.0, force_kind=2)
+    force = dict(force_kind=2, A_abc=2e-6, kf=2 * math.pi / 48)
+    b, o, got, want = run_pair(lbgb, orc, (48, 48, 48), w.tau, w.M, w.W, w.sigma, w.phi, w.u, 50, force=force)
+    e = max_err(got, want)
+    assert max(e) <= TOL, e
+    assert not got[2].any()
+    check_diagnostics(b.diagnostics(), o.diagnostics(), 48 ** 3)
