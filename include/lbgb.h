@@ -210,7 +210,7 @@ int lb_get_tile(const lb_ctx* ctx, int* ty, int* zc);
 /*
  * lb_tune -- time tile heights ty in {4, 8} with z-chunks zc in {16, 32, 64,
  * 128} and the two chunkings whose block count best fills the last wave of
- * resident blocks, `steps` steps each (best of two windows), and keep the
+ * resident blocks, `steps` steps each (best of three windows), and keep the
  * fastest.  Before lb_init it times on the context's own
  * arrays, so the timed launches have the real box's block counts, and leaves
  * the context uninitialised; after lb_init it times on a scratch box with this

@@ -865,7 +865,7 @@ int lb_tune(lb_ctx* c, int steps) {
                 continue;
             }
             float shape_best = 1e30f;
-            for (int rep = 0; rep < 2; ++rep) {  // best of two windows
+            for (int rep = 0; rep < 3; ++rep) {  // best of three windows
                 cudaEventRecord(e0, c->stream);
                 int r2 = lb_step(s, 2 * steps);
                 cudaEventRecord(e1, c->stream);
