@@ -30,7 +30,7 @@ namespace {
 // plane z, each once, spread over the block (264 + 288 faces), and per thread
 // D lap - kappa div J and the flux through its column's upper z face (the
 // lower one carried from the plane below); barrier; the stage combination,
-// then the load of plane z + 4.
+// then the asynchronous copy of plane z + 4.
 constexpr int TX = 32, TY = 8, WH = 3;
 constexpr int PX = TX + 2 * WH, PY = TY + 2 * WH, NP = PX * PY;  // 38 x 14
 constexpr int QX = TX + 2, QY = TY + 2, NQ = QX * QY;            // 34 x 10
@@ -113,12 +113,15 @@ __global__ void __launch_bounds__(WNT, 4) weno_stage_kernel(const float* __restr
     const int own = wrap_mod(y0 + ly, ny) * nx + wrap_mod(x0 + lx, nx);
     const bool active = x0 + lx < nx && y0 + ly < ny;
 
+    // asynchronous copy of phi plane zp into its ring slot (one commit group
+    // per call; the caller waits before the barrier that publishes it)
     auto load_plane = [&](int zp) {
         const float* src = pin + (long long)wrap_mod(zp, nz) * plane;
         float* dst = &s_p[zp & (PR - 1)][0][0];
 #pragma unroll
         for (int k = 0; k < NPL; ++k)
-            if (p_dst[k] >= 0) dst[p_dst[k]] = __ldg(src + p_off[k]);
+            if (p_dst[k] >= 0) cp_async4(dst + p_dst[k], src + p_off[k]);
+        cp_async_commit();
     };
     // J of plane zp on the halo-1 ring, from phi planes zp - 1 .. zp + 1
     auto make_J = [&](int zp) {
@@ -168,6 +171,7 @@ __global__ void __launch_bounds__(WNT, 4) weno_stage_kernel(const float* __restr
 
     // prologue: phi planes z0 - 3 .. z0 + 3, J of z0 - 1 and z0, the z face below z0
     for (int zp = z0 - WH; zp <= z0 + WH; ++zp) load_plane(zp);
+    cp_async_wait<0>();
     __syncthreads();
     make_J(z0 - 1);
     make_J(z0);
@@ -176,7 +180,8 @@ __global__ void __launch_bounds__(WNT, 4) weno_stage_kernel(const float* __restr
 
     for (int z = z0; z < z1; ++z) {
         make_J(z + 1);
-        __syncthreads();  // J of z + 1 and phi of z + 3 are in place
+        cp_async_wait<0>();  // this thread's copies of plane z + 3 (issued last iteration) have landed
+        __syncthreads();     // J of z + 1 and phi of z + 3 are in place
 
         const long long zb = (long long)z * plane;  // z < nz
         const float(*P0)[PX] = s_p[z & (PR - 1)];
@@ -252,7 +257,7 @@ __global__ void __launch_bounds__(WNT, 4) weno_stage_kernel(const float* __restr
         }
         fzm = fzp;
         uzc = uzn;
-        load_plane(z + 4);
+        if (z + 1 < z1) load_plane(z + 4);  // the next plane's; no copy may be in flight when the march ends
     }
 }
 
