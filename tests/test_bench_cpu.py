@@ -1,0 +1,67 @@
+"""The host-side parts of bench.py: the reference arm's JSON line and the
+oracle samples behind cpu_baseline, for every workload option (run here on a
+16^3 sample so that the suite stays fast)."""
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """Rank 0 prints one JSON line with the contract's keys, the reference
+    marked, the cpu_baseline and e2e of the same run, and value > 0."""
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setattr(bench, "REF_EDGE", 16)
+
+    class Args:
+        steps, warmup, gpus = 2, 1, 1
+
+    assert bench.run_reference(Args()) == 0
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "MLUPS"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["dtype"] == "f64"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+@pytest.mark.parametrize("density,phase", [(None, "lb"), ((1.0, 0.1, 0.51, 0.55), "lb"), ("droplet", "lb"),
+                                           ("abc", "lb"), (None, "weno5")])
+def test_cpu_baseline_samples(monkeypatch, density, phase):
+    """Every workload option gives a positive oracle rate, the thread count it
+    used, and a sample description naming the options."""
+    monkeypatch.setattr(bench, "SAMPLE_EDGE", 16)
+    monkeypatch.setattr(bench, "SAMPLE_STEPS", 2)
+    c = bench.cpu_baseline_sample(density, phase)
+    assert c["kind"] == "oracle" and c["unit"] == "MLUPS" and c["value"] > 0 and c["cores"] >= 1
+    assert "16^3" in c["sample"]
+    if density == "abc":
+        assert "ABC" in c["sample"]
+    elif density == "droplet":
+        assert "density ratio 100" in c["sample"]
+    elif density:
+        assert "density contrasts" in c["sample"]
+    if phase == "weno5":
+        assert "WENO-5" in c["sample"]
+
+
+def test_gravity_argument_takes_three_components():
+    """--gravity takes one comma-separated triple (a leading minus in
+    scientific notation would read as an option otherwise)."""
+    import subprocess
+
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gravity", "0,0"],
+                       capture_output=True, text=True)
+    assert r.returncode != 0 and "three comma-separated" in r.stderr
