@@ -216,3 +216,39 @@ def test_set_phase_solver_rejects_unknown_names(orc):
     with pytest.raises(KeyError):
         o.set_phase_solver("spectral")
     o.close()
+
+
+def test_fd_with_density_ratio_one_is_the_fd_step(orc):
+    """The finite-difference phase field with the Sec. 2.3 contrasts at ratio 1
+    and one tau is the finite-difference step alone, bit for bit (the added
+    terms are exact zeros), with linear forcing and bubbles."""
+    w = inputs.bubbly_hit(16, 2, 3.0, seed=11, tau=0.6)
+    runs = []
+    for vd in (False, True):
+        o = orc.Oracle(16, 16, 16, w.tau, w.M, w.W, w.sigma, force_kind=orc.FORCE_LINEAR, T_relax=50.0)
+        o.set_phase_solver("weno5")
+        if vd:
+            o.set_density(1.0, 1.0, w.tau, w.tau)
+        o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
+        o.step(8)
+        runs.append(o.moments())
+        o.close()
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
+
+
+def test_fd_phase_does_not_depend_on_the_d3q7_relaxation(orc):
+    """The finite-difference phase field uses D = M and kappa = 4M/W only: the
+    D3Q7 populations play no part, so phi after a step with u = 0 is the
+    explicit RK3 update of the initial phi by the diffusion and sharpening
+    terms, the same for any tau of the hydrodynamics."""
+    phi = inputs.droplet(12, 12, 12, 3.5, 3.0)
+    res = []
+    for tau in (0.6, 1.4):
+        o = orc.Oracle(12, 12, 12, tau, 0.1, 3.0, 0.0)
+        o.set_phase_solver("weno5")
+        o.init(phi.astype(np.float64), np.zeros((3, 12, 12, 12)))
+        o.step(1)
+        res.append(o.moments()[2])
+        o.close()
+    assert np.array_equal(res[0], res[1])
