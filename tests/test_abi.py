@@ -30,6 +30,23 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_header_is_plain_c99():
+    """A C99 program (no C++) can include the header and name every declared
+    function: the boundary needs no C++ or torch types (gcc, syntax only, source
+    on stdin)."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    body = "\n".join(f"    (void)&{n};" for n in declared_functions())
+    src = f'#include "lbgb.h"\nint main(void) {{\n{body}\n    return 0;\n}}\n'
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", "c",
+                        "-I", os.path.join(ROOT, "include"), "-"], input=src, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_library_exports_every_declared_symbol(lbgb):
     lib = lbgb.lib()
     for name in declared_functions():
