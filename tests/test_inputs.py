@@ -5,6 +5,7 @@ non-overlapping bubbles, tanh profiles, reproducibility)."""
 import math
 
 import numpy as np
+import pytest
 
 from paper_2505_01126_gb300 import inputs
 
@@ -66,3 +67,16 @@ def test_droplet_is_mirror_symmetric_and_generators_are_reproducible():
     s1 = inputs.ensemble_specs(16, seed=4)
     s2 = inputs.ensemble_specs(16, seed=4)
     assert s1 == s2
+
+
+def test_device_generator_reproduces_the_host_one():
+    """The torch path used for the large boxes (run here on the CPU) draws the
+    same bubbles and modes and gives the same FP32 fields as the numpy one, to
+    one FP32 rounding."""
+    pytest.importorskip("torch")
+    a = inputs.bubbly_hit(32, 3, 5.0, seed=13)
+    b = inputs.bubbly_hit_device(32, 3, 5.0, seed=13, device="cpu")
+    pb, ub = b.phi.numpy(), b.u.numpy()
+    assert pb.dtype == np.float32 and ub.dtype == np.float32
+    assert np.abs(pb.astype(np.float64) - a.phi).max() <= 1e-7
+    assert np.abs(ub.astype(np.float64) - a.u).max() <= 1e-8
