@@ -192,90 +192,92 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline_sample(density=None, phase="lb"):
-    """Time the oracle (as it stands) on a bounded sample of the workload (with the
-    density contrasts and flipped phase field when `density` is given)."""
+def oracle_sample(n: int, kind: str = "hit", density=None, gravity=None, phase: str = "lb"):
+    """The oracle (as it stands) initialised on an n^3 sample of the benchmark's
+    workload with its options, as the GPU arm builds it: the bubbly HIT recipe
+    (its bubbles flipped to gas at phi = 0 when density contrasts are given),
+    the two-component droplet, or the single-phase ABC HIT.  Returns the oracle
+    and a description of the sample."""
     import oracle
 
     oracle.build()
-    n = SAMPLE_EDGE
-    if density == "abc":
+    if kind == "abc":
         w = abc_workload(n)
         o = oracle.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma, force_kind=oracle.FORCE_ABC, A_abc=ABC_A,
                           kf=2 * math.pi / n)
-        o.set_phase_solver(phase)
-        o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
-        o.step(1)
-        t0 = time.perf_counter()
-        o.step(SAMPLE_STEPS)
-        dt = time.perf_counter() - t0
-        o.close()
-        return {"value": n ** 3 * SAMPLE_STEPS / dt / 1e6, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-                "sample": f"{n}^3 box of the same recipe (single phase, ABC forcing k_f = 2 pi/{n}), "
-                          f"{SAMPLE_STEPS} FP64 oracle steps after 1 untimed step, {dt:.1f} s"}
-    if density == "droplet":
+        desc = f"single phase, ABC forcing k_f = 2 pi/{n}"
+    elif kind == "droplet":
         w = droplet_workload(n)
         o = oracle.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma)
-        o.set_phase_solver(phase)
-        o.set_density(*DROPLET_DENSITY)
-        o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
-        o.step(1)
-        t0 = time.perf_counter()
-        o.step(SAMPLE_STEPS)
-        dt = time.perf_counter() - t0
-        o.close()
-        return {"value": n ** 3 * SAMPLE_STEPS / dt / 1e6, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-                "sample": f"{n}^3 box of the same recipe (droplet R={n // 4}, density ratio 100, tau 0.515), "
-                          f"{SAMPLE_STEPS} FP64 oracle steps after 1 untimed step, {dt:.1f} s"}
-    w, _ = workload(SAMPLE_EDGE)
-    o = oracle.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma, force_kind=oracle.FORCE_LINEAR, T_relax=w.T_relax)
-    o.set_phase_solver(phase)
+        density = DROPLET_DENSITY
+        desc = f"droplet R={n / 4:g}, density ratio 100, tau 0.515"
+    else:
+        w, nb = workload(n)
+        o = oracle.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma, force_kind=oracle.FORCE_LINEAR, T_relax=w.T_relax)
+        desc = f"{nb} bubble{'s' if nb != 1 else ''} R=10, u_rms 0.02, tau 0.51, linear forcing"
     phi = w.phi.astype(np.float64)
+    o.set_phase_solver(phase)
     if density:
         o.set_density(*density)
-        phi = (1.0 - w.phi).astype(np.float64)
+        if kind != "droplet":
+            phi = 1.0 - phi  # the gas at phi = 0, as the GPU arm does
+        desc += ", density contrasts"
+        if gravity:
+            o.set_gravity(gravity, density[1] + (density[0] - density[1]) * float(phi.mean()))
+            desc += ", buoyancy"
+    if phase != "lb":
+        desc += ", WENO-5 phase field"
     o.init(phi, w.u.astype(np.float64))
+    return o, desc
+
+
+def cpu_baseline_sample(kind: str = "hit", density=None, gravity=None, phase: str = "lb"):
+    """Time the oracle (as it stands) on a bounded sample of the workload:
+    SAMPLE_STEPS steps of a SAMPLE_EDGE^3 box after one untimed step."""
+    import oracle
+
+    n = SAMPLE_EDGE
+    o, desc = oracle_sample(n, kind, density, gravity, phase)
     o.step(1)  # first touch of the arrays
     t0 = time.perf_counter()
     o.step(SAMPLE_STEPS)
     dt = time.perf_counter() - t0
     o.close()
-    value = n ** 3 * SAMPLE_STEPS / dt / 1e6
-    return {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{n}^3 box of the same recipe ({SAMPLE_BUBBLES} bubbles R=10, u_rms 0.02, tau 0.51, "
-                      f"linear forcing{', density contrasts' if density else ''}"
-                      f"{', WENO-5 phase field' if phase != 'lb' else ''}), "
-                      f"{SAMPLE_STEPS} FP64 oracle steps after 1 untimed step, "
-                      f"{dt:.1f} s"}
+    return {"value": n ** 3 * SAMPLE_STEPS / dt / 1e6, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{n}^3 box of the same recipe ({desc}), {SAMPLE_STEPS} FP64 oracle steps after 1 untimed "
+                      f"step, {dt:.1f} s"}
 
 
 def run_reference(args):
     """Reference arm: the FP64 oracle on the host cores, each step one oracle step of
-    the REF_EDGE^3 (64^3) sample of the workload."""
+    the REF_EDGE^3 (64^3) sample of the workload and options the GPU arm runs (the
+    ensemble's arm times the bubbly sample)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
 
-    oracle.build()
-    w, nb = workload(REF_EDGE)
+    kind = getattr(args, "workload", "hit")
+    kind = kind if kind in ("droplet", "abc") else "hit"
     n = REF_EDGE
-    o = oracle.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma, force_kind=oracle.FORCE_LINEAR, T_relax=w.T_relax)
-    o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
+    o, desc = oracle_sample(n, kind, getattr(args, "density", None), getattr(args, "gravity", None),
+                            getattr(args, "phase", "lb"))
     o.step(args.warmup)
     t0 = time.perf_counter()
     o.step(args.steps)
     dt = time.perf_counter() - t0
+    o.close()
     value = n ** 3 * args.steps / dt / 1e6
-    sample = (f"{n}^3 box of the same recipe ({nb} bubble R=10, u_rms 0.02, tau 0.51, linear forcing), "
-              f"one FP64 oracle step per bench step")
+    sample = f"{n}^3 box of the same recipe ({desc}), one FP64 oracle step per bench step"
+    full = {"hit": "the 256^3 periodic bubbly forced HIT workload (bubbles R=10, W=3, sigma=0.01, tau=0.51, M=0.1, "
+                   "u_rms=0.02, linear forcing)",
+            "droplet": "the 512^3 two-component droplet case (density ratio 100, nu 0.005)",
+            "abc": "the 512^3 single-phase ABC-forced HIT"}[kind]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"{n}^3 sample of the 256^3 periodic bubbly forced HIT workload "
-                                   f"(bubbles R=10, W=3, sigma=0.01, tau=0.51, M=0.1, u_rms=0.02, linear forcing)",
-                       "edge": n, "bubbles": nb, "storage": "f64"},
+            "config": {"workload": f"{n}^3 sample of {full}: {desc}", "edge": n, "storage": "f64"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -527,7 +529,8 @@ def main():
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             try:
-                cpu = cpu_baseline_sample("droplet" if droplet else ("abc" if abc else args.density), args.phase)
+                cpu = cpu_baseline_sample("droplet" if droplet else ("abc" if abc else "hit"), args.density,
+                                          args.gravity, args.phase)
             except Exception as ex:  # report, do not fail the benchmark line
                 cpu = {"error": str(ex)}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

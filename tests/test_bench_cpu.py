@@ -37,24 +37,46 @@ def test_reference_arm_line(monkeypatch, capsys):
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
 
 
-@pytest.mark.parametrize("density,phase", [(None, "lb"), ((1.0, 0.1, 0.51, 0.55), "lb"), ("droplet", "lb"),
-                                           ("abc", "lb"), (None, "weno5")])
-def test_cpu_baseline_samples(monkeypatch, density, phase):
+@pytest.mark.parametrize("kind,density,gravity,phase", [
+    ("hit", None, None, "lb"), ("hit", (1.0, 0.1, 0.51, 0.55), None, "lb"),
+    ("hit", (1.0, 0.1, 0.51, 0.55), (0.0, 0.0, -1e-5), "lb"), ("droplet", None, None, "lb"),
+    ("abc", None, None, "lb"), ("hit", None, None, "weno5"), ("droplet", None, None, "weno5")])
+def test_cpu_baseline_samples(monkeypatch, kind, density, gravity, phase):
     """Every workload option gives a positive oracle rate, the thread count it
     used, and a sample description naming the options."""
     monkeypatch.setattr(bench, "SAMPLE_EDGE", 16)
     monkeypatch.setattr(bench, "SAMPLE_STEPS", 2)
-    c = bench.cpu_baseline_sample(density, phase)
+    c = bench.cpu_baseline_sample(kind, density, gravity, phase)
     assert c["kind"] == "oracle" and c["unit"] == "MLUPS" and c["value"] > 0 and c["cores"] >= 1
     assert "16^3" in c["sample"]
-    if density == "abc":
+    if kind == "abc":
         assert "ABC" in c["sample"]
-    elif density == "droplet":
+    elif kind == "droplet":
         assert "density ratio 100" in c["sample"]
-    elif density:
+    if density:
         assert "density contrasts" in c["sample"]
+    if gravity:
+        assert "buoyancy" in c["sample"]
     if phase == "weno5":
         assert "WENO-5" in c["sample"]
+
+
+@pytest.mark.parametrize("workload", ["hit", "droplet", "abc", "ensemble"])
+def test_reference_arm_follows_the_workload_option(monkeypatch, capsys, workload):
+    """The reference arm times the oracle on a sample of the workload the GPU
+    arm runs (the ensemble's on the bubbly sample)."""
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setattr(bench, "REF_EDGE", 16)
+
+    class Args:
+        steps, warmup, gpus, density, gravity, phase = 1, 1, 1, None, None, "lb"
+
+    Args.workload = workload
+    assert bench.run_reference(Args()) == 0
+    d = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    want = {"hit": "bubbly", "ensemble": "bubbly", "droplet": "droplet", "abc": "ABC"}[workload]
+    assert want in d["config"]["workload"]
 
 
 def test_gravity_argument_takes_three_components():
