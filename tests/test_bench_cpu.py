@@ -87,3 +87,19 @@ def test_gravity_argument_takes_three_components():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gravity", "0,0"],
                        capture_output=True, text=True)
     assert r.returncode != 0 and "three comma-separated" in r.stderr
+
+
+def test_reference_arm_from_the_command_line():
+    """`python bench.py --impl reference` (the driver's command) prints exactly
+    one JSON line with the reference marked, on the default 64^3 sample."""
+    import subprocess
+
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "1"], capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["warmup"] == 3 and d["steps"] == 1 and d["value"] > 0
+    assert "64^3 sample" in d["config"]["workload"]
