@@ -135,8 +135,8 @@ int lb_init(lb_ctx* ctx, const float* phi, const float* u);
  * overshoots phi slightly above 1 but not below 0, and an overshoot into a light
  * phase at phi = 1 drives rho(phi) towards 0 (such runs blow up within tens of
  * steps at ratio 10).  Every storage supports it; it stays on for the life
- * of the context (a checkpoint holds the state, not these parameters: set them
- * again on the context that loads it).
+ * of the context (a checkpoint records these parameters, and lb_load accepts
+ * it only into a context with the same ones: set them before loading).
  * Errors: LB_EINVAL unless rho_l, rho_g > 0 and tau_l, tau_g > 1/2 (finite).
  */
 int lb_set_density(lb_ctx* ctx, double rho_l, double rho_g, double tau_l, double tau_g);
@@ -208,10 +208,11 @@ int lb_set_tile(lb_ctx* ctx, int ty, int zc);
 int lb_get_tile(const lb_ctx* ctx, int* ty, int* zc);
 
 /*
- * lb_tune -- time tile heights ty in {4, 8} with z-chunks zc in {16, 32, 64,
+ * lb_tune -- time tile heights ty in {8, 4} with z-chunks zc in {16, 32, 64,
  * 128} and the two chunkings whose block count best fills the last wave of
- * resident blocks, `steps` steps each (best of three windows), and keep the
- * fastest.  Before lb_init it times on the context's own
+ * resident blocks, each as the median of five windows of 2*steps steps, and
+ * keep the first shape in that order whose median is within 1% of the
+ * fastest (so shapes that time alike do not trade places on noise).  Before lb_init it times on the context's own
  * arrays, so the timed launches have the real box's block counts, and leaves
  * the context uninitialised; after lb_init it times on a scratch box with this
  * box's nx, ny, storage and min(nz, 128) planes, allocated and freed here,
@@ -223,19 +224,21 @@ int lb_tune(lb_ctx* ctx, int steps);
 
 /*
  * Checkpoint / restart.  lb_save copies the complete state of time t to host
- * memory: a header (sizes, storage, phase solver, t), the device state
+ * memory: a header (sizes, storage, phase solver, t, and the density,
+ * viscosity and gravity settings of lb_set_density / lb_set_gravity), the device state
  * (forcing amplitude and target, last diagnostics, non-finite flag), the
  * populations of time t (the AA array, or the moment-only coefficients the
  * next step reads) and the D3Q7 populations of time t (with LB_PHASE_WENO5:
  * the buffer holding phi).  lb_load restores it into a context of the same
- * sizes, storage and phase solver (initialised or not; density contrasts and
- * gravity are settings, not state: set them as on the saving context), after
- * which lb_step continues
+ * sizes, storage, phase solver and density, viscosity and gravity settings
+ * (initialised or not; call lb_set_density and lb_set_gravity as on the saving
+ * context before lb_load), after which lb_step continues
  * exactly as the saved run would have: the results are bitwise those of an
  * uninterrupted run.  Both calls are synchronous on the context's stream.
  *   buf    host memory of at least lb_state_bytes(ctx) bytes (pinned memory
  *          makes the copies faster); caller-owned
- * Errors: LB_EINVAL (NULL, short buffer, foreign or mismatched checkpoint),
+ * Errors: LB_EINVAL (NULL, short buffer, foreign checkpoint, or one whose sizes,
+ * storage, phase solver or density/gravity settings differ from the context's),
  * LB_ESTATE (lb_save before lb_init), LB_ECUDA.
  */
 size_t lb_state_bytes(const lb_ctx* ctx);
@@ -359,14 +362,15 @@ void lb_batch_destroy(lb_batch* batch);            /* NULL is ignored */
  * must not call cudaMalloc: a framework whose caching allocator owns the device
  * memory budget, a latency-critical path where an allocation may synchronise
  * the device, or a plugin that is handed its buffers.
- *   phi    N floats, device memory, read only
- *   u      3N floats (ux | uy | uz planes), device memory, read only
+ *   phi    N floats, device memory of the current device (or managed), read only
+ *   u      3N floats (ux | uy | uz planes), as phi
  *   stream cudaStream_t for the work, or NULL for the legacy default stream
  *   out    5 doubles: {Phi = sum phi, K = 1/2 sum |u|^2, 0, max|u|, 0}, the
  *          numbers lb_diagnostics reports right after lb_init with these
  *          fields.  Host memory: the call waits for the result.  Device
- *          memory: the result is written in stream order and the call
- *          returns at once.
+ *          memory (of the current device): the result is written in stream
+ *          order and the call returns at once, with no non-finite report (a
+ *          NaN or Inf in the fields shows as a non-finite Phi or K).
  * Scratch is a file-scope __device__ array of LB_STATIC_MAX_BLOCKS * 5 doubles
  * (1.25 MiB), which every device that loads the library holds until the process
  * exits.  A box needs ceil(nx/32)*ceil(ny/8)*ceil(nz/32) records; larger boxes
@@ -374,8 +378,9 @@ void lb_batch_destroy(lb_batch* batch);            /* NULL is ignored */
  * device looks up the array's device address, so make that first call before
  * any stream capture.  All calls on a device share the array: calls that
  * overlap on the GPU (e.g. on two streams) race.
- * Errors: LB_EINVAL (NULL, sizes, host phi/u), LB_ECUDA, LB_ENONFINITE (a NaN or
- * Inf in phi or u; host out only, out still filled).
+ * Errors: LB_EINVAL (NULL, sizes, phi/u/out in host memory or in another
+ * device's memory), LB_ECUDA, LB_ENONFINITE (a NaN or Inf in phi or u; host out
+ * only, out still filled).
  */
 #define LB_STATIC_MAX_BLOCKS 32768
 int lb_field_stats_static(const float* phi, const float* u, int nx, int ny, int nz, void* stream,

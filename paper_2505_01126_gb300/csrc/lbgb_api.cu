@@ -700,12 +700,15 @@ int lb_get_tile(const lb_ctx* c, int* ty, int* zc) {
 // array, or the coefficient buffer the next step reads), the D3Q7 buffer of
 // time t.
 struct CkptHeader {
-    char magic[8];  // "LBGBCKP2"
+    char magic[8];  // "LBGBCKP3"
     int nx, ny, nz, storage;
     int phase;      // LB_PHASE_LB or LB_PHASE_WENO5: how the phase buffer is laid out
-    int reserved;
+    int vd;         // density contrasts on (1) or off (0)
     long long t;
     long long f_bytes, g_bytes;
+    // the settings the saved run stepped with: density contrasts (rho_l, rho_g,
+    // tau_l, tau_g) and buoyancy (g, rho_ref); zero when contrasts are off
+    double rho_l, rho_g, tau_l, tau_g, gb[3], rho_ref;
 };
 
 static size_t ckpt_f_bytes(const lb_ctx* c) {
@@ -731,10 +734,16 @@ int lb_save(lb_ctx* c, void* buf, size_t bytes) {
     if (!c->initialized) return fail(LB_ESTATE, "lb_save before lb_init");
     if (bytes < lb_state_bytes(c)) return fail(LB_EINVAL, "lb_save: buffer of %zu bytes < %zu", bytes, lb_state_bytes(c));
     CkptHeader h;
-    memcpy(h.magic, "LBGBCKP2", 8);
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, "LBGBCKP3", 8);
     h.nx = c->nx; h.ny = c->ny; h.nz = c->nz; h.storage = c->storage;
     h.phase = c->fd ? LB_PHASE_WENO5 : LB_PHASE_LB;
-    h.reserved = 0;
+    h.vd = c->vd ? 1 : 0;
+    if (c->vd) {
+        h.rho_l = c->rho_l; h.rho_g = c->rho_g; h.tau_l = c->tau_l; h.tau_g = c->tau_g;
+        for (int k = 0; k < 3; ++k) h.gb[k] = c->gb[k];
+        h.rho_ref = c->rho_ref;
+    }
     h.t = c->t;
     h.f_bytes = (long long)ckpt_f_bytes(c);
     h.g_bytes = (long long)c->N * 7 * (long long)sizeof(float);
@@ -755,7 +764,18 @@ int lb_load(lb_ctx* c, const void* buf, size_t bytes) {
     if (bytes < sizeof(CkptHeader)) return fail(LB_EINVAL, "lb_load: %zu bytes hold no checkpoint", bytes);
     CkptHeader h;
     memcpy(&h, buf, sizeof(h));
-    if (memcmp(h.magic, "LBGBCKP2", 8) != 0) return fail(LB_EINVAL, "lb_load: not a checkpoint of this library");
+    if (memcmp(h.magic, "LBGBCKP3", 8) != 0) return fail(LB_EINVAL, "lb_load: not a checkpoint of this library");
+    // the saved run's physics must be the context's: a state stepped with density
+    // contrasts continued without them (or with other ones) would change the flow
+    if (h.vd != (c->vd ? 1 : 0))
+        return fail(LB_EINVAL, "lb_load: checkpoint %s density contrasts, the context %s", h.vd ? "with" : "without",
+                    c->vd ? "has them" : "has none (call lb_set_density first)");
+    if (c->vd && (h.rho_l != c->rho_l || h.rho_g != c->rho_g || h.tau_l != c->tau_l || h.tau_g != c->tau_g ||
+                  h.gb[0] != c->gb[0] || h.gb[1] != c->gb[1] || h.gb[2] != c->gb[2] || h.rho_ref != c->rho_ref))
+        return fail(LB_EINVAL,
+                    "lb_load: checkpoint stepped with rho %g/%g, tau %g/%g, g (%g, %g, %g), rho_ref %g; the context "
+                    "has other density, viscosity or gravity settings",
+                    h.rho_l, h.rho_g, h.tau_l, h.tau_g, h.gb[0], h.gb[1], h.gb[2], h.rho_ref);
     if (h.phase != (c->fd ? LB_PHASE_WENO5 : LB_PHASE_LB))
         return fail(LB_EINVAL, "lb_load: checkpoint of phase solver %d, context uses %d", h.phase,
                     c->fd ? LB_PHASE_WENO5 : LB_PHASE_LB);
@@ -852,9 +872,16 @@ int lb_tune(lb_ctx* c, int steps) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int tys[2] = {4, 8};
-    float best = 1e30f;
-    int bty = c->ty, bzc = c->zc;
+    // Candidates in a fixed order (tile height 8 first); each is timed as the
+    // median of TUNE_WINDOWS windows.  The pick is the first candidate whose
+    // median is within TUNE_TIE of the fastest, so shapes that time alike do
+    // not trade places from run to run on noise.
+    constexpr int TUNE_WINDOWS = 5;
+    constexpr float TUNE_TIE = 0.01f;
+    const int tys[2] = {8, 4};
+    int cand_ty[12], cand_zc[12];
+    float cand_ms[12];
+    int ncand = 0;
     for (int a = 0; a < 2 && rc == LB_OK; ++a) {
         int zcs[6];
         const int nzc = tune_chunks(s, tys[a], zcs);
@@ -864,25 +891,43 @@ int lb_tune(lb_ctx* c, int steps) {
                 cudaGetLastError();
                 continue;
             }
-            float shape_best = 1e30f;
-            for (int rep = 0; rep < 3; ++rep) {  // best of three windows
+            float win[TUNE_WINDOWS];
+            int nwin = 0;
+            for (int rep = 0; rep < TUNE_WINDOWS; ++rep) {
                 cudaEventRecord(e0, c->stream);
                 int r2 = lb_step(s, 2 * steps);
                 cudaEventRecord(e1, c->stream);
                 cudaEventSynchronize(e1);
                 float ms = 0;
                 cudaEventElapsedTime(&ms, e0, e1);
-                if (r2 == LB_OK && ms < shape_best) shape_best = ms;
+                if (r2 == LB_OK) win[nwin++] = ms;
             }
-            if (shape_best < best) {
-                best = shape_best;
-                bty = tys[a];
-                bzc = zcs[b];
-            }
+            if (nwin == 0) continue;
+            for (int i = 1; i < nwin; ++i)  // insertion sort of the windows
+                for (int j = i; j > 0 && win[j] < win[j - 1]; --j) {
+                    const float t = win[j];
+                    win[j] = win[j - 1];
+                    win[j - 1] = t;
+                }
+            cand_ty[ncand] = tys[a];
+            cand_zc[ncand] = zcs[b];
+            cand_ms[ncand] = win[nwin / 2];
+            ++ncand;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    int bty = c->ty, bzc = c->zc;
+    if (ncand > 0) {
+        float best = cand_ms[0];
+        for (int k = 1; k < ncand; ++k) best = cand_ms[k] < best ? cand_ms[k] : best;
+        for (int k = 0; k < ncand; ++k)
+            if (cand_ms[k] <= best * (1.f + TUNE_TIE)) {
+                bty = cand_ty[k];
+                bzc = cand_zc[k];
+                break;
+            }
+    }
     if (in_place) {
         LB_CUDA(cudaStreamSynchronize(c->stream));
         c->initialized = false;  // the timed steps left no usable state

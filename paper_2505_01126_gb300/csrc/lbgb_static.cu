@@ -130,7 +130,20 @@ int scratch_for_current_device(DeviceScratch** out) {
     return LB_OK;
 }
 
-bool on_device(const void* p) {
+// Device memory of the current device `dev`, or managed memory.  Device
+// memory of another GPU is refused: the kernels run on the current device, and
+// reading a peer's memory without peer access enabled faults.
+bool on_device(const void* p, int dev) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+bool is_device_memory(const void* p) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
@@ -153,7 +166,13 @@ extern "C" int lb_field_stats_static(const float* phi, const float* u, int nx, i
                     "box %d x %d x %d needs %lld partial records, more than the %d this entry point holds "
                     "(cubic boxes up to 640^3)",
                     nx, ny, nz, nblk, LB_STATIC_MAX_BLOCKS);
-    if (!on_device(phi) || !on_device(u)) return fail(LB_EINVAL, "phi and u must be device memory");
+    int dev = -1;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 != cudaSuccess) return fail(LB_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e0));
+    if (!on_device(phi, dev) || !on_device(u, dev))
+        return fail(LB_EINVAL, "phi and u must be device memory of the current device (%d)", dev);
+    if (is_device_memory(out) && !on_device(out, dev))
+        return fail(LB_EINVAL, "a device out must be memory of the current device (%d)", dev);
     DeviceScratch* d = nullptr;
     int rc = scratch_for_current_device(&d);
     if (rc != LB_OK) return rc;
@@ -161,7 +180,7 @@ extern "C" int lb_field_stats_static(const float* phi, const float* u, int nx, i
     field_stats_kernel<<<grid, ST_NT, 0, s>>>(phi, u, nx, ny, nz, d->partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(LB_ECUDA, "field_stats_kernel launch: %s", cudaGetErrorString(e));
-    const bool dev_out = on_device(out);
+    const bool dev_out = is_device_memory(out);
     field_stats_finalize<<<1, 256, 0, s>>>(d->partials, (int)nblk, d->result);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(LB_ECUDA, "field_stats_finalize launch: %s", cudaGetErrorString(e));

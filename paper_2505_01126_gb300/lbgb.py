@@ -145,12 +145,18 @@ def field_stats_static(phi, u, stream=None) -> np.ndarray:
     """FP64 {Phi, K, 0, max|u|, 0} of device fields phi (nz, ny, nx) and u (3, nz, ny, nx)
     through lb_field_stats_static, which allocates no device memory (for callers
     that must not call cudaMalloc); the result is returned in host memory."""
+    import torch
+
     nz, ny, nx = (int(v) for v in phi.shape)
     p, _a = _ptr(phi, nx * ny * nz)
     q, _b = _ptr(u, 3 * nx * ny * nz)
     handle = getattr(stream, "cuda_stream", stream)
     out = (ctypes.c_double * 5)()
-    _check(_lib.lb_field_stats_static(p, q, nx, ny, nz, ctypes.c_void_p(int(handle) if handle else 0), out))
+    with torch.cuda.device(phi.device):  # the library runs on the current device
+        rc = _lib.lb_field_stats_static(p, q, nx, ny, nz, ctypes.c_void_p(int(handle) if handle else 0), out)
+    if rc == LB_ENONFINITE:
+        raise LBError(rc, _lib.lb_last_error().decode())
+    _check(rc)
     return np.array(list(out))
 
 

@@ -5,6 +5,7 @@ import json
 import os
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -103,3 +104,30 @@ def test_reference_arm_from_the_command_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["warmup"] == 3 and d["steps"] == 1 and d["value"] > 0
     assert "64^3 sample" in d["config"]["workload"]
+
+
+def test_oracle_references_of_the_error_cases(monkeypatch):
+    """The oracle runs behind the default line's errors and CPU baseline: K and
+    Phi at every sample, the final fields, a finite droplet pressure jump of
+    the right sign (the droplet is at higher pressure), and the stepping time
+    counted over both cases."""
+    monkeypatch.setattr(bench, "SURR_EDGE", 16)
+    monkeypatch.setattr(bench, "SURR_STEPS", 4)
+    monkeypatch.setattr(bench, "SURR_EVERY", 2)
+    monkeypatch.setattr(bench, "LAP_SAMPLES", [1, 2])
+    ref = bench.oracle_references("hit512")
+    assert len(ref["K"]) == 2 and len(ref["Phi"]) == 2 and all(k > 0 for k in ref["K"])
+    assert len(ref["final"]) == 3 and ref["final"][1].shape == (3, 16, 16, 16)
+    assert ref["dp"] > 0 and ref["time_s"] > 0 and ref["cores"] >= 1
+    assert ref["updates"] == 16 ** 3 * 4 + bench.LAP_EDGE ** 3 * 2
+
+
+def test_laplace_jump_of_a_uniform_pressure_is_zero():
+    rho = np.ones((32, 32, 32))
+    assert bench.laplace_dp(rho, 32, 8.0, 3.0) == 0.0
+    rho[:] = 1.0
+    z, y, x = np.meshgrid(*[np.arange(32)] * 3, indexing="ij")
+    c = 15.5
+    inside = np.sqrt((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2) < 2.0
+    rho[inside] = 1.03
+    assert abs(bench.laplace_dp(rho, 32, 8.0, 3.0) - 0.01) < 1e-12

@@ -242,6 +242,39 @@ def test_checkpoint_restart_with_contrast(lbgb, storage):
         assert np.array_equal(x, y)
 
 
+def test_checkpoint_with_other_contrast_settings_is_rejected(lbgb):
+    """A checkpoint records the density, viscosity and gravity settings it was
+    stepped with; a context without them, or with other values, refuses it."""
+    shape = (8, 8, 12)
+    phi, u = smooth_fields(shape, 4)
+    a = lbgb.Box(12, 8, 8, 0.8, 0.1, 3.0, 0.01)
+    a.set_density(10.0, 1.0, 0.6, 0.8)
+    a.set_gravity((0.0, 0.0, -1e-5), 2.0)
+    a.init(phi, u)
+    a.step(3)
+    buf = a.save()
+    plain = lbgb.Box(12, 8, 8, 0.8, 0.1, 3.0, 0.01)
+    other = lbgb.Box(12, 8, 8, 0.8, 0.1, 3.0, 0.01)
+    other.set_density(10.0, 1.0, 0.6, 0.8)  # no gravity
+    for c in (plain, other):
+        with pytest.raises(lbgb.LBError) as e:
+            c.load(buf)
+        assert e.value.code == lbgb.LB_EINVAL
+    same = lbgb.Box(12, 8, 8, 0.8, 0.1, 3.0, 0.01)
+    same.set_density(10.0, 1.0, 0.6, 0.8)
+    same.set_gravity((0.0, 0.0, -1e-5), 2.0)
+    same.load(buf)
+    assert same.time == 3
+    # a checkpoint without contrasts does not load into a context with them
+    b = lbgb.Box(12, 8, 8, 0.8, 0.1, 3.0, 0.01)
+    b.init(phi, u)
+    with pytest.raises(lbgb.LBError) as e:
+        same.load(b.save())
+    assert e.value.code == lbgb.LB_EINVAL
+    for x in (a, plain, other, same, b):
+        x.close()
+
+
 def test_set_density_rejects_bad_parameters(lbgb):
     b = lbgb.Box(8, 8, 8, 1.0, 0.1, 3.0, 0.01)
     for bad in ((0.0, 1.0, 1.0, 1.0), (1.0, -1.0, 1.0, 1.0), (1.0, 1.0, 0.5, 1.0), (1.0, 1.0, 1.0, 0.4),

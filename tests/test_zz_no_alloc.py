@@ -77,3 +77,53 @@ def test_static_stats_reject_boxes_beyond_the_array(lbgb):
     rc = lbgb.lib().lb_field_stats_static(phi.data_ptr(), u.data_ptr(), 1024, 1024, 1024, None, out)
     assert rc == lbgb.LB_EINVAL
     assert "partial records" in lbgb.lib().lb_last_error().decode()
+
+
+def test_static_stats_on_a_side_stream_and_after_a_larger_box(lbgb):
+    """A larger box leaves more records in the shared array than a smaller one
+    writes; the smaller box's result must not see them.  The calls run on a
+    side stream, as a caller with its own stream would make them."""
+    import torch
+
+    side = torch.cuda.Stream()
+    for shape in [(70, 24, 48), (9, 7, 5)]:
+        phi, u = fields(shape, seed=3)
+        nz, ny, nx = shape
+        box = lbgb.Box(nx, ny, nz, 0.8, 0.1, 3.0, 0.01)
+        box.init(phi, u)
+        ref = box.diagnostics()
+        box.close()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            out = lbgb.field_stats_static(phi, u, stream=side)
+        np.testing.assert_allclose(out[[0, 1, 3]], ref[[0, 1, 3]], rtol=RTOL)
+
+
+def test_static_stats_report_a_nan_with_a_host_result(lbgb):
+    phi, u = fields((16, 16, 16), seed=5)
+    u[1, 3, 4, 5] = float("nan")
+    with pytest.raises(lbgb.LBError) as exc:
+        lbgb.field_stats_static(phi, u)
+    assert exc.value.code == lbgb.LB_ENONFINITE
+
+
+def test_static_stats_reject_host_fields(lbgb):
+    phi = np.zeros(8, np.float32)
+    u = np.zeros(24, np.float32)
+    out = (lbgb.ctypes.c_double * 5)()
+    rc = lbgb.lib().lb_field_stats_static(phi.ctypes.data, u.ctypes.data, 2, 2, 2, None, out)
+    assert rc == lbgb.LB_EINVAL
+    assert "device memory" in lbgb.lib().lb_last_error().decode()
+
+
+def test_static_stats_reject_another_devices_memory(lbgb):
+    import torch
+
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two GPUs")
+    phi = torch.zeros(8, device="cuda:1")
+    u = torch.zeros(24, device="cuda:1")
+    out = (lbgb.ctypes.c_double * 5)()
+    with torch.cuda.device(0):
+        rc = lbgb.lib().lb_field_stats_static(phi.data_ptr(), u.data_ptr(), 2, 2, 2, None, out)
+    assert rc == lbgb.LB_EINVAL
