@@ -265,15 +265,15 @@ void lb_destroy(lb_ctx* ctx);
  *   scale    bin unit: > 0 as given, <= 0 the RMS gradient sqrt(M2)
  *   stream   cudaStream_t (NULL: legacy default stream); the call returns
  *            when its results are on the host
- *   out      host, 3 + 2*rmax doubles: M2, M3, M4, then S_2(1..rmax), then
- *            S_3(1..rmax)
+ *   out      host, 5 + 2*rmax doubles: M2, M3, M4, the skewness S and the
+ *            flatness F, then S_2(1..rmax), then S_3(1..rmax)
  *   hist     host, nbins + 2 counts (NULL allowed when nbins == 0): the bins,
  *            then the samples below and above the range
  * The samples are the longitudinal gradients g = d_a u_a, a = x, y, z, at
  * every site (3N samples), with the lattice gradient of Sec. 2.3 evaluated in
  * FP32 with each operation rounded on its own; M_n is the mean of g^n (FP32
- * per-thread sums, FP64 across threads), so the skewness is M3 / M2^(3/2) and
- * the flatness M4 / M2^2.  Sample g falls in bin
+ * per-thread sums, FP64 across threads); S = M3 / M2^(3/2) and F = M4 / M2^2
+ * are formed in FP64 on the device (NaN when M2 = 0).  Sample g falls in bin
  * floor((g * (1/scale) + range) * (nbins / (2 range))), evaluated in FP64.
  * S_n(r) is the mean over a and sites of (u_a(x + r e_a) - u_a(x))^n (FP32
  * differences and per-thread sums, FP64 across threads).  Scratch memory is

@@ -10,17 +10,13 @@ Definitions (readings of Sec. 5.1, which defines S, F, S_2 and S_3 but not
 the discretisation or the sampling):
 - Longitudinal gradient samples: g = d_a u_a for a = x, y, z at every site
   (3N samples of a periodic nx*ny*nz field), with the lattice gradient of
-  Sec. 2.3, (1/cs^2) sum_i w_i c_ia psi(x + c_i).  Using the factorisation of
-  the D3Q27 weights this is (1/72) sum over the two transverse offsets of
-  k(c) k(c') [psi(+1) - psi(-1)], k = (1, 4, 1); the sums are taken in the
-  order written in `longitudinal_gradients`, which the device code follows.
+  Sec. 2.3, (1/cs^2) sum_i w_i c_ia psi(x + c_i), in FP64.  Using the
+  factorisation of the D3Q27 weights this is (1/72) sum over the two
+  transverse offsets of k(c) k(c') [psi(+1) - psi(-1)], k = (1, 4, 1).
 - Moments M_n = mean of g^n (n = 2, 3, 4); S = M3 / M2^(3/2), F = M4 / M2^2.
-- Histogram of g / scale over nbins equal bins on [-range, range): bin
-  floor((g * (1/scale) + range) * (nbins / (2 range))) in FP64, with counts
-  below and above.  A bin is an integer decided by floating point, so it is
-  decided from the samples in the precision the device computes them in:
-  FP32, with every operation of the stencil rounded on its own
-  (`longitudinal_gradients(u, np.float32)`).
+- Histogram of g / scale over nbins equal bins on [-range, range): sample g
+  falls in bin floor((g / scale + range) * nbins / (2 range)), with counts
+  below and above the range; all in FP64.
 - Longitudinal structure functions S_n(r) = mean over a and sites of
   (u_a(x + r e_a) - u_a(x))^n, n = 2, 3, periodic.
 """
@@ -37,28 +33,38 @@ def _shift(f: np.ndarray, axis: int, c: int) -> np.ndarray:
     return np.roll(f, -c, axis=axis)
 
 
-def longitudinal_gradients(u: np.ndarray, dtype=np.float64) -> np.ndarray:
-    """d_a u_a for a = x, y, z: array (3, nz, ny, nx) in `dtype` (FP64, or FP32
-    with each operation rounded to FP32, as the device evaluates it).
-
-    For each a, with t1 < t2 the two transverse directions:
-      d(c1, c2) = u_a(x + e_a + c1 e_t1 + c2 e_t2) - u_a(x - e_a + c1 e_t1 + c2 e_t2)
-      e(c2)     = (d(-1, c2) + d(+1, c2)) + 4 d(0, c2)
-      g         = ((e(-1) + e(+1)) + 4 e(0)) / 72
-    """
-    u = np.asarray(u, dtype=dtype)
-    four, c72 = dtype(4.0), dtype(72.0)
-    out = np.empty_like(u)
+def _stencil_terms(u: np.ndarray):
+    """For each direction a: the nine differences d(c1, c2) = u_a(x + e_a + c1 e_t1
+    + c2 e_t2) - u_a(x - e_a + c1 e_t1 + c2 e_t2) (t1, t2 the transverse
+    directions) with their weights k(c1) k(c2), k = (1, 4, 1)."""
+    u = np.asarray(u, dtype=np.float64)
+    k = {-1: 1.0, 0: 4.0, 1: 1.0}
     for a in range(3):
-        ua = u[a]
         ax = _AX[a]
         t1, t2 = [_AX[t] for t in range(3) if t != a]
-        d = _shift(ua, ax, 1) - _shift(ua, ax, -1)
-        e = {}
-        for c2 in (-1, 0, 1):
-            dc = _shift(d, t2, c2)
-            e[c2] = (_shift(dc, t1, -1) + _shift(dc, t1, 1)) + four * dc
-        out[a] = ((e[-1] + e[1]) + four * e[0]) / c72
+        d = _shift(u[a], ax, 1) - _shift(u[a], ax, -1)
+        yield a, [(k[c1] * k[c2], _shift(_shift(d, t1, c1), t2, c2)) for c1 in (-1, 0, 1) for c2 in (-1, 0, 1)]
+
+
+def longitudinal_gradients(u: np.ndarray) -> np.ndarray:
+    """d_a u_a for a = x, y, z: array (3, nz, ny, nx), FP64,
+    g = (1/72) sum_{c1, c2} k(c1) k(c2) d(c1, c2)."""
+    u = np.asarray(u, dtype=np.float64)
+    out = np.empty_like(u)
+    for a, terms in _stencil_terms(u):
+        out[a] = sum(w * d for w, d in terms) / 72.0
+    return out
+
+
+def stencil_magnitude(u: np.ndarray) -> np.ndarray:
+    """(1/72) sum_{c1, c2} k(c1) k(c2) |d(c1, c2)| per sample, shape (3, nz, ny, nx):
+    the scale of the rounding error of any evaluation of the gradient that
+    rounds each of its operations (an FP32 evaluation is off by at most a few
+    2^-24 of it)."""
+    u = np.asarray(u, dtype=np.float64)
+    out = np.empty_like(u)
+    for a, terms in _stencil_terms(u):
+        out[a] = sum(w * np.abs(d) for w, d in terms) / 72.0
     return out
 
 
@@ -71,9 +77,8 @@ def gradient_moments(u: np.ndarray) -> dict:
 
 def gradient_histogram(u: np.ndarray, nbins: int, rng: float, scale: float) -> np.ndarray:
     """Counts (nbins + 2 integers): the nbins bins, then below and above."""
-    g = longitudinal_gradients(u, np.float32).ravel().astype(np.float64)
-    f = nbins / (2.0 * rng)
-    b = np.floor((g * (1.0 / scale) + rng) * f)
+    g = longitudinal_gradients(u).ravel()
+    b = np.floor((g / scale + rng) * (nbins / (2.0 * rng)))
     out = np.zeros(nbins + 2, dtype=np.int64)
     inside = (b >= 0) & (b < nbins)
     np.add.at(out, b[inside].astype(np.int64), 1)

@@ -103,6 +103,14 @@ __global__ void __launch_bounds__(ST_NT) reduce_cols_kernel(const double* part, 
     }
 }
 
+// Skewness S = M3 / M2^(3/2) and flatness F = M4 / M2^2 from the moments
+// mom[0..2], into mom[3], mom[4] (FP64; NaN for a field without gradients).
+__global__ void skew_flat_kernel(double* mom) {
+    const double m2 = mom[0];
+    mom[3] = mom[1] / (m2 * sqrt(m2));
+    mom[4] = mom[2] / (m2 * m2);
+}
+
 // Pass 2: histogram of g / scale (scale from the host if > 0, else sqrt(M2)
 // from pass 1 on the device) in nbins bins on [-range, range), then the
 // counts below and above.
@@ -275,7 +283,7 @@ extern "C" int lb_velocity_statistics(const float* u, int nx, int ny, int nz, in
 
     // device scratch: moment partials, moments (3), structure partials and results, histogram
     const size_t n_mp = 3 * (size_t)blocks, n_sp = 2 * (size_t)blocks * (size_t)(rmax > 0 ? rmax : 1);
-    const size_t n_dbl = n_mp + 3 + n_sp + 2 * (size_t)rmax;
+    const size_t n_dbl = n_mp + 5 + n_sp + 2 * (size_t)rmax;
     double* scratch = nullptr;
     unsigned long long* dhist = nullptr;
     e = cudaMalloc(&scratch, n_dbl * sizeof(double));
@@ -289,12 +297,13 @@ extern "C" int lb_velocity_statistics(const float* u, int nx, int ny, int nz, in
     }
     double* mp = scratch;
     double* mom = mp + n_mp;
-    double* sp = mom + 3;
+    double* sp = mom + 5;
     double* sres = sp + n_sp;
     int rc = LB_OK;
     do {
         grad_moments_kernel<<<blocks, ST_NT, 0, st>>>(F, N, mp);
         reduce_cols_kernel<<<1, ST_NT, 0, st>>>(mp, blocks, 3, 3.0 * (double)N, mom);
+        skew_flat_kernel<<<1, 1, 0, st>>>(mom);
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         if (nbins > 0) {
             if ((e = cudaMemsetAsync(dhist, 0, (size_t)(nbins + 2) * sizeof(unsigned long long), st)) != cudaSuccess)
@@ -310,9 +319,9 @@ extern "C" int lb_velocity_statistics(const float* u, int nx, int ny, int nz, in
             structure_reduce_kernel<<<rmax, ST_NT, 0, st>>>(sp, blocks, 3.0 * (double)N, sres, sres + rmax);
             if ((e = cudaGetLastError()) != cudaSuccess) break;
         }
-        if ((e = cudaMemcpyAsync(out, mom, 3 * sizeof(double), cudaMemcpyDefault, st)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(out, mom, 5 * sizeof(double), cudaMemcpyDefault, st)) != cudaSuccess) break;
         if (rmax > 0 &&
-            (e = cudaMemcpyAsync(out + 3, sres, 2 * (size_t)rmax * sizeof(double), cudaMemcpyDefault, st)) !=
+            (e = cudaMemcpyAsync(out + 5, sres, 2 * (size_t)rmax * sizeof(double), cudaMemcpyDefault, st)) !=
                 cudaSuccess)
             break;
         if (nbins > 0 && (e = cudaMemcpyAsync(hist, dhist, (size_t)(nbins + 2) * sizeof(unsigned long long),

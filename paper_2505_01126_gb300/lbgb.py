@@ -168,14 +168,12 @@ def velocity_statistics(u, rmax: int = 0, nbins: int = 0, range_: float = 8.0, s
     _, nz, ny, nx = (int(v) for v in u.shape)
     q, _a = _ptr(u, 3 * nx * ny * nz)
     handle = getattr(stream, "cuda_stream", stream)
-    out = (ctypes.c_double * (3 + 2 * rmax))()
+    out = (ctypes.c_double * (5 + 2 * rmax))()
     hist = (ctypes.c_ulonglong * (nbins + 2))() if nbins > 0 else None
     _check(_lib.lb_velocity_statistics(q, nx, ny, nz, int(rmax), int(nbins), float(range_), float(scale),
                                        ctypes.c_void_p(int(handle) if handle else 0), out, hist))
     o = np.array(list(out))
-    m2, m3, m4 = o[:3]
-    res = {"M2": m2, "M3": m3, "M4": m4, "S": m3 / m2 ** 1.5 if m2 > 0 else float("nan"),
-           "F": m4 / (m2 * m2) if m2 > 0 else float("nan"), "S2": o[3:3 + rmax], "S3": o[3 + rmax:]}
+    res = {"M2": o[0], "M3": o[1], "M4": o[2], "S": o[3], "F": o[4], "S2": o[5:5 + rmax], "S3": o[5 + rmax:]}
     if nbins > 0:
         res["hist"] = np.array(list(hist), dtype=np.int64)
     return res

@@ -76,7 +76,7 @@ def test_droplet_32_with_density_and_viscosity_contrast(lbgb, orc, dens):
     b, o, got, want = run_vd(lbgb, orc, (32, 32, 32), w.tau, w.M, w.W, w.sigma, w.phi, w.u, 50, dens)
     e = max_err(got, want)
     assert max(e) <= TOL, e
-    check_diagnostics(b.diagnostics(), o.diagnostics(), 32 ** 3)
+    check_diagnostics(b.diagnostics(), o.diagnostics(), 32 ** 3, field_err=max(e), tau=dens[2:])
 
 
 @pytest.mark.parametrize("shape", [(11, 13, 37), (5, 9, 70), (40, 3, 33), (2, 2, 2), (1, 1, 1), (3, 1, 5)])
@@ -100,7 +100,7 @@ def test_forcing_kinds(lbgb, orc, kind):
     e = max_err(got, want)
     assert max(e) <= TOL, e
     dg, do = b.diagnostics(), o.diagnostics()
-    check_diagnostics(dg, do, int(np.prod(shape)))
+    check_diagnostics(dg, do, int(np.prod(shape)), field_err=max(e), tau=(0.6, 0.8))
     if kind == "linear":
         assert abs(dg[4] - do[4]) <= 1e-5 * abs(do[4]) + 1e-9
 
@@ -122,20 +122,36 @@ def test_hit_64_heavy_droplets(lbgb, orc):
                              (10.0, 1.0, 0.55, 0.51), force=force)
     e = max_err(got, want)
     assert max(e) <= TOL, e
-    check_diagnostics(b.diagnostics(), o.diagnostics(), 64 ** 3)
+    check_diagnostics(b.diagnostics(), o.diagnostics(), 64 ** 3, field_err=max(e), tau=(0.55, 0.51))
+
+
+def storage_rounded_oracle(orc, o):
+    """One step of oracle `o` followed by rounding its state to what FP32
+    storage keeps (f as the shifted population f/w - 1, g as is)."""
+    _, wt = orc.lattice27()
+    o.step(1)
+    f, g = o.populations()
+    w4 = wt[:, None, None, None]
+    d = (f / w4 - 1.0).astype(np.float32).astype(np.float64)
+    o.set_populations(w4 * (1.0 + d), g.astype(np.float32).astype(np.float64))
+
+
+GAS_K = 4.0  # GPU error in phi at most GAS_K times the oracle's own storage-rounding spread
 
 
 def test_hit_64_gas_bubbles(lbgb, orc):
     """64^3 forced turbulence (tau 0.51 in the liquid), two gas bubbles R = 10 at
     density ratio 10 and tau 0.55 in the gas (phi = 0 in the bubbles), linear
-    forcing.  p* and u meet the FP32 bar after 50 steps.  phi does after 10 steps
-    but not after 50: the liquid bulk sits at phi ~ 1, where FP32 resolves phi to
-    6e-8 only, and on the nearly flat plateaus next to the bulk (phi (1 - phi)
-    ~ 1e-2, |grad phi| ~ 1e-5) the normal grad phi / |grad phi| turns with that
-    rounding; the sharpening flux amplifies the difference by about 1.26 per step
-    to ~1.3e-4 after 50 steps.  The single-density kernel on the same phase field
-    shows the same growth (1.26e-4 against the oracle), so the bar for phi at 50
-    steps is: no worse than 1.5 x the single-density kernel's own error."""
+    forcing.  p* and u meet the FP32 bar after 50 steps; phi does after 10
+    steps.  After 50 it does not: the liquid bulk sits at phi ~ 1, where FP32
+    resolves phi to 6e-8 only, and on the nearly flat plateaus next to the bulk
+    (phi (1 - phi) ~ 1e-2, |grad phi| ~ 1e-5) the normal grad phi / |grad phi|
+    turns with that rounding, which the sharpening flux amplifies about 1.26x
+    per step.  The bar for phi at 50 steps therefore comes from the method's
+    own sensitivity: a second oracle run whose state is rounded to FP32 storage
+    after every step (f as f/w - 1, g as is) departs from the plain oracle by a
+    spread s; the GPU, which rounds its storage the same way and its arithmetic
+    on top, must stay within GAS_K = 4 s of the plain oracle (measured: 2.1 s)."""
     w, phi = gas_bubbles(64, 2, 10.0, 2)
     force = dict(force_kind=3, T_relax=w.T_relax)
     dens = (1.0, 0.1, 0.51, 0.55)
@@ -147,16 +163,15 @@ def test_hit_64_gas_bubbles(lbgb, orc):
     got, want = b.moments_numpy(), o.moments()
     e = max_err(got, want)
     assert max(e[:2]) <= TOL, e
-    check_diagnostics(b.diagnostics(), o.diagnostics(), 64 ** 3, delta=e[2])
-    # the single-density kernel and oracle on the same phase field
-    sd = lbgb.Box(64, 64, 64, w.tau, w.M, w.W, w.sigma, force=_lb_force(lbgb, force))
-    sd.init(phi, w.u)
-    sd.step(50)
-    osd = orc.Oracle(64, 64, 64, w.tau, w.M, w.W, w.sigma, **force)
-    osd.init(phi.astype(np.float64), w.u.astype(np.float64))
-    osd.step(50)
-    e_sd = max_err(sd.moments_numpy(), osd.moments())
-    assert e[2] <= 1.5 * e_sd[2], (e, e_sd)
+    check_diagnostics(b.diagnostics(), o.diagnostics(), 64 ** 3, delta=e[2], tau=dens[2:])
+    r = orc.Oracle(64, 64, 64, w.tau, w.M, w.W, w.sigma, **force)
+    r.set_density(*dens)
+    r.init(phi.astype(np.float64), w.u.astype(np.float64))
+    for _ in range(50):
+        storage_rounded_oracle(orc, r)
+    spread = max_err(r.moments(), want)
+    r.close()
+    assert 0.0 < spread[2] and e[2] <= GAS_K * spread[2], (e, spread)
 
 
 @pytest.mark.parametrize("tile", [(4, 8), (8, 16), (8, 5)])
@@ -326,7 +341,7 @@ def test_full_size_256_gas_bubbles_one_step_each_parity(lbgb, orc):
     o.close()
     e = max_err(got, want)
     assert max(e) <= TOL, e
-    check_diagnostics(dg, do, n ** 3)
+    check_diagnostics(dg, do, n ** 3, field_err=max(e), tau=(0.51, 0.55))
 
 
 def test_gas_bubbles_64_stay_finite_for_400_steps(lbgb):
@@ -370,7 +385,7 @@ def test_paper_droplet_case_256_full_parity(lbgb, orc):
     o.close()
     e = max_err(got, want)
     assert max(e) <= TOL, e
-    check_diagnostics(dg, do, n ** 3)
+    check_diagnostics(dg, do, n ** 3, field_err=max(e), tau=dens[2:])
 
 
 def test_paper_droplet_case_512_properties(lbgb):
@@ -428,7 +443,7 @@ def test_buoyant_droplet_32(lbgb, orc, storage):
     e = max_err(got, o.moments())
     assert max(e) <= TOL, e
     assert float(np.abs(got[1][2]).max()) > 1e-5  # the droplet does move
-    check_diagnostics(b.diagnostics(), o.diagnostics(), 32 ** 3)
+    check_diagnostics(b.diagnostics(), o.diagnostics(), 32 ** 3, field_err=max(e), tau=dens[2:])
 
 
 def test_buoyant_turbulence_64_heavy_droplets(lbgb, orc):
@@ -450,7 +465,7 @@ def test_buoyant_turbulence_64_heavy_droplets(lbgb, orc):
     o.step(50)
     e = max_err(b.moments_numpy(), o.moments())
     assert max(e) <= TOL, e
-    check_diagnostics(b.diagnostics(), o.diagnostics(), 64 ** 3)
+    check_diagnostics(b.diagnostics(), o.diagnostics(), 64 ** 3, field_err=max(e), tau=dens[2:])
 
 
 def test_gravity_switched_on_mid_run(lbgb, orc):

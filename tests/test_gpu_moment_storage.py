@@ -100,7 +100,7 @@ def test_moment_storage_hit_64_against_oracle(lbgb, orc):
     b.step(50)
     e = max_err(b.moments_numpy(), o.moments())
     assert max(e) <= TOL, e
-    check_diagnostics(b.diagnostics(), o.diagnostics(), n ** 3)
+    check_diagnostics(b.diagnostics(), o.diagnostics(), n ** 3, field_err=max(e), tau=w.tau)
 
 
 def test_moment_storage_full_size_256(lbgb):

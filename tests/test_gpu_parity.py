@@ -75,15 +75,32 @@ def max_err(got, want):
     return [float(np.abs(g.astype(np.float64) - w).max()) for g, w in zip(got, want)]
 
 
-def check_diagnostics(dg, do, N, delta=TOL):
+def eps_weight(tau: float) -> float:
+    """eps per unit of sum a2:a2 at relaxation time tau: 2 nu (3 / (2 tau))^2."""
+    return 2.0 * (tau - 0.5) / 3.0 * (1.5 / tau) ** 2
+
+
+def check_diagnostics(dg, do, N, delta=TOL, tau=1.0, field_err=None):
     """GPU FP64 reductions against the oracle's, with bounds that follow from
     fields agreeing to `delta` per component: Phi within N delta; K within
-    sqrt(2 K 3N) delta + 1.5 N delta^2 (Cauchy-Schwarz on sum u.du); max|u| within
-    sqrt(3) delta; eps (a sum of squared Hermite coefficients) within 2%."""
+    sqrt(2 K 3N) delta + 1.5 N delta^2 (Cauchy-Schwarz on sum u.du); max|u|
+    within sqrt(3) delta.  eps = sum_sites c(tau_s) a2:a2 (c = eps_weight; tau a
+    number, or the (tau_l, tau_g) pair of a density contrast) is held to the
+    field error actually measured, field_err (default delta): the Hermite
+    coefficients are moments of the same populations as p* and u, formed from
+    them in FP32 (27 shifted terms of size ~0.1, rounding ~2e-7), so each of
+    the 9 entries of a2 is taken within da = 2 field_err + 2e-7; with
+    S = sum a2:a2 <= eps_oracle / c_min, Cauchy-Schwarz gives
+    |d eps| <= c_max (2 sqrt(S) sqrt(9N) da + 9N da^2)."""
     assert abs(dg[0] - do[0]) <= N * delta
     assert abs(dg[1] - do[1]) <= math.sqrt(2 * do[1] * 3 * N) * delta + 1.5 * N * delta ** 2
     assert abs(dg[3] - do[3]) <= math.sqrt(3) * delta
-    assert abs(dg[2] - do[2]) <= 0.02 * abs(do[2]) + 1e-12
+    taus = tau if isinstance(tau, (tuple, list)) else (tau,)
+    cs = [eps_weight(t) for t in taus]
+    da = 2.0 * (delta if field_err is None else field_err) + 2e-7
+    S = abs(do[2]) / min(cs)
+    bound = max(cs) * (2.0 * math.sqrt(S) * math.sqrt(9.0 * N) * da + 9.0 * N * da * da)
+    assert abs(dg[2] - do[2]) <= bound, (dg[2], do[2], bound)
 
 
 def test_static_droplet_32_50_steps(lbgb, orc):
@@ -92,7 +109,7 @@ def test_static_droplet_32_50_steps(lbgb, orc):
     b, o, got, want = run_pair(lbgb, orc, (32, 32, 32), w.tau, w.M, w.W, w.sigma, w.phi, w.u, 50)
     e = max_err(got, want)
     assert max(e) <= TOL, e
-    check_diagnostics(b.diagnostics(), o.diagnostics(), 32 ** 3)
+    check_diagnostics(b.diagnostics(), o.diagnostics(), 32 ** 3, field_err=max(e), tau=w.tau)
 
 
 def test_init_state_moments(lbgb, orc):
@@ -125,7 +142,7 @@ def test_forcing_kinds(lbgb, orc, kind):
     e = max_err(got, want)
     assert max(e) <= TOL, e
     dg, do = b.diagnostics(), o.diagnostics()
-    check_diagnostics(dg, do, int(np.prod(shape)))
+    check_diagnostics(dg, do, int(np.prod(shape)), field_err=max(e), tau=0.6)
     if kind == "linear":
         assert abs(dg[4] - do[4]) <= 1e-5 * abs(do[4]) + 1e-9
 
@@ -289,7 +306,7 @@ def test_full_size_256_one_step_each_parity(lbgb, orc):
     o.close()
     e = max_err(got, want)
     assert max(e) <= TOL, e
-    check_diagnostics(dg, do, n ** 3)
+    check_diagnostics(dg, do, n ** 3, field_err=max(e), tau=w.tau)
 
 
 def test_single_phase_abc_hit(lbgb, orc):
@@ -302,4 +319,4 @@ def test_single_phase_abc_hit(lbgb, orc):
     e = max_err(got, want)
     assert max(e) <= TOL, e
     assert not got[2].any()
-    check_diagnostics(b.diagnostics(), o.diagnostics(), 48 ** 3)
+    check_diagnostics(b.diagnostics(), o.diagnostics(), 48 ** 3, field_err=max(e), tau=w.tau)

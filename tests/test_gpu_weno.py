@@ -78,7 +78,7 @@ def test_droplet_32_50_steps(lbgb, orc):
     b, o, got, want = run_fd(lbgb, orc, (32, 32, 32), w.tau, w.M, w.W, w.sigma, w.phi, w.u, 50)
     e = max_err(got, want)
     assert max(e) <= TOL, e
-    check_diagnostics(b.diagnostics(), o.diagnostics(), 32 ** 3)
+    check_diagnostics(b.diagnostics(), o.diagnostics(), 32 ** 3, field_err=max(e), tau=w.tau)
 
 
 @pytest.mark.parametrize("shape", [(11, 13, 37), (5, 9, 70), (40, 3, 33), (2, 2, 2), (1, 1, 1), (3, 1, 5),
@@ -101,7 +101,7 @@ def test_forcing_kinds(lbgb, orc, kind):
     e = max_err(got, want)
     assert max(e) <= TOL, e
     dg, do = b.diagnostics(), o.diagnostics()
-    check_diagnostics(dg, do, int(np.prod(shape)))
+    check_diagnostics(dg, do, int(np.prod(shape)), field_err=max(e), tau=0.6)
     if kind == "linear":
         assert abs(dg[4] - do[4]) <= 1e-5 * abs(do[4]) + 1e-9
 
@@ -112,7 +112,7 @@ def test_hit_64_two_bubbles(lbgb, orc):
     b, o, got, want = run_fd(lbgb, orc, (64, 64, 64), w.tau, w.M, w.W, w.sigma, w.phi, w.u, 50, force=force)
     e = max_err(got, want)
     assert max(e) <= TOL, e
-    check_diagnostics(b.diagnostics(), o.diagnostics(), 64 ** 3)
+    check_diagnostics(b.diagnostics(), o.diagnostics(), 64 ** 3, field_err=max(e), tau=w.tau)
 
 
 def test_density_contrast_and_buoyancy(lbgb, orc):
@@ -234,7 +234,7 @@ def test_full_size_256_one_step_each_parity(lbgb, orc):
     o.close()
     e = max_err(got, want)
     assert max(e) <= TOL, e
-    check_diagnostics(dg, do, n ** 3)
+    check_diagnostics(dg, do, n ** 3, field_err=max(e), tau=w.tau)
 
 
 def test_phase_mass_over_500_steps(lbgb):
