@@ -202,23 +202,46 @@ int lb_sync(lb_ctx* ctx);
 long long lb_time(const lb_ctx* ctx);
 
 /* Launch shape of the fused step kernel: tile height ty (x tile is 32 sites)
- * in {4, 8} and z-chunk zc >= 1 planes per block.  Takes effect at the
+ * in {4, 8} (and 16 while the paired kernel runs the step, see
+ * lb_set_pairing) and z-chunk zc >= 1 planes per block.  Takes effect at the
  * next lb_step; lb_tune picks it by measurement. */
 int lb_set_tile(lb_ctx* ctx, int ty, int zc);
 int lb_get_tile(const lb_ctx* ctx, int* ty, int* zc);
 
 /*
+ * lb_set_pairing -- which kernel runs the step of the FP16 and BF16 storages.
+ * on = 1 (the default where it applies): the paired kernel, in which each
+ * thread owns two x-adjacent sites, evaluates steps 4-13 for both with packed
+ * two-lane FP32 instructions (sm_100's FADD2 / FMUL2 / FFMA2: one instruction,
+ * two IEEE-rounded FP32 results) and loads and stores the two sites' stored
+ * populations as one 32-bit pair wherever their AA slots are adjacent (every
+ * direction at even t, those with c_x = 0 at odd t).  These storages are
+ * bound by instruction issue, which this halves for the arithmetic.  on = 0:
+ * one site per thread, as for every other storage.  The two compute the same
+ * formulas in FP32; their results agree to FP32 rounding, not bit for bit.
+ * The paired kernel applies to FP16/BF16 storage with nx % 4 == 0, the D3Q7
+ * phase field and no density contrasts; lb_set_density and
+ * lb_set_phase_solver(LB_PHASE_WENO5) switch back to the one-site kernel
+ * (a tile height of 16 becomes 8).  lb_get_pairing reports whether the paired
+ * kernel runs the step.
+ * Errors: LB_EINVAL for on = 1 where the paired kernel does not apply.
+ */
+int lb_set_pairing(lb_ctx* ctx, int on);
+int lb_get_pairing(const lb_ctx* ctx, int* on);
+
+/*
  * lb_tune -- time tile heights ty in {8, 4} with z-chunks zc in {16, 32, 64,
  * 128} and the two chunkings whose block count best fills the last wave of
- * resident blocks, each as the median of five windows of 2*steps steps, and
- * keep the first shape in that order whose median is within 1% of the
- * fastest (so shapes that time alike do not trade places on noise).  Before lb_init it times on the context's own
+ * resident blocks (with FP16/BF16 storage first the paired kernel's heights
+ * 8, 16, 4, then the one-site kernel's), each as the median of five windows of
+ * 2*steps steps, and keep the first shape in that order whose median is within
+ * 1% of the fastest (so shapes that time alike do not trade places on noise).  Before lb_init it times on the context's own
  * arrays, so the timed launches have the real box's block counts, and leaves
  * the context uninitialised; after lb_init it times on a scratch box with this
  * box's nx, ny, storage and min(nz, 128) planes, allocated and freed here,
  * and leaves the state untouched.  Results are cached per (device name, nx,
- * ny, nz, storage, density contrasts on or off) in the file named by
- * LBGB_TUNE_CACHE, if set.
+ * ny, nz, storage, density contrasts on or off, phase solver), with the
+ * pairing choice, in the file named by LBGB_TUNE_CACHE, if set.
  */
 int lb_tune(lb_ctx* ctx, int steps);
 
@@ -302,6 +325,26 @@ int lb_velocity_statistics(const float* u, int nx, int ny, int nz, int rmax, int
  * allocated and freed here.  Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA.
  */
 int lb_spectrum(const float* f, int ncomp, int n, int kmax, void* stream, double* out);
+
+/*
+ * lb_measure_fp32_peak -- the FP32 throughput this device sustains, measured:
+ * a grid filling every SM (64 resident warps each) runs independent FP32
+ * fused multiply-add chains for about 10 ms (best of three timed launches
+ * after one warm-up, CUDA events on `stream`, NULL: the legacy default
+ * stream), once as scalar FMAs and once as packed two-lane FMAs (__ffma2_rn,
+ * two FP32 FMAs per instruction).  The roofline of the kernels that are bound
+ * by instruction issue rather than HBM (the 16-bit and moment-only storages,
+ * the finite-difference stages) is taken against it.  Not part of the method
+ * (the paper has no counterpart).
+ *   out  host, 6 doubles: FP32 FLOP/s with scalar FMAs (2 per FMA), scalar FMA
+ *        warp-instructions issued per second (one per scheduler and cycle at
+ *        most), that kernel's time in ms, the SM clock in MHz seen by the first
+ *        block (clock64 cycles over the global timer), FP32 FLOP/s with packed
+ *        FMAs, packed FMA warp-instructions per second
+ * Allocates and frees a few bytes of device memory.  Errors: LB_EINVAL,
+ * LB_ENOMEM, LB_ECUDA.
+ */
+int lb_measure_fp32_peak(void* stream, double out[6]);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* lb_last_error(void);

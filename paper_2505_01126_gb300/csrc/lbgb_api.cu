@@ -126,6 +126,9 @@ struct lb_ctx {
 
     cudaGraphExec_t graph = nullptr;  // two steps starting at even parity
     int graph_ty = 0, graph_zc = 0;
+    bool graph_pair = false;
+
+    bool pair = false;  // paired step kernel preferred (16-bit storages; see use_pair)
 
     bool fd = false;  // phase field by finite differences (lb_set_phase_solver)
     bool vd = false;  // density and viscosity contrasts (lb_set_density)
@@ -145,6 +148,14 @@ dim3 grid_for(const lb_ctx* c, int ty, int zc) {
 }
 
 bool is_mc(const lb_ctx* c) { return c->storage == LB_F32_MOMENTS; }
+
+// The paired step kernel (two x-adjacent sites per thread, packed two-lane FP32
+// arithmetic) runs the step when it is preferred and applies: a 16-bit AA
+// storage, nx a multiple of 4, the D3Q7 phase field, no density contrasts.
+bool pair_applies(const lb_ctx* c) {
+    return (c->storage == LB_F16_SHIFTED || c->storage == LB_BF16_SHIFTED) && c->nx % 4 == 0 && !c->vd && !c->fd;
+}
+bool use_pair(const lb_ctx* c) { return c->pair && pair_applies(c); }
 
 size_t f_bytes(const lb_ctx* c) { return (size_t)c->N * (is_mc(c) ? 20 * sizeof(float) : 27 * c->fsize); }
 
@@ -270,7 +281,12 @@ int enqueue_step(lb_ctx* c, int par, cudaStream_t s, bool first = false) {
         }
         LB_CUDA(cudaEventRecord(c->ev_start[c->ev_used], s));
     }
-    LB_CUDA(launch_any(c, MODE_STEP, is_mc(c) ? (first ? 0 : 1) : par, c->ty, grid, a, s));
+    if (use_pair(c)) {
+        LB_CUDA(c->storage == LB_F16_SHIFTED ? launch_fused_pair<__half>(par, c->ty, grid, a, s)
+                                             : launch_fused_pair<__nv_bfloat16>(par, c->ty, grid, a, s));
+    } else {
+        LB_CUDA(launch_any(c, MODE_STEP, is_mc(c) ? (first ? 0 : 1) : par, c->ty, grid, a, s));
+    }
     if (timed) {
         LB_CUDA(cudaEventRecord(c->ev_stop[c->ev_used], s));
         c->ev_used += 1;
@@ -325,6 +341,7 @@ int capture_graph(lb_ctx* c) {
     }
     c->graph_ty = c->ty;
     c->graph_zc = c->zc;
+    c->graph_pair = use_pair(c);
     return LB_OK;
 }
 
@@ -333,8 +350,11 @@ int ensure_stage(lb_ctx* c) {
     return LB_OK;
 }
 
-int check_tile(int ty, int zc) {
-    if (ty != 4 && ty != 8) return fail(LB_EINVAL, "tile height %d not in {4, 8}", ty);
+// Tile heights: {4, 8} for the one-site-per-thread kernels, {4, 8, 16} for the
+// paired kernel.
+int check_tile(int ty, int zc, bool pair = false) {
+    if (ty != 4 && ty != 8 && !(pair && ty == 16))
+        return fail(LB_EINVAL, "tile height %d not in {4, 8%s}", ty, pair ? ", 16" : "");
     if (zc < 1) return fail(LB_EINVAL, "z chunk %d < 1", zc);
     return LB_OK;
 }
@@ -363,6 +383,9 @@ int tune_chunks(const lb_ctx* c, int ty, int zcs[6]) {
         case LB_F32_MOMENTS: per_sm = x ? LBGB_XO(float, true) : fused_mc_blocks_per_sm(ty, vec); break;
     }
 #undef LBGB_XO
+    if (use_pair(c))
+        per_sm = c->storage == LB_F16_SHIFTED ? fused_pair_blocks_per_sm<__half>(ty)
+                                              : fused_pair_blocks_per_sm<__nv_bfloat16>(ty);
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
         cudaGetLastError();
@@ -459,6 +482,7 @@ int lb_create(int nx, int ny, int nz, double tau, double M, double W, double sig
     // default launch shape: z chunk of 32 planes, smaller for thin boxes
     c->ty = 8;
     c->zc = nz < 32 ? nz : 32;
+    c->pair = pair_applies(c);  // the paired kernel by default where it applies
 
     int rc = LB_OK;
     auto alloc = [&](void** p, size_t bytes) {
@@ -553,13 +577,13 @@ int lb_step(lb_ctx* c, int n) {
     if (!c) return fail(LB_EINVAL, "ctx is NULL");
     if (n < 0) return fail(LB_EINVAL, "n = %d < 0", n);
     if (!c->initialized) return fail(LB_ESTATE, "lb_step before lb_init");
-    int rc = check_tile(c->ty, c->zc);
+    int rc = check_tile(c->ty, c->zc, use_pair(c));
     if (rc) return rc;
     while (n > 0) {
         const int par = (int)(c->t & 1);
         const bool first = is_mc(c) && c->t == 0;
         if (par == 0 && n >= 2 && !c->timing && !first) {
-            if (!c->graph || c->graph_ty != c->ty || c->graph_zc != c->zc) {
+            if (!c->graph || c->graph_ty != c->ty || c->graph_zc != c->zc || c->graph_pair != use_pair(c)) {
                 rc = capture_graph(c);
                 if (rc) return rc;
             }
@@ -634,6 +658,7 @@ int lb_set_density(lb_ctx* c, double rho_l, double rho_g, double tau_l, double t
                     tau_l, tau_g);
     c->vd = true;
     c->rho_l = rho_l; c->rho_g = rho_g; c->tau_l = tau_l; c->tau_g = tau_g;
+    if (c->ty == 16) c->ty = 8;  // the contrast kernels are one site per thread
     drop_graph(c);  // the captured launches carry the old kernel and arguments
     return LB_OK;
 }
@@ -644,6 +669,7 @@ int lb_set_phase_solver(lb_ctx* c, int solver) {
     if (c->initialized && (solver == LB_PHASE_WENO5) != c->fd)
         return fail(LB_ESTATE, "lb_set_phase_solver after lb_init (the state is held differently)");
     c->fd = solver == LB_PHASE_WENO5;
+    if (c->fd && c->ty == 16) c->ty = 8;
     drop_graph(c);
     return LB_OK;
 }
@@ -682,10 +708,26 @@ int lb_kernel_time(lb_ctx* c, double* ms, long long* launches) {
 
 int lb_set_tile(lb_ctx* c, int ty, int zc) {
     if (!c) return fail(LB_EINVAL, "ctx is NULL");
-    int rc = check_tile(ty, zc);
+    int rc = check_tile(ty, zc, use_pair(c));
     if (rc) return rc;
     c->ty = ty;
     c->zc = zc > c->nz ? c->nz : zc;
+    return LB_OK;
+}
+
+int lb_set_pairing(lb_ctx* c, int on) {
+    if (!c) return fail(LB_EINVAL, "ctx is NULL");
+    if (on && !pair_applies(c))
+        return fail(LB_EINVAL, "the paired step kernel needs FP16 or BF16 storage, nx %% 4 == 0, the D3Q7 phase "
+                               "field and no density contrasts");
+    c->pair = on != 0;
+    if (!c->pair && c->ty == 16) c->ty = 8;  // the one-site kernels have no 16-row tile
+    return LB_OK;
+}
+
+int lb_get_pairing(const lb_ctx* c, int* on) {
+    if (!c || !on) return fail(LB_EINVAL, "lb_get_pairing: NULL argument");
+    *on = use_pair(c) ? 1 : 0;
     return LB_OK;
 }
 
@@ -824,11 +866,12 @@ int lb_tune(lb_ctx* c, int steps) {
         if (fp) {
             char line[640];
             while (fgets(line, sizeof(line), fp)) {
-                int ty, zc;
+                int ty, zc, pr = 0;
                 size_t kl = strlen(key);
-                if (strncmp(line, key, kl) == 0 && sscanf(line + kl, " %d %d", &ty, &zc) == 2 &&
-                    check_tile(ty, zc) == LB_OK) {
+                if (strncmp(line, key, kl) == 0 && sscanf(line + kl, " %d %d %d", &ty, &zc, &pr) >= 2 &&
+                    (!pr || pair_applies(c)) && check_tile(ty, zc, pr != 0) == LB_OK) {
                     fclose(fp);
+                    c->pair = pr != 0;
                     return lb_set_tile(c, ty, zc);
                 }
             }
@@ -876,17 +919,22 @@ int lb_tune(lb_ctx* c, int steps) {
     // median of TUNE_WINDOWS windows.  The pick is the first candidate whose
     // median is within TUNE_TIE of the fastest, so shapes that time alike do
     // not trade places from run to run on noise.
+    // With a 16-bit storage the paired kernel's shapes (tile heights 8, 16, 4)
+    // come first, then the one-site kernel's.
     constexpr int TUNE_WINDOWS = 5;
     constexpr float TUNE_TIE = 0.01f;
-    const int tys[2] = {8, 4};
-    int cand_ty[12], cand_zc[12];
-    float cand_ms[12];
+    const bool try_pair = pair_applies(s);
+    const int kinds[5][2] = {{1, 8}, {1, 16}, {1, 4}, {0, 8}, {0, 4}};  // (paired, tile height)
+    int cand_ty[30], cand_zc[30], cand_pr[30];
+    float cand_ms[30];
     int ncand = 0;
-    for (int a = 0; a < 2 && rc == LB_OK; ++a) {
+    for (int a = 0; a < 5 && rc == LB_OK; ++a) {
+        if (kinds[a][0] && !try_pair) continue;
+        s->pair = kinds[a][0] != 0;
         int zcs[6];
-        const int nzc = tune_chunks(s, tys[a], zcs);
+        const int nzc = tune_chunks(s, kinds[a][1], zcs);
         for (int b = 0; b < nzc && rc == LB_OK; ++b) {
-            if (lb_set_tile(s, tys[a], zcs[b]) != LB_OK) continue;
+            if (lb_set_tile(s, kinds[a][1], zcs[b]) != LB_OK) continue;
             if (lb_step(s, 2) != LB_OK) {  // warm-up and graph capture; skip shapes that fail
                 cudaGetLastError();
                 continue;
@@ -909,15 +957,16 @@ int lb_tune(lb_ctx* c, int steps) {
                     win[j] = win[j - 1];
                     win[j - 1] = t;
                 }
-            cand_ty[ncand] = tys[a];
+            cand_ty[ncand] = kinds[a][1];
             cand_zc[ncand] = zcs[b];
+            cand_pr[ncand] = kinds[a][0];
             cand_ms[ncand] = win[nwin / 2];
             ++ncand;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    int bty = c->ty, bzc = c->zc;
+    int bty = c->ty, bzc = c->zc, bpr = c->pair ? 1 : 0;
     if (ncand > 0) {
         float best = cand_ms[0];
         for (int k = 1; k < ncand; ++k) best = cand_ms[k] < best ? cand_ms[k] : best;
@@ -925,6 +974,7 @@ int lb_tune(lb_ctx* c, int steps) {
             if (cand_ms[k] <= best * (1.f + TUNE_TIE)) {
                 bty = cand_ty[k];
                 bzc = cand_zc[k];
+                bpr = cand_pr[k];
                 break;
             }
     }
@@ -941,10 +991,11 @@ int lb_tune(lb_ctx* c, int steps) {
     if (cache) {
         FILE* fp = fopen(cache, "a");
         if (fp) {
-            fprintf(fp, "%s %d %d\n", key, bty, bzc);
+            fprintf(fp, "%s %d %d %d\n", key, bty, bzc, bpr);
             fclose(fp);
         }
     }
+    c->pair = bpr != 0 && pair_applies(c);
     return lb_set_tile(c, bty, bzc);
 }
 

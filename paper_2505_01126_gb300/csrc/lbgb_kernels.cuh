@@ -102,13 +102,21 @@ struct Codec;
 
 // ldr loads the stored value as is and dec widens it to FP32, so that a load
 // can be issued well ahead of the conversion that waits for it.
+// The pair members serve the paired kernel (two x-adjacent sites per thread):
+// raw2 holds both sites' stored values of one direction, ldr2/st2 access an
+// aligned pair (even first site), pack joins two single loads.
 template <>
 struct Codec<float> {
     using raw = float;
+    using raw2 = float2;
     static __device__ __forceinline__ raw ldr(const float* p) { return *p; }
     static __device__ __forceinline__ float dec(raw r) { return r; }
     static __device__ __forceinline__ float ld(const float* p) { return *p; }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+    static __device__ __forceinline__ raw2 ldr2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+    static __device__ __forceinline__ raw2 pack(raw a, raw b) { return make_float2(a, b); }
+    static __device__ __forceinline__ float2 dec2(raw2 r) { return r; }
+    static __device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
 };
 
 template <>
@@ -118,6 +126,13 @@ struct Codec<__half> {
     static __device__ __forceinline__ float dec(raw r) { return __half2float(r); }
     static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+    using raw2 = __half2;
+    static __device__ __forceinline__ raw2 ldr2(const __half* p) { return *reinterpret_cast<const __half2*>(p); }
+    static __device__ __forceinline__ raw2 pack(raw a, raw b) { return __halves2half2(a, b); }
+    static __device__ __forceinline__ float2 dec2(raw2 r) { return __half22float2(r); }
+    static __device__ __forceinline__ void st2(__half* p, float2 v) {
+        *reinterpret_cast<__half2*>(p) = __float22half2_rn(v);
+    }
 };
 
 template <>
@@ -127,6 +142,15 @@ struct Codec<__nv_bfloat16> {
     static __device__ __forceinline__ float dec(raw r) { return __bfloat162float(r); }
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+    using raw2 = __nv_bfloat162;
+    static __device__ __forceinline__ raw2 ldr2(const __nv_bfloat16* p) {
+        return *reinterpret_cast<const __nv_bfloat162*>(p);
+    }
+    static __device__ __forceinline__ raw2 pack(raw a, raw b) { return __halves2bfloat162(a, b); }
+    static __device__ __forceinline__ float2 dec2(raw2 r) { return __bfloat1622float2(r); }
+    static __device__ __forceinline__ void st2(__nv_bfloat16* p, float2 v) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v);
+    }
 };
 
 __device__ __forceinline__ int wrap_mod(int v, int n) {
@@ -326,6 +350,136 @@ __host__ __device__ __forceinline__ void collide_site(float pp, float m0, float 
     quad_poly27(e0, Pp, Pm, Xxy, Xxz, Xyz, v);
 }
 
+// ---------------------------------------------- two sites per thread (PAIR)
+// The 16-bit storages are bound by instruction issue, not HBM.  Their paired
+// kernel gives each thread two x-adjacent sites and evaluates every per-site
+// formula for both at once with sm_100's packed two-lane FP32 instructions
+// (FADD2, FMUL2, FFMA2: one instruction, two IEEE-rounded FP32 results), so
+// the arithmetic takes half the issue slots.  .x is the even site, .y the odd.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b, as b * (-1) + a: the product is exact, so this is the rounded difference
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// shifted_moments for a pair of sites (the same separable sums).
+__device__ __forceinline__ void shifted_moments2(const float2 (&d)[27], float2& pp, float2& m0, float2& m1,
+                                                 float2& m2, float2& P00, float2& P11, float2& P22, float2& P01,
+                                                 float2& P02, float2& P12) {
+    const float2 four = f2(4.f);
+    float2 A0[3][3], A1[3][3], A2[3][3];
+#pragma unroll
+    for (int cy = 0; cy < 3; ++cy)
+#pragma unroll
+        for (int cx = 0; cx < 3; ++cx) {
+            const int b = cx + 3 * cy;
+            const float2 s = add2(d[b], d[b + 18]);
+            A2[cy][cx] = s;
+            A0[cy][cx] = fma2(four, d[b + 9], s);
+            A1[cy][cx] = sub2(d[b + 18], d[b]);
+        }
+    float2 B00[3], B01[3], B02[3], B10[3], B11[3], B20[3];
+#pragma unroll
+    for (int cx = 0; cx < 3; ++cx) {
+        const float2 s0 = add2(A0[0][cx], A0[2][cx]);
+        B00[cx] = fma2(four, A0[1][cx], s0);
+        B02[cx] = s0;
+        B01[cx] = sub2(A0[2][cx], A0[0][cx]);
+        B10[cx] = fma2(four, A1[1][cx], add2(A1[0][cx], A1[2][cx]));
+        B11[cx] = sub2(A1[2][cx], A1[0][cx]);
+        B20[cx] = fma2(four, A2[1][cx], add2(A2[0][cx], A2[2][cx]));
+    }
+    const float2 k = f2(1.f / 216.f);
+    const float2 t = add2(B00[0], B00[2]);
+    pp = mul2(fma2(four, B00[1], t), k);
+    m0 = mul2(sub2(B00[2], B00[0]), k);
+    P00 = mul2(t, k);
+    m1 = mul2(fma2(four, B01[1], add2(B01[0], B01[2])), k);
+    P01 = mul2(sub2(B01[2], B01[0]), k);
+    P11 = mul2(fma2(four, B02[1], add2(B02[0], B02[2])), k);
+    m2 = mul2(fma2(four, B10[1], add2(B10[0], B10[2])), k);
+    P02 = mul2(sub2(B10[2], B10[0]), k);
+    P12 = mul2(fma2(four, B11[1], add2(B11[0], B11[2])), k);
+    P22 = mul2(fma2(four, B20[1], add2(B20[0], B20[2])), k);
+}
+
+// quad_poly27 for a pair of sites.
+__device__ __forceinline__ void quad_poly27_2(float2 e0, const float2 (&Pp)[3], const float2 (&Pm)[3], float2 Xxy,
+                                              float2 Xxz, float2 Xyz, float2 (&v)[27]) {
+    v[IDX(0, 0, 0)] = e0;
+    const float2 fxp = add2(e0, Pp[0]), fxm = add2(e0, Pm[0]);
+    const float2 fyp = add2(e0, Pp[1]), fym = add2(e0, Pm[1]);
+    v[IDX(1, 0, 0)] = fxp;
+    v[IDX(-1, 0, 0)] = fxm;
+    v[IDX(0, 1, 0)] = fyp;
+    v[IDX(0, -1, 0)] = fym;
+    v[IDX(0, 0, 1)] = add2(e0, Pp[2]);
+    v[IDX(0, 0, -1)] = add2(e0, Pm[2]);
+    const float2 epp = add2(fxp, add2(Pp[1], Xxy)), epm = add2(fxp, sub2(Pm[1], Xxy));
+    const float2 emp = add2(fxm, sub2(Pp[1], Xxy)), emm = add2(fxm, add2(Pm[1], Xxy));
+    v[IDX(1, 1, 0)] = epp;
+    v[IDX(1, -1, 0)] = epm;
+    v[IDX(-1, 1, 0)] = emp;
+    v[IDX(-1, -1, 0)] = emm;
+    v[IDX(1, 0, 1)] = add2(fxp, add2(Pp[2], Xxz));
+    v[IDX(1, 0, -1)] = add2(fxp, sub2(Pm[2], Xxz));
+    v[IDX(-1, 0, 1)] = add2(fxm, sub2(Pp[2], Xxz));
+    v[IDX(-1, 0, -1)] = add2(fxm, add2(Pm[2], Xxz));
+    v[IDX(0, 1, 1)] = add2(fyp, add2(Pp[2], Xyz));
+    v[IDX(0, 1, -1)] = add2(fyp, sub2(Pm[2], Xyz));
+    v[IDX(0, -1, 1)] = add2(fym, sub2(Pp[2], Xyz));
+    v[IDX(0, -1, -1)] = add2(fym, add2(Pm[2], Xyz));
+    const float2 Vpp = add2(Xxz, Xyz), Vpm = sub2(Xxz, Xyz);
+    v[IDX(1, 1, 1)] = add2(epp, add2(Pp[2], Vpp));
+    v[IDX(1, 1, -1)] = add2(epp, sub2(Pm[2], Vpp));
+    v[IDX(1, -1, 1)] = add2(epm, add2(Pp[2], Vpm));
+    v[IDX(1, -1, -1)] = add2(epm, sub2(Pm[2], Vpm));
+    v[IDX(-1, 1, 1)] = add2(emp, sub2(Pp[2], Vpm));
+    v[IDX(-1, 1, -1)] = add2(emp, add2(Pm[2], Vpm));
+    v[IDX(-1, -1, 1)] = add2(emm, sub2(Pp[2], Vpp));
+    v[IDX(-1, -1, -1)] = add2(emm, add2(Pm[2], Vpp));
+}
+
+// collide_site for a pair of sites: steps 8-10 (inv = 1/(1 - A/2) and the
+// relaxation rate are the same for both).
+__device__ __forceinline__ void collide_pair(float2 pp, float2 m0, float2 m1, float2 m2, float2 P00, float2 P11,
+                                             float2 P22, float2 P01, float2 P02, float2 P12, float2 Fe0, float2 Fe1,
+                                             float2 Fe2, float A_lin, float inv_s, float omega, float2& u0,
+                                             float2& u1, float2& u2, float2& aa, float2 (&v)[27]) {
+    const float2 half = f2(0.5f), inv = f2(inv_s), A = f2(A_lin);
+    u0 = mul2(fma2(half, Fe0, m0), inv);
+    u1 = mul2(fma2(half, Fe1, m1), inv);
+    u2 = mul2(fma2(half, Fe2, m2), inv);
+    const float2 F0 = fma2(A, u0, Fe0), F1 = fma2(A, u1, Fe1), F2 = fma2(A, u2, Fe2);
+    // a2 = Pi - p*/3 I - u u + (u F + F u)/2, with Pi - p*/3 I = P' - p'/3 I
+    const float2 p3 = mul2(pp, f2(1.f / 3.f));
+    const float2 a00 = fma2(u0, sub2(F0, u0), sub2(P00, p3));
+    const float2 a11 = fma2(u1, sub2(F1, u1), sub2(P11, p3));
+    const float2 a22 = fma2(u2, sub2(F2, u2), sub2(P22, p3));
+    const float2 a01 = fma2(half, fma2(u0, F1, mul2(F0, u1)), fma2(mul2(u0, f2(-1.f)), u1, P01));
+    const float2 a02 = fma2(half, fma2(u0, F2, mul2(F0, u2)), fma2(mul2(u0, f2(-1.f)), u2, P02));
+    const float2 a12 = fma2(half, fma2(u1, F2, mul2(F1, u2)), fma2(mul2(u1, f2(-1.f)), u2, P12));
+    const float2 offd = fma2(a01, a01, fma2(a02, a02, mul2(a12, a12)));
+    aa = fma2(f2(2.f), offd, fma2(a00, a00, fma2(a11, a11, mul2(a22, a22))));
+    const float2 om1 = f2(1.f - omega);
+    const float2 B00 = fma2(om1, a00, mul2(u0, u0)), B11 = fma2(om1, a11, mul2(u1, u1));
+    const float2 B22 = fma2(om1, a22, mul2(u2, u2)), B01 = fma2(om1, a01, mul2(u0, u1));
+    const float2 B02 = fma2(om1, a02, mul2(u0, u2)), B12 = fma2(om1, a12, mul2(u1, u2));
+    const float2 uF = fma2(u0, F0, fma2(u1, F1, mul2(u2, F2)));
+    const float2 e0 = fma2(f2(-1.5f), add2(add2(B00, B11), add2(B22, uF)), pp);
+    const float2 L0 = fma2(f2(1.5f), F0, mul2(f2(3.f), u0)), L1 = fma2(f2(1.5f), F1, mul2(f2(3.f), u1));
+    const float2 L2 = fma2(f2(1.5f), F2, mul2(f2(3.f), u2));
+    const float2 Q0 = mul2(f2(4.5f), fma2(u0, F0, B00)), Q1 = mul2(f2(4.5f), fma2(u1, F1, B11));
+    const float2 Q2 = mul2(f2(4.5f), fma2(u2, F2, B22));
+    const float2 Pp[3] = {add2(Q0, L0), add2(Q1, L1), add2(Q2, L2)};
+    const float2 Pm[3] = {sub2(Q0, L0), sub2(Q1, L1), sub2(Q2, L2)};
+    const float2 Xxy = fma2(f2(9.f), B01, mul2(f2(4.5f), fma2(u0, F1, mul2(u1, F0))));
+    const float2 Xxz = fma2(f2(9.f), B02, mul2(f2(4.5f), fma2(u0, F2, mul2(u2, F0))));
+    const float2 Xyz = fma2(f2(9.f), B12, mul2(f2(4.5f), fma2(u1, F2, mul2(u2, F1))));
+    quad_poly27_2(e0, Pp, Pm, Xxy, Xxz, Xyz, v);
+}
+
 // Density and viscosity contrasts (Sec. 2.3), per site, from phi, grad phi,
 // the shifted moments (p' = p* - 1, m, P' = Pi - I/3) and the force density
 // F = F^s + F^ext:
@@ -425,8 +579,13 @@ __device__ __forceinline__ void pull_column(LD ld, float& vm, float& v0, float& 
 // PF: the phase field is a stored field (one plane, gin[0]) advanced by the
 // finite-difference step of lbgb_weno.cu; this kernel then reads phi from it
 // and writes u (gout[0..2]) instead of the D3Q7 update (INIT: copies phi).
-template <class FT, int TY, int MODE, int PAR, bool VEC, bool MC = false, bool VD = false, bool PF = false>
-__global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 512 / (32 * TY)))
+// PAIR: the paired kernel of the 16-bit AA step (16 TY threads, two sites each;
+// nx a multiple of 4); its tiles with TY = 8 fit three blocks per SM in
+// registers and shared memory.
+template <class FT, int TY, int MODE, int PAR, bool VEC, bool MC = false, bool VD = false, bool PF = false,
+          bool PAIR = false>
+__global__ void __launch_bounds__(PAIR ? 16 * TY : 32 * TY,
+                                  PAIR ? (TY == 4 ? 4 : TY == 8 ? 3 : 1) : (TY >= 16 ? 1 : 512 / (32 * TY)))
 fused_step_kernel(const StepArgs a) {
 #define TILE_BX blockIdx.x
 #define TILE_BY blockIdx.y
@@ -519,6 +678,7 @@ batch_step_kernel(const __grid_constant__ BatchArgs b) {
             constexpr bool MC = MC_;
             constexpr bool VD = false;
             constexpr bool PF = false;
+            constexpr bool PAIR = false;
 #define TILE_BX tbx
 #define TILE_BY tby
 #define TILE_BZ tbz
@@ -559,6 +719,14 @@ int batch_blocks_per_sm(int ty, bool vec);
 // vec selects the float4 phase-A loads (requires nx % 4 == 0).
 template <class FT>
 cudaError_t launch_fused(int mode, int parity, int ty, bool vec, dim3 grid, const StepArgs& a, cudaStream_t st);
+
+// The paired step kernel of a 16-bit storage (__half or __nv_bfloat16): tile
+// height ty in {4, 8, 16} (16 ty threads per block), nx % 4 == 0, MODE_STEP.
+// Defined in lbgb_step_pair_*.cu.
+template <class FT>
+cudaError_t launch_fused_pair(int parity, int ty, dim3 grid, const StepArgs& a, cudaStream_t st);
+template <class FT>
+int fused_pair_blocks_per_sm(int ty);
 
 // The same kernels with the density and viscosity contrasts (VD) and/or the
 // phase field as a stored field (PF), mode STEP or MOMENTS (and INIT for PF

@@ -42,7 +42,7 @@ EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_step", "lb_moments", "lb
            "lb_batch_step", "lb_batch_moments", "lb_batch_diagnostics", "lb_batch_set_tile", "lb_batch_get_tile",
            "lb_batch_tune", "lb_batch_sites", "lb_batch_time", "lb_batch_destroy", "lb_velocity_statistics",
            "lb_spectrum", "lb_state_bytes", "lb_save", "lb_load", "lb_set_density", "lb_set_gravity",
-           "lb_set_phase_solver"]
+           "lb_set_phase_solver", "lb_measure_fp32_peak", "lb_set_pairing", "lb_get_pairing"]
 
 
 def _load():
@@ -101,6 +101,9 @@ def _load():
     lib.lb_set_gravity.argtypes = [vp, d, d, d, d]
     lib.lb_set_phase_solver.argtypes = [vp, i]
     lib.lb_load.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.lb_measure_fp32_peak.argtypes = [vp, dp_]
+    lib.lb_set_pairing.argtypes = [vp, i]
+    lib.lb_get_pairing.argtypes = [vp, ctypes.POINTER(i)]
     return lib
 
 
@@ -158,6 +161,15 @@ def field_stats_static(phi, u, stream=None) -> np.ndarray:
         raise LBError(rc, _lib.lb_last_error().decode())
     _check(rc)
     return np.array(list(out))
+
+
+def measure_fp32_peak(stream=None) -> dict:
+    """The device's measured FP32 FMA throughput (lb_measure_fp32_peak)."""
+    handle = getattr(stream, "cuda_stream", stream)
+    out = (ctypes.c_double * 6)()
+    _check(_lib.lb_measure_fp32_peak(ctypes.c_void_p(int(handle) if handle else 0), out))
+    return {"fp32_flops": out[0], "warp_inst_per_s": out[1], "ms": out[2], "sm_mhz": out[3],
+            "fp32_flops_paired": out[4], "paired_warp_inst_per_s": out[5]}
 
 
 def velocity_statistics(u, rmax: int = 0, nbins: int = 0, range_: float = 8.0, scale: float = 0.0, stream=None):
@@ -294,6 +306,16 @@ class Box:
     def tune(self, steps: int = 3):
         _check(_lib.lb_tune(self._h, int(steps)))
         return self.tile()
+
+    def set_pairing(self, on: bool):
+        """The paired step kernel (two sites per thread) for FP16/BF16 storage (lb_set_pairing)."""
+        _check(_lib.lb_set_pairing(self._h, 1 if on else 0))
+
+    @property
+    def paired(self) -> bool:
+        v = ctypes.c_int()
+        _check(_lib.lb_get_pairing(self._h, ctypes.byref(v)))
+        return bool(v.value)
 
     @property
     def bytes_per_site(self) -> float:

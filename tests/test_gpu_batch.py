@@ -5,7 +5,8 @@ Every box is computed by the same per-tile code as a single box, so after any
 number of steps its fields (and FP64 reductions) must equal, bit for bit,
 those of the single-box path with the same tile shape.  Together with the
 single-box parity tests against the FP64 oracle, this carries the oracle
-parity over to every box of a batch.
+parity over to every box of a batch; test_batch_boxes_match_the_oracle also
+compares every box of a batch with its own oracle directly.
 """
 import math
 
@@ -60,6 +61,7 @@ def test_batch_boxes_equal_single_boxes(lbgb, dims, storage):
     assert batch.time == 7
     for k, (d, (phi, u)) in enumerate(zip(dims, fields)):
         box = lbgb.Box(*d, tau[k], 0.1, 3.0, sigma[k], storage=storage)
+        box.set_pairing(False)  # the batch runs the one-site tile body
         box.set_tile(4, 16)
         box.init(phi, u)
         box.step(7)
@@ -67,6 +69,39 @@ def test_batch_boxes_equal_single_boxes(lbgb, dims, storage):
             assert np.array_equal(a, b), (k, d)
         np.testing.assert_array_equal(box.diagnostics()[:4], batch.diagnostics(k)[:4])
         box.close()
+    batch.close()
+
+
+@pytest.mark.parametrize("dims", [
+    [(32, 24, 20), (24, 24, 24), (16, 40, 12), (8, 8, 8), (48, 16, 9)],     # every nx % 4 == 0: float4 phase A
+    [(32, 24, 20), (37, 13, 11), (24, 24, 24), (13, 9, 30), (5, 7, 3)],     # ragged nx: per-site phase A
+])
+@pytest.mark.parametrize("storage", ["f32", "moments"])
+def test_batch_boxes_match_the_oracle(lbgb, orc, dims, storage):
+    """Five boxes of uneven sizes with their own tau and sigma, advanced 50 steps
+    by the persistent batch kernel (graph pairs and a last single step), each
+    against its own FP64 oracle: max|delta| <= 1e-5 in p*, u and phi, and the
+    per-box FP64 reductions within the bounds the field error gives."""
+    from test_gpu_parity import TOL, check_diagnostics, max_err
+
+    tau = [0.8, 1.0, 0.6, 0.9, 0.7]
+    sigma = [0.01, 0.005, 0.02, 0.015, 0.01]
+    fields = [box_fields(*d, seed=20 + k) for k, d in enumerate(dims)]
+    batch = lbgb.Batch(dims, tau, 0.1, 3.0, sigma, storage=storage)
+    for k, (phi, u) in enumerate(fields):
+        batch.init(k, phi, u)
+    batch.step(49)
+    batch.step(1)
+    assert batch.time == 50
+    for k, (d, (phi, u)) in enumerate(zip(dims, fields)):
+        o = orc.Oracle(*d, tau[k], 0.1, 3.0, sigma[k])
+        o.init(phi.astype(np.float64), u.astype(np.float64))
+        o.step(50)
+        e = max_err(batch.moments_numpy(k), o.moments())
+        assert max(e) <= TOL, (k, d, e)
+        dg, do = batch.diagnostics(k), o.diagnostics()
+        check_diagnostics(dg, do, int(np.prod(d)), field_err=max(e), tau=tau[k])
+        o.close()
     batch.close()
 
 

@@ -1,0 +1,118 @@
+"""The benchmark's own box: 512^3 bubble-laden forced HIT (256 bubbles R = 12,
+seed 3, tau 0.51), FP32 storage, in the launch shape the tuner picks for it.
+
+The oracle cannot run this box for many steps, so parity is checked on
+sampled outputs the oracle can compute one by one.  Without the linear
+forcing (whose amplitude is a reduction over the whole box) a site's fields
+after two steps depend only on the inputs within 9 sites of it: the initial
+normal reads phi at radius 1, each step reads the state at radius 3 (one
+streaming hop of the populations of sites whose curvature reads phi at
+radius 2), and the moments at t = 2 read phi at radius 2 for the curvature in
+the forced velocity.  A periodic 24^3 window of the inputs centred on a site
+keeps its seam 12 sites away, so the oracle on that window gives the site's
+exact fields.  Two steps cover both AA parities.  Over 50 steps with the
+forcing on, the box is checked by properties: finite fields and reductions,
+the phase mass conserved to FP32 rounding, and the controller holding the
+kinetic energy.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import bench
+from paper_2505_01126_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+WIN = 24
+
+
+@pytest.fixture(scope="module")
+def lbgb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_01126_gb300 import build
+
+    build.build()
+    from paper_2505_01126_gb300 import lbgb as mod
+
+    return mod
+
+
+@pytest.fixture(scope="module")
+def workload():
+    import torch
+
+    w, nb = bench.preset_workload("hit512")
+    phi, u = w.phi.cpu().numpy(), w.u.cpu().numpy()
+    del w.phi, w.u
+    torch.cuda.empty_cache()
+    return w, phi, u
+
+
+def tuned_box(lbgb, w, n, force):
+    os.environ.setdefault("LBGB_TUNE_CACHE", os.path.join(bench.ROOT, "paper_2505_01126_gb300", "tune_cache.txt"))
+    b = lbgb.Box(n, n, n, w.tau, w.M, w.W, w.sigma, force=force, storage="f32")
+    b.tune(8)
+    return b
+
+
+def sample_sites(n, zc, count, seed):
+    """Random sites plus sites on the box faces and on z-chunk and tile boundaries."""
+    rng = np.random.default_rng(seed)
+    pts = [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(count)]
+    for z in (0, zc - 1, zc, n - 1):
+        for x, y in ((0, 0), (31, 7), (32, 8), (n - 1, n - 1), (n // 2, 3)):
+            pts.append((x % n, y % n, z % n))
+    return pts
+
+
+def window(a, x, y, z, n):
+    """Periodic WIN^3 window of a (..., n, n, n) field centred on (x, y, z)."""
+    h = WIN // 2
+    ix, iy, iz = [np.arange(c - h, c - h + WIN) % n for c in (x, y, z)]
+    return a[..., iz[:, None, None], iy[None, :, None], ix[None, None, :]]
+
+
+def test_bench_box_two_steps_against_windowed_oracle(lbgb, orc, workload):
+    w, phi, u = workload
+    n = phi.shape[0]
+    b = tuned_box(lbgb, w, n, None)
+    ty, zc = b.tile()
+    b.init(phi, u)
+    b.step(2)
+    got = b.moments_numpy()
+    b.close()
+    worst = 0.0
+    for (x, y, z) in sample_sites(n, zc, 96, seed=17):
+        o = orc.Oracle(WIN, WIN, WIN, w.tau, w.M, w.W, w.sigma)
+        o.init(window(phi, x, y, z, n).astype(np.float64), window(u, x, y, z, n).astype(np.float64))
+        o.step(2)
+        rho_o, u_o, phi_o = o.moments()
+        o.close()
+        c = WIN // 2
+        diffs = [abs(float(got[0][z, y, x]) - rho_o[c, c, c]), abs(float(got[2][z, y, x]) - phi_o[c, c, c])]
+        diffs += [abs(float(got[1][a, z, y, x]) - u_o[a, c, c, c]) for a in range(3)]
+        worst = max(worst, max(diffs))
+        assert max(diffs) <= TOL, ((x, y, z), diffs, (ty, zc))
+    assert worst > 0.0  # the check compares something
+
+
+def test_bench_box_fifty_forced_steps_properties(lbgb, workload):
+    w, phi, u = workload
+    n = phi.shape[0]
+    b = tuned_box(lbgb, w, n, lbgb.Force(kind=lbgb.LB_FORCE_LINEAR, T_relax=w.T_relax))
+    b.init(phi, u)
+    d0 = b.diagnostics()
+    b.step(50)
+    d = b.diagnostics()
+    rho, uu, ph = b.moments_numpy()
+    b.close()
+    assert np.isfinite(d).all() and np.isfinite(rho).all() and np.isfinite(uu).all() and np.isfinite(ph).all()
+    assert abs(d[0] / d0[0] - 1) < 1e-6          # phase mass, FP32 storage rounding only
+    assert abs(d[1] / d0[1] - 1) < 0.05          # K held by the controller (T_relax = 100 steps)
+    assert abs(float(rho.astype(np.float64).mean()) - 1.0) < 1e-6   # sum p* conserved
