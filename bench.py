@@ -498,6 +498,7 @@ def run_box(args, lbgb, torch, w, storage: str, force, rank: int, world: int, pg
     elif not args.no_tune:
         box.tune(8)
     ty, zc = box.tile()
+    paired = box.paired if storage in ("f16", "bf16") else False
     phi_d = w.phi if torch.is_tensor(w.phi) else torch.from_numpy(w.phi).cuda()
     if args.density and not droplet:
         phi_d = 1.0 - phi_d  # gas bubbles: phi = 0 inside
@@ -556,7 +557,8 @@ def run_box(args, lbgb, torch, w, storage: str, force, rank: int, world: int, pg
     key = storage + ("+density" if args.density else "") + ("+weno5" if args.phase != "lb" else "")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": measured_traffic(key, N, [32, ty, zc]),
-            "kernel": "fused_step_kernel" + (" (VD)" if args.density else "") + (" (PF)" if args.phase != "lb" else ""),
+            "kernel": "fused_step_kernel" + (" (VD)" if args.density else "") + (" (PF)" if args.phase != "lb" else "")
+                      + (" (paired: two sites per thread)" if paired else ""),
             "bytes_per_site": bps, "kernel_ms_avg": kern_avg_s * 1e3, "peak_source": peak_kind}
     if args.phase == "lb" and not args.density and storage in SURVEY_BYTES:
         # the same kernel time against the survey's count, which adds 8 B/site for
@@ -568,6 +570,7 @@ def run_box(args, lbgb, torch, w, storage: str, force, rank: int, world: int, pg
         roof["other_kernels_ms_per_step"] = t_max / args.steps - kern_avg_s * 1e3
         roof["other_kernels_bytes_per_site"] = 3 * (4 + 12 + 4) + 2 * 4
     return {"storage": storage, "value": value, "ms_per_step": t_max / args.steps, "tile": [32, ty, zc],
+            "paired": paired,
             "roofline": roof, "clocks": clk, "gpu_launches": launches, "rho_ref": rho_ref,
             "l2": "inputs larger than L2 (populations %.2f GB), no flush" % (bps * N / 2 / 1e9),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * N * 4 / args.steps,
@@ -720,7 +723,7 @@ def main():
                 "roofline": main_run["roofline"], "cpu_baseline": cpu, "e2e": main_run["e2e"],
                 "clocks": main_run["clocks"], "gpu_launches": main_run["gpu_launches"]}
         if compare is not None:
-            line["storage16"] = {k: compare[k] for k in ("storage", "value", "ms_per_step", "tile", "roofline",
+            line["storage16"] = {k: compare[k] for k in ("storage", "value", "ms_per_step", "tile", "paired", "roofline",
                                                          "e2e", "clocks", "gpu_launches", "diagnostics")}
             line["storage16"]["speedup_vs_f32"] = compare["value"] / main_run["value"]
             line["storage16"]["errors"] = errors[args.compare] if errors else None

@@ -202,8 +202,7 @@ int lb_sync(lb_ctx* ctx);
 long long lb_time(const lb_ctx* ctx);
 
 /* Launch shape of the fused step kernel: tile height ty (x tile is 32 sites)
- * in {4, 8} (and 16 while the paired kernel runs the step, see
- * lb_set_pairing) and z-chunk zc >= 1 planes per block.  Takes effect at the
+ * in {4, 8} and z-chunk zc >= 1 planes per block.  Takes effect at the
  * next lb_step; lb_tune picks it by measurement. */
 int lb_set_tile(lb_ctx* ctx, int ty, int zc);
 int lb_get_tile(const lb_ctx* ctx, int* ty, int* zc);
@@ -221,9 +220,8 @@ int lb_get_tile(const lb_ctx* ctx, int* ty, int* zc);
  * formulas in FP32; their results agree to FP32 rounding, not bit for bit.
  * The paired kernel applies to FP16/BF16 storage with nx % 4 == 0, the D3Q7
  * phase field and no density contrasts; lb_set_density and
- * lb_set_phase_solver(LB_PHASE_WENO5) switch back to the one-site kernel
- * (a tile height of 16 becomes 8).  lb_get_pairing reports whether the paired
- * kernel runs the step.
+ * lb_set_phase_solver(LB_PHASE_WENO5) switch back to the one-site kernel.
+ * lb_get_pairing reports whether the paired kernel runs the step.
  * Errors: LB_EINVAL for on = 1 where the paired kernel does not apply.
  */
 int lb_set_pairing(lb_ctx* ctx, int on);
@@ -233,7 +231,7 @@ int lb_get_pairing(const lb_ctx* ctx, int* on);
  * lb_tune -- time tile heights ty in {8, 4} with z-chunks zc in {16, 32, 64,
  * 128} and the two chunkings whose block count best fills the last wave of
  * resident blocks (with FP16/BF16 storage first the paired kernel's heights
- * 8, 16, 4, then the one-site kernel's), each as the median of five windows of
+ * 8, 4, then the one-site kernel's), each as the median of five windows of
  * 2*steps steps, and keep the first shape in that order whose median is within
  * 1% of the fastest (so shapes that time alike do not trade places on noise).  Before lb_init it times on the context's own
  * arrays, so the timed launches have the real box's block counts, and leaves

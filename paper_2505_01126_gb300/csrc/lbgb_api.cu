@@ -350,11 +350,10 @@ int ensure_stage(lb_ctx* c) {
     return LB_OK;
 }
 
-// Tile heights: {4, 8} for the one-site-per-thread kernels, {4, 8, 16} for the
-// paired kernel.
+// Tile heights: {4, 8} for both the one-site and the paired kernels.
 int check_tile(int ty, int zc, bool pair = false) {
-    if (ty != 4 && ty != 8 && !(pair && ty == 16))
-        return fail(LB_EINVAL, "tile height %d not in {4, 8%s}", ty, pair ? ", 16" : "");
+    (void)pair;
+    if (ty != 4 && ty != 8) return fail(LB_EINVAL, "tile height %d not in {4, 8}", ty);
     if (zc < 1) return fail(LB_EINVAL, "z chunk %d < 1", zc);
     return LB_OK;
 }
@@ -658,7 +657,6 @@ int lb_set_density(lb_ctx* c, double rho_l, double rho_g, double tau_l, double t
                     tau_l, tau_g);
     c->vd = true;
     c->rho_l = rho_l; c->rho_g = rho_g; c->tau_l = tau_l; c->tau_g = tau_g;
-    if (c->ty == 16) c->ty = 8;  // the contrast kernels are one site per thread
     drop_graph(c);  // the captured launches carry the old kernel and arguments
     return LB_OK;
 }
@@ -669,7 +667,6 @@ int lb_set_phase_solver(lb_ctx* c, int solver) {
     if (c->initialized && (solver == LB_PHASE_WENO5) != c->fd)
         return fail(LB_ESTATE, "lb_set_phase_solver after lb_init (the state is held differently)");
     c->fd = solver == LB_PHASE_WENO5;
-    if (c->fd && c->ty == 16) c->ty = 8;
     drop_graph(c);
     return LB_OK;
 }
@@ -721,7 +718,6 @@ int lb_set_pairing(lb_ctx* c, int on) {
         return fail(LB_EINVAL, "the paired step kernel needs FP16 or BF16 storage, nx %% 4 == 0, the D3Q7 phase "
                                "field and no density contrasts");
     c->pair = on != 0;
-    if (!c->pair && c->ty == 16) c->ty = 8;  // the one-site kernels have no 16-row tile
     return LB_OK;
 }
 
@@ -919,16 +915,16 @@ int lb_tune(lb_ctx* c, int steps) {
     // median of TUNE_WINDOWS windows.  The pick is the first candidate whose
     // median is within TUNE_TIE of the fastest, so shapes that time alike do
     // not trade places from run to run on noise.
-    // With a 16-bit storage the paired kernel's shapes (tile heights 8, 16, 4)
-    // come first, then the one-site kernel's.
+    // With a 16-bit storage the paired kernel's shapes (tile heights 8, 4) come
+    // first, then the one-site kernel's.
     constexpr int TUNE_WINDOWS = 5;
     constexpr float TUNE_TIE = 0.01f;
     const bool try_pair = pair_applies(s);
-    const int kinds[5][2] = {{1, 8}, {1, 16}, {1, 4}, {0, 8}, {0, 4}};  // (paired, tile height)
+    const int kinds[4][2] = {{1, 8}, {1, 4}, {0, 8}, {0, 4}};  // (paired, tile height)
     int cand_ty[30], cand_zc[30], cand_pr[30];
     float cand_ms[30];
     int ncand = 0;
-    for (int a = 0; a < 5 && rc == LB_OK; ++a) {
+    for (int a = 0; a < 4 && rc == LB_OK; ++a) {
         if (kinds[a][0] && !try_pair) continue;
         s->pair = kinds[a][0] != 0;
         int zcs[6];

@@ -580,12 +580,12 @@ __device__ __forceinline__ void pull_column(LD ld, float& vm, float& v0, float& 
 // finite-difference step of lbgb_weno.cu; this kernel then reads phi from it
 // and writes u (gout[0..2]) instead of the D3Q7 update (INIT: copies phi).
 // PAIR: the paired kernel of the 16-bit AA step (16 TY threads, two sites each;
-// nx a multiple of 4); its tiles with TY = 8 fit three blocks per SM in
-// registers and shared memory.
+// nx a multiple of 4).  Blocks per SM that fit in registers (168 per thread,
+// none spilled) and shared memory: six of TY = 4, three of TY = 8.
 template <class FT, int TY, int MODE, int PAR, bool VEC, bool MC = false, bool VD = false, bool PF = false,
           bool PAIR = false>
 __global__ void __launch_bounds__(PAIR ? 16 * TY : 32 * TY,
-                                  PAIR ? (TY == 4 ? 4 : TY == 8 ? 3 : 1) : (TY >= 16 ? 1 : 512 / (32 * TY)))
+                                  PAIR ? (TY == 4 ? 6 : 3) : (TY >= 16 ? 1 : 512 / (32 * TY)))
 fused_step_kernel(const StepArgs a) {
 #define TILE_BX blockIdx.x
 #define TILE_BY blockIdx.y
@@ -721,7 +721,7 @@ template <class FT>
 cudaError_t launch_fused(int mode, int parity, int ty, bool vec, dim3 grid, const StepArgs& a, cudaStream_t st);
 
 // The paired step kernel of a 16-bit storage (__half or __nv_bfloat16): tile
-// height ty in {4, 8, 16} (16 ty threads per block), nx % 4 == 0, MODE_STEP.
+// height ty in {4, 8} (16 ty threads per block), nx % 4 == 0, MODE_STEP.
 // Defined in lbgb_step_pair_*.cu.
 template <class FT>
 cudaError_t launch_fused_pair(int parity, int ty, dim3 grid, const StepArgs& a, cudaStream_t st);

@@ -18,7 +18,6 @@ cudaError_t launch_fused_pair<LBGB_FT>(int parity, int ty, dim3 grid, const Step
     switch (ty) {
         case 4: launch_pair_ty<LBGB_FT, 4>(parity, grid, a, st); break;
         case 8: launch_pair_ty<LBGB_FT, 8>(parity, grid, a, st); break;
-        case 16: launch_pair_ty<LBGB_FT, 16>(parity, grid, a, st); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -34,9 +33,6 @@ int fused_pair_blocks_per_sm<LBGB_FT>(int ty) {
     else if (ty == 8)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &n, fused_step_kernel<LBGB_FT, 8, MODE_STEP, 1, true, false, false, false, true>, 128, 0);
-    else if (ty == 16)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &n, fused_step_kernel<LBGB_FT, 16, MODE_STEP, 1, true, false, false, false, true>, 256, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;
