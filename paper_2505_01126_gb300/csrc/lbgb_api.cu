@@ -142,8 +142,9 @@ struct lb_ctx {
 
 namespace {
 
-dim3 grid_for(const lb_ctx* c, int ty, int zc) {
-    return dim3((unsigned)((c->nx + 31) / 32), (unsigned)((c->ny + ty - 1) / ty),
+// tx: tile width in sites (32; 64 for the paired kernel)
+dim3 grid_for(const lb_ctx* c, int ty, int zc, int tx = 32) {
+    return dim3((unsigned)((c->nx + tx - 1) / tx), (unsigned)((c->ny + ty - 1) / ty),
                 (unsigned)((c->nz + zc - 1) / zc));
 }
 
@@ -267,7 +268,7 @@ int enqueue_step(lb_ctx* c, int par, cudaStream_t s, bool first = false) {
     StepArgs a = base_args(c);
     a.zc = c->zc;
     set_g(a, c, par);
-    const dim3 grid = grid_for(c, c->ty, c->zc);
+    const dim3 grid = grid_for(c, c->ty, c->zc, use_pair(c) ? 64 : 32);
     const long long nblk = (long long)grid.x * grid.y * grid.z;
     if (nblk > c->npart_cap) return fail(LB_EINVAL, "tile (%d,%d) needs %lld partials > %lld", c->ty, c->zc, nblk, c->npart_cap);
     const bool timed = c->timing && s == c->stream;
@@ -392,7 +393,8 @@ int tune_chunks(const lb_ctx* c, int ty, int zcs[6]) {
     }
     const long long resident = (long long)sms * per_sm;
     if (resident <= 0) return n;
-    const long long tiles = (long long)((c->nx + 31) / 32) * ((c->ny + ty - 1) / ty);
+    const int tx = use_pair(c) ? 64 : 32;
+    const long long tiles = (long long)((c->nx + tx - 1) / tx) * ((c->ny + ty - 1) / ty);
     double fill[2] = {0.0, 0.0};
     int pick[2] = {0, 0};
     for (int nc = (c->nz + 127) / 128; nc <= c->nz / 24; ++nc) {

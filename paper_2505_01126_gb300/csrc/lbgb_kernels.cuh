@@ -579,13 +579,13 @@ __device__ __forceinline__ void pull_column(LD ld, float& vm, float& v0, float& 
 // PF: the phase field is a stored field (one plane, gin[0]) advanced by the
 // finite-difference step of lbgb_weno.cu; this kernel then reads phi from it
 // and writes u (gout[0..2]) instead of the D3Q7 update (INIT: copies phi).
-// PAIR: the paired kernel of the 16-bit AA step (16 TY threads, two sites each;
-// nx a multiple of 4).  Blocks per SM that fit in registers (168 per thread,
-// none spilled) and shared memory: six of TY = 4, three of TY = 8.
+// PAIR: the paired kernel of the 16-bit AA step (64 x TY tiles, 32 TY threads,
+// two sites each; nx a multiple of 4).  Blocks per SM that fit in registers
+// and shared memory: three of TY = 4 (168 registers, none spilled), two of
+// TY = 8.
 template <class FT, int TY, int MODE, int PAR, bool VEC, bool MC = false, bool VD = false, bool PF = false,
           bool PAIR = false>
-__global__ void __launch_bounds__(PAIR ? 16 * TY : 32 * TY,
-                                  PAIR ? (TY == 4 ? 6 : 3) : (TY >= 16 ? 1 : 512 / (32 * TY)))
+__global__ void __launch_bounds__(32 * TY, PAIR ? (TY == 4 ? 3 : 2) : (TY >= 16 ? 1 : 512 / (32 * TY)))
 fused_step_kernel(const StepArgs a) {
 #define TILE_BX blockIdx.x
 #define TILE_BY blockIdx.y
@@ -720,8 +720,9 @@ int batch_blocks_per_sm(int ty, bool vec);
 template <class FT>
 cudaError_t launch_fused(int mode, int parity, int ty, bool vec, dim3 grid, const StepArgs& a, cudaStream_t st);
 
-// The paired step kernel of a 16-bit storage (__half or __nv_bfloat16): tile
-// height ty in {4, 8} (16 ty threads per block), nx % 4 == 0, MODE_STEP.
+// The paired step kernel of a 16-bit storage (__half or __nv_bfloat16): tiles
+// of 64 x ty sites, ty in {4, 8} (32 ty threads per block), nx % 4 == 0,
+// MODE_STEP.
 // Defined in lbgb_step_pair_*.cu.
 template <class FT>
 cudaError_t launch_fused_pair(int parity, int ty, dim3 grid, const StepArgs& a, cudaStream_t st);

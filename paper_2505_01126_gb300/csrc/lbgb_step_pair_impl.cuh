@@ -9,8 +9,8 @@ namespace lbgb {
 
 template <class FT, int TY>
 static void launch_pair_ty(int parity, dim3 grid, const StepArgs& a, cudaStream_t st) {
-    if (parity == 0) fused_step_kernel<FT, TY, MODE_STEP, 0, true, false, false, false, true><<<grid, 16 * TY, 0, st>>>(a);
-    else fused_step_kernel<FT, TY, MODE_STEP, 1, true, false, false, false, true><<<grid, 16 * TY, 0, st>>>(a);
+    if (parity == 0) fused_step_kernel<FT, TY, MODE_STEP, 0, true, false, false, false, true><<<grid, 32 * TY, 0, st>>>(a);
+    else fused_step_kernel<FT, TY, MODE_STEP, 1, true, false, false, false, true><<<grid, 32 * TY, 0, st>>>(a);
 }
 
 template <>
@@ -29,10 +29,10 @@ int fused_pair_blocks_per_sm<LBGB_FT>(int ty) {
     cudaError_t e = cudaErrorInvalidValue;
     if (ty == 4)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &n, fused_step_kernel<LBGB_FT, 4, MODE_STEP, 1, true, false, false, false, true>, 64, 0);
+            &n, fused_step_kernel<LBGB_FT, 4, MODE_STEP, 1, true, false, false, false, true>, 128, 0);
     else if (ty == 8)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &n, fused_step_kernel<LBGB_FT, 8, MODE_STEP, 1, true, false, false, false, true>, 128, 0);
+            &n, fused_step_kernel<LBGB_FT, 8, MODE_STEP, 1, true, false, false, false, true>, 256, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;
