@@ -140,8 +140,8 @@ def whole_job(ms_local: float, sites_per_rank: int, steps: int, world: int, dist
 def measured_traffic(storage: str, n_sites: int, tile=None):
     """DRAM bytes per fused-kernel launch from the committed ncu record, scaled to
     n_sites, or None if the kernel sources changed since the capture or the
-    capture was taken in another launch shape (tile height and z-chunk; a
-    capture on a smaller box of the same shape scales by the sites)."""
+    capture was taken in another launch shape (tile width, height and
+    z-chunk; a capture on a smaller box of the same shape scales by the sites)."""
     try:
         import hashlib
 
@@ -154,7 +154,7 @@ def measured_traffic(storage: str, n_sites: int, tile=None):
         if h.hexdigest() != rec["kernel_sources_sha256"] or storage not in rec["captures"]:
             return None
         cap = rec["captures"][storage]
-        if tile is not None and list(cap["tile"])[1:] != list(tile)[1:]:
+        if tile is not None and list(cap["tile"]) != list(tile):
             return None
         return cap["bytes_per_site"] * n_sites
     except Exception:
@@ -328,6 +328,8 @@ def run_ensemble(args):
     stream = torch.cuda.Stream()
     batch = lbgb.Batch(dims, [sp["tau"] for sp in specs], [sp["M"] for sp in specs], [sp["W"] for sp in specs],
                        [sp["sigma"] for sp in specs], storage=args.storage, stream=stream)
+    if args.density:  # every box with the same contrasts: droplets of the phase at phi = 1
+        batch.set_density(*args.density)
     ty, zc = batch.tune(3)
     fields = {}
     for k, sp in enumerate(specs):
@@ -348,13 +350,16 @@ def run_ensemble(args):
     ms = e0.elapsed_time(e1)
     sites = batch.sites
     value = sites * args.steps / (ms * 1e-3) / 1e6
-    bps = {"f32": 272.0, "f16": 164.0, "bf16": 164.0, "moments": 136.0}[args.storage]
+    bps = {"f32": 272.0, "f16": 164.0, "bf16": 164.0, "moments": 136.0}[args.storage]  # per site and step
     peak, peak_kind = peaks()
     achieved = bps * sites / (ms / args.steps * 1e-3) / 1e9
     errs = []
     for k, sp in enumerate(specs):
         e, R, W = sp["edge"], sp["R"], sp["W"]
-        rho, _, _ = batch.moments_numpy(k)
+        rho, _, phi = batch.moments_numpy(k)
+        if args.density:  # p = (p* - 1) rho(phi) cs^2, the pressure of the contrast step
+            rl, rg = args.density[0], args.density[1]
+            rho = (rho.astype(np.float64) - 1.0) * (rg + (rl - rg) * phi.astype(np.float64))
         c = (e - 1) / 2
         ax = np.arange(e)
         d = np.sqrt((ax[None, None, :] - c) ** 2 + (ax[None, :, None] - c) ** 2 + (ax[:, None, None] - c) ** 2)
@@ -366,7 +371,9 @@ def run_ensemble(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{len(specs)} independent periodic droplet boxes, edges in {{24,32,48,64,96}}, "
                                    "R = 0.25 edge (1 +- 20%), sigma in [0.005, 0.02], tau 1, M 0.1, W 3; one "
-                                   "persistent launch per step under a CUDA graph",
+                                   "persistent launch per step under a CUDA graph"
+                                   + (", density and viscosity contrasts rho_l, rho_g, tau_l, tau_g = "
+                                      + ", ".join(f"{v:g}" for v in args.density) if args.density else ""),
                        "boxes": len(specs), "sites": sites, "storage": args.storage, "tile": [32, ty, zc],
                        "l2": "populations larger than L2, no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -556,7 +563,7 @@ def run_box(args, lbgb, torch, w, storage: str, force, rank: int, world: int, pg
     achieved = bps * N / kern_avg_s / 1e9
     key = storage + ("+density" if args.density else "") + ("+weno5" if args.phase != "lb" else "")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": measured_traffic(key, N, [32, ty, zc]),
+            "traffic": measured_traffic(key + ("+paired" if paired else ""), N, [64 if paired else 32, ty, zc]),
             "kernel": "fused_step_kernel" + (" (VD)" if args.density else "") + (" (PF)" if args.phase != "lb" else "")
                       + (" (paired: two sites per thread)" if paired else ""),
             "bytes_per_site": bps, "kernel_ms_avg": kern_avg_s * 1e3, "peak_source": peak_kind}
@@ -569,7 +576,7 @@ def run_box(args, lbgb, torch, w, storage: str, force, rank: int, world: int, pg
         # the three finite-difference stage kernels and the reduction, per step
         roof["other_kernels_ms_per_step"] = t_max / args.steps - kern_avg_s * 1e3
         roof["other_kernels_bytes_per_site"] = 3 * (4 + 12 + 4) + 2 * 4
-    return {"storage": storage, "value": value, "ms_per_step": t_max / args.steps, "tile": [32, ty, zc],
+    return {"storage": storage, "value": value, "ms_per_step": t_max / args.steps, "tile": [64 if paired else 32, ty, zc],
             "paired": paired,
             "roofline": roof, "clocks": clk, "gpu_launches": launches, "rho_ref": rho_ref,
             "l2": "inputs larger than L2 (populations %.2f GB), no flush" % (bps * N / 2 / 1e9),

@@ -366,7 +366,8 @@ int lb_kernel_time(lb_ctx* ctx, double* ms, long long* launches);
  * items of all boxes, plus one per-box FP64 reduction launch; runs of two or
  * more steps replay a captured CUDA graph.  Every box is computed by the same
  * per-tile code as a single box (lb_step), so its fields are bitwise those of
- * lb_step with the same tile shape.  No external force (LB_FORCE_NONE).
+ * lb_step with the same tile shape and the one-site kernel (lb_set_pairing
+ * off).  No external force (LB_FORCE_NONE).
  */
 typedef struct lb_batch lb_batch;
 
@@ -393,6 +394,14 @@ int lb_batch_get_tile(const lb_batch* batch, int* ty, int* zc);
 /* Time every tile shape on the batch's own arrays (zeroed) and keep the
  * fastest; call before lb_batch_init (LB_ESTATE otherwise). */
 int lb_batch_tune(lb_batch* batch, int steps);
+/* Density and viscosity contrasts (Sec. 2.3, as lb_set_density) for every box,
+ * each with its own rho_l, rho_g, tau_l, tau_g (count values each; tau of
+ * lb_batch_create is then no longer used).  From the next step every box runs
+ * the contrast step, in the same persistent launch; the denser phase belongs
+ * at phi = 1.  No buoyancy in a batch.
+ * Errors: LB_EINVAL unless every rho > 0 and tau > 1/2 (finite). */
+int lb_batch_set_density(lb_batch* batch, const double* rho_l, const double* rho_g, const double* tau_l,
+                         const double* tau_g);
 long long lb_batch_sites(const lb_batch* batch);  /* sum of the boxes' sites */
 long long lb_batch_time(const lb_batch* batch);   /* steps taken */
 void lb_batch_destroy(lb_batch* batch);            /* NULL is ignored */

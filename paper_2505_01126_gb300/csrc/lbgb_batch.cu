@@ -45,11 +45,13 @@ int bfail(int code, const char* fmt, ...) {
 
 // Per-box FP64 reduction of a contiguous range of partial records: one block
 // per box (the block index plus box_base), fixed summation order.  mode 0 =
-// step (Phi, K, eps, max|u|), 1 = init (Phi, K, 0, max|u|).
+// step (Phi, K, eps, max|u|), 1 = init (Phi, K, 0, max|u|).  epsw[box] turns
+// the summed a2:a2 partials into eps: 2 nu (3/(2 tau))^2, or 1 with density
+// contrasts (the partials then carry each site's own weight).
 __global__ void __launch_bounds__(256) batch_reduce_kernel(const double* __restrict__ part,
                                                            const int* __restrict__ start,
                                                            const int* __restrict__ count, int box_base,
-                                                           int fixed_count, const double* __restrict__ tau,
+                                                           int fixed_count, const double* __restrict__ epsw,
                                                            DevState* st, int mode) {
     const int box = box_base + blockIdx.x;
     const int s0 = start ? start[box] : 0;
@@ -67,11 +69,9 @@ __global__ void __launch_bounds__(256) batch_reduce_kernel(const double* __restr
     if (threadIdx.x == 0) {
         DevState& S = st[box];
         const bool bad = !isfinite(v0 + v1 + v2 + v3);
-        const double tb = tau[box];
-        const double s = 1.5 / tb;
         S.diag[0] = v0;
         S.diag[1] = v1;
-        S.diag[2] = mode == 0 ? 2.0 * ((tb - 0.5) / 3.0) * s * s * v2 : 0.0;
+        S.diag[2] = mode == 0 ? epsw[box] * v2 : 0.0;
         S.diag[3] = sqrt(v4);
         S.diag[4] = 0.0;
         S.mass = mode == 0 ? v3 : 0.0;
@@ -100,6 +100,7 @@ struct lb_batch {
     std::vector<BoxDesc> boxes;       // host copy (item fields follow the current tile)
     bool mc = false;                  // moment-only storage
     std::vector<double> tau, M, W, sigma;
+    bool vd = false;                  // density and viscosity contrasts (lb_batch_set_density)
     long long total_sites = 0, max_N = 0;
     bool vec = true;                  // every box has nx % 4 == 0
 
@@ -111,7 +112,7 @@ struct lb_batch {
     int* d_item_box = nullptr;
     int* d_item0 = nullptr;
     int* d_nitem = nullptr;
-    double* d_tau = nullptr;
+    double* d_epsw = nullptr;         // eps per unit of the summed a2:a2 partials, per box
     DevState* d_st = nullptr;
     float* stage = nullptr;           // host I/O staging: 5 * max_N floats
     cudaStream_t stream = nullptr;
@@ -167,7 +168,12 @@ int build_work(lb_batch* B) {
     BCUDA(cudaMemcpy(B->d_nitem, nitem.data(), (size_t)B->count * sizeof(int), cudaMemcpyHostToDevice));
     B->nitems = item;
     int per_sm = 0;
-    switch (B->storage) {
+    if (B->vd) switch (B->storage) {
+        case LB_F32_MOMENTS: per_sm = batch_vd_blocks_per_sm<float, true>(B->ty, B->vec); break;
+        case LB_F32: per_sm = batch_vd_blocks_per_sm<float, false>(B->ty, B->vec); break;
+        case LB_F16_SHIFTED: per_sm = batch_vd_blocks_per_sm<__half, false>(B->ty, B->vec); break;
+        default: per_sm = batch_vd_blocks_per_sm<__nv_bfloat16, false>(B->ty, B->vec); break;
+    } else switch (B->storage) {
         case LB_F32_MOMENTS: per_sm = batch_mc_blocks_per_sm(B->ty, B->vec); break;
         case LB_F32: per_sm = batch_blocks_per_sm<float>(B->ty, B->vec); break;
         case LB_F16_SHIFTED: per_sm = batch_blocks_per_sm<__half>(B->ty, B->vec); break;
@@ -204,6 +210,7 @@ StepArgs box_args(const lb_batch* B, int box, int par) {
     }
     a.force_kind = FK_NONE;
     a.omega = d.omega; a.omega_phi = d.omega_phi; a.sharp = d.sharp; a.beta = d.beta;
+    a.rho_g = d.rho_g; a.drho = d.drho; a.tau_g = d.tau_g; a.dtau = d.dtau;
     a.st = B->d_st + box;
     a.partials = B->partials;
     return a;
@@ -211,6 +218,14 @@ StepArgs box_args(const lb_batch* B, int box, int par) {
 
 // par: AA parity; for the moment-only storage, 1 to pull (t > 0).
 cudaError_t launch_box(const lb_batch* B, int mode, int par, dim3 grid, const StepArgs& a, bool vec) {
+    if (B->vd && mode == MODE_MOMENTS) {  // the forced velocity includes the contrast forces
+        switch (B->storage) {
+            case LB_F32_MOMENTS: return launch_fused_x<float, true, true, false>(mode, par, 8, vec, grid, a, B->stream);
+            case LB_F32: return launch_fused_x<float, false, true, false>(mode, par, 8, vec, grid, a, B->stream);
+            case LB_F16_SHIFTED: return launch_fused_x<__half, false, true, false>(mode, par, 8, vec, grid, a, B->stream);
+            default: return launch_fused_x<__nv_bfloat16, false, true, false>(mode, par, 8, vec, grid, a, B->stream);
+        }
+    }
     switch (B->storage) {
         case LB_F32_MOMENTS: return launch_fused_mc(mode, par, 8, vec, grid, a, B->stream);
         case LB_F32: return launch_fused<float>(mode, par, 8, vec, grid, a, B->stream);
@@ -238,14 +253,21 @@ int enqueue_batch_step(lb_batch* B, int par, cudaStream_t s, bool first = false)
     }
     b.partials = B->partials;
     cudaError_t e;
-    switch (B->storage) {
+    if (B->vd) {
+        switch (B->storage) {
+            case LB_F32_MOMENTS: e = launch_batch_vd<float, true>(first ? 0 : 1, B->ty, B->vec, B->grid_blocks, b, s); break;
+            case LB_F32: e = launch_batch_vd<float, false>(par, B->ty, B->vec, B->grid_blocks, b, s); break;
+            case LB_F16_SHIFTED: e = launch_batch_vd<__half, false>(par, B->ty, B->vec, B->grid_blocks, b, s); break;
+            default: e = launch_batch_vd<__nv_bfloat16, false>(par, B->ty, B->vec, B->grid_blocks, b, s); break;
+        }
+    } else switch (B->storage) {
         case LB_F32_MOMENTS: e = launch_batch_mc(first ? 0 : 1, B->ty, B->vec, B->grid_blocks, b, s); break;
         case LB_F32: e = launch_batch<float>(par, B->ty, B->vec, B->grid_blocks, b, s); break;
         case LB_F16_SHIFTED: e = launch_batch<__half>(par, B->ty, B->vec, B->grid_blocks, b, s); break;
         default: e = launch_batch<__nv_bfloat16>(par, B->ty, B->vec, B->grid_blocks, b, s); break;
     }
     if (e != cudaSuccess) return bfail(LB_ECUDA, "batch step launch: %s", cudaGetErrorString(e));
-    batch_reduce_kernel<<<B->count, 256, 0, s>>>(B->partials, B->d_item0, B->d_nitem, 0, 0, B->d_tau, B->d_st, 0);
+    batch_reduce_kernel<<<B->count, 256, 0, s>>>(B->partials, B->d_item0, B->d_nitem, 0, 0, B->d_epsw, B->d_st, 0);
     BCUDA(cudaGetLastError());
     B->launches += 2;
     return LB_OK;
@@ -301,7 +323,7 @@ void lb_batch_destroy(lb_batch* B) {
     cudaFree(B->d_item_box);
     cudaFree(B->d_item0);
     cudaFree(B->d_nitem);
-    cudaFree(B->d_tau);
+    cudaFree(B->d_epsw);
     cudaFree(B->d_st);
     cudaFree(B->stage);
     if (prev >= 0) cudaSetDevice(prev);
@@ -378,10 +400,15 @@ int lb_batch_create(int count, const int* dims, const double* tau, const double*
     alloc((void**)&B->d_boxes, (size_t)count * sizeof(BoxDesc));
     alloc((void**)&B->d_item0, (size_t)count * sizeof(int));
     alloc((void**)&B->d_nitem, (size_t)count * sizeof(int));
-    alloc((void**)&B->d_tau, (size_t)count * sizeof(double));
+    alloc((void**)&B->d_epsw, (size_t)count * sizeof(double));
     alloc((void**)&B->d_st, (size_t)count * sizeof(DevState));
     if (rc == LB_OK) {
-        cudaError_t e = cudaMemcpy(B->d_tau, B->tau.data(), (size_t)count * sizeof(double), cudaMemcpyHostToDevice);
+        std::vector<double> w(count);
+        for (int b = 0; b < count; ++b) {
+            const double s = 1.5 / B->tau[b];
+            w[b] = 2.0 * ((B->tau[b] - 0.5) / 3.0) * s * s;
+        }
+        cudaError_t e = cudaMemcpy(B->d_epsw, w.data(), (size_t)count * sizeof(double), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemset(B->d_st, 0, (size_t)count * sizeof(DevState));
         if (e != cudaSuccess) rc = bfail(LB_ECUDA, "batch set-up: %s", cudaGetErrorString(e));
     }
@@ -425,7 +452,7 @@ int lb_batch_init(lb_batch* B, int box, const float* phi, const float* u) {
     const dim3 grid((d.nx + 31) / 32, (d.ny + 7) / 8, (d.nz + a.zc - 1) / a.zc);
     BCUDA(launch_box(B, MODE_INIT, 0, grid, a, false));
     batch_reduce_kernel<<<1, 256, 0, B->stream>>>(B->partials, nullptr, nullptr, box, (int)(grid.x * grid.y * grid.z),
-                                                  B->d_tau, B->d_st, 1);
+                                                  B->d_epsw, B->d_st, 1);
     BCUDA(cudaGetLastError());
     B->launches += 2;
     if (!B->initialized[box]) {
@@ -560,6 +587,29 @@ int lb_batch_tune(lb_batch* B, int steps) {
     cudaEventDestroy(e1);
     B->launches = 0;
     return lb_batch_set_tile(B, bty, bzc);
+}
+
+int lb_batch_set_density(lb_batch* B, const double* rho_l, const double* rho_g, const double* tau_l,
+                         const double* tau_g) {
+    if (!B || !rho_l || !rho_g || !tau_l || !tau_g) return bfail(LB_EINVAL, "lb_batch_set_density: NULL argument");
+    std::vector<double> w(B->count);
+    for (int b = 0; b < B->count; ++b) {
+        const double rl = rho_l[b], rg = rho_g[b], tl = tau_l[b], tg = tau_g[b];
+        if (!(rl > 0) || !(rg > 0) || !(tl > 0.5) || !(tg > 0.5) || !isfinite(rl) || !isfinite(rg) || !isfinite(tl) ||
+            !isfinite(tg))
+            return bfail(LB_EINVAL, "lb_batch_set_density: box %d needs rho > 0 and tau > 1/2", b);
+    }
+    for (int b = 0; b < B->count; ++b) {
+        BoxDesc& d = B->boxes[b];
+        d.rho_g = (float)rho_g[b];
+        d.drho = (float)(rho_l[b] - rho_g[b]);
+        d.tau_g = (float)tau_g[b];
+        d.dtau = (float)(tau_l[b] - tau_g[b]);
+        w[b] = 1.0;  // the contrast kernels weight each site's a2:a2 by its own 2 nu (3/(2 tau))^2
+    }
+    B->vd = true;
+    BCUDA(cudaMemcpy(B->d_epsw, w.data(), (size_t)B->count * sizeof(double), cudaMemcpyHostToDevice));
+    return build_work(B);  // uploads the descriptors, sizes the grid for the contrast kernel, drops the graph
 }
 
 long long lb_batch_sites(const lb_batch* B) { return B ? B->total_sites : -1; }

@@ -608,6 +608,7 @@ struct BoxDesc {
     long long c_off;                        // moment-only storage: offset of the box's 10 planes in a buffer
     float omega, omega_phi, sharp, beta;
     int item0, tiles_x, tiles_y, tiles_z;   // this box's slice of the work list
+    float rho_g, drho, tau_g, dtau;         // density and viscosity contrasts (kernels with VD)
 };
 
 struct BatchArgs {
@@ -646,12 +647,15 @@ struct BoxTileArgs {
     const float *in_phi, *in_u;
     PlaneSet<const float> cin;  // moment-only storage
     PlaneSet<float> cout;
+    float rho_g, drho, tau_g, dtau;  // density and viscosity contrasts (VD); no buoyancy in a batch
+    float gb0, gb1, gb2, rho_ref;
 };
 
 // Persistent kernel: the grid strides over the work list of all boxes.  With
 // MC_ (moment-only storage, FT float) PAR = 0 evaluates each site's own
-// coefficients (the step from t = 0) and PAR = 1 pulls.
-template <class FT, int TY, int PAR, bool VEC, bool MC_ = false>
+// coefficients (the step from t = 0) and PAR = 1 pulls.  VD_: every box with
+// its own density and viscosity contrasts (Sec. 2.3).
+template <class FT, int TY, int PAR, bool VEC, bool MC_ = false, bool VD_ = false>
 __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 512 / (32 * TY)))
 batch_step_kernel(const __grid_constant__ BatchArgs b) {
     for (int item = blockIdx.x; item < b.nitems; item += gridDim.x) {
@@ -669,6 +673,8 @@ batch_step_kernel(const __grid_constant__ BatchArgs b) {
         t.in_phi = t.in_u = nullptr;
         t.cin = PlaneSet<const float>{MC_ ? b.c_in + d.c_off : nullptr, (long long)d.N};
         t.cout = PlaneSet<float>{MC_ ? b.c_out + d.c_off : nullptr, (long long)d.N};
+        t.rho_g = d.rho_g; t.drho = d.drho; t.tau_g = d.tau_g; t.dtau = d.dtau;
+        t.gb0 = t.gb1 = t.gb2 = t.rho_ref = 0.f;
         const int local = item - d.item0;
         const int tbx = local % d.tiles_x, rest = local / d.tiles_x;
         const int tby = rest % d.tiles_y, tbz = rest / d.tiles_y;
@@ -676,7 +682,7 @@ batch_step_kernel(const __grid_constant__ BatchArgs b) {
             const BoxTileArgs<FT>& a = t;
             constexpr int MODE = MODE_STEP;
             constexpr bool MC = MC_;
-            constexpr bool VD = false;
+            constexpr bool VD = VD_;
             constexpr bool PF = false;
             constexpr bool PAIR = false;
 #define TILE_BX tbx
@@ -728,6 +734,14 @@ template <class FT>
 cudaError_t launch_fused_pair(int parity, int ty, dim3 grid, const StepArgs& a, cudaStream_t st);
 template <class FT>
 int fused_pair_blocks_per_sm(int ty);
+
+// The batch kernel with density and viscosity contrasts (every box its own),
+// for the AA storage FT (MC = false) or the moment-only storage (FT float,
+// MC = true, parity = pull).  Defined in lbgb_step_vd_*.cu.
+template <class FT, bool MC>
+cudaError_t launch_batch_vd(int parity, int ty, bool vec, int blocks, const BatchArgs& b, cudaStream_t st);
+template <class FT, bool MC>
+int batch_vd_blocks_per_sm(int ty, bool vec);
 
 // The same kernels with the density and viscosity contrasts (VD) and/or the
 // phase field as a stored field (PF), mode STEP or MOMENTS (and INIT for PF

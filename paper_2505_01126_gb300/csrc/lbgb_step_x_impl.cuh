@@ -61,4 +61,38 @@ int fused_x_blocks_per_sm<LBGB_FT, LBGB_MC, LBGB_VD, LBGB_PF>(int ty, bool vec) 
     return n;
 }
 
+#if LBGB_VD && !LBGB_PF
+template <int TY, bool VEC>
+static void launch_batch_vd_ty(int parity, int blocks, const BatchArgs& b, cudaStream_t st) {
+    if (parity) batch_step_kernel<LBGB_FT, TY, 1, VEC, LBGB_MC, true><<<blocks, 32 * TY, 0, st>>>(b);
+    else batch_step_kernel<LBGB_FT, TY, 0, VEC, LBGB_MC, true><<<blocks, 32 * TY, 0, st>>>(b);
+}
+
+template <>
+cudaError_t launch_batch_vd<LBGB_FT, LBGB_MC>(int parity, int ty, bool vec, int blocks, const BatchArgs& b,
+                                              cudaStream_t st) {
+    if (ty == 4) vec ? launch_batch_vd_ty<4, true>(parity, blocks, b, st) : launch_batch_vd_ty<4, false>(parity, blocks, b, st);
+    else if (ty == 8) vec ? launch_batch_vd_ty<8, true>(parity, blocks, b, st) : launch_batch_vd_ty<8, false>(parity, blocks, b, st);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+template <>
+int batch_vd_blocks_per_sm<LBGB_FT, LBGB_MC>(int ty, bool vec) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (ty == 4)
+        e = vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LBGB_FT, 4, 1, true, LBGB_MC, true>, 128, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LBGB_FT, 4, 1, false, LBGB_MC, true>, 128, 0);
+    else if (ty == 8)
+        e = vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LBGB_FT, 8, 1, true, LBGB_MC, true>, 256, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LBGB_FT, 8, 1, false, LBGB_MC, true>, 256, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+#endif
+
 }  // namespace lbgb

@@ -105,6 +105,40 @@ def test_batch_boxes_match_the_oracle(lbgb, orc, dims, storage):
     batch.close()
 
 
+@pytest.mark.parametrize("storage", ["f32", "moments"])
+def test_batch_with_density_contrasts_matches_the_oracle(lbgb, orc, storage):
+    """Four boxes with their own density and viscosity contrasts (heavy droplets
+    at ratios 10 and 100, a light one at 1/10, and ratio 1), one persistent
+    launch per step, 50 steps: each box against its own FP64 oracle with the
+    same contrasts within 1e-5, and its reductions within the derived bounds."""
+    from test_gpu_parity import TOL, check_diagnostics, max_err
+
+    dims = [(32, 24, 20), (24, 24, 24), (16, 40, 12), (36, 12, 16)]
+    tau = [0.8, 1.0, 0.6, 0.9]
+    sigma = [0.01, 0.005, 0.02, 0.015]
+    dens = [(10.0, 1.0, 0.6, 0.8), (100.0, 1.0, 0.8, 0.8), (1.0, 10.0, 1.0, 0.6), (1.0, 1.0, 0.7, 0.7)]
+    fields = [box_fields(*d, seed=40 + k) for k, d in enumerate(dims)]
+    batch = lbgb.Batch(dims, tau, 0.1, 3.0, sigma, storage=storage)
+    batch.set_density(*[[dd[j] for dd in dens] for j in range(4)])
+    for k, (phi, u) in enumerate(fields):
+        batch.init(k, phi, u)
+    batch.step(50)
+    for k, (d, (phi, u)) in enumerate(zip(dims, fields)):
+        o = orc.Oracle(*d, tau[k], 0.1, 3.0, sigma[k])
+        o.set_density(*dens[k])
+        o.init(phi.astype(np.float64), u.astype(np.float64))
+        o.step(50)
+        e = max_err(batch.moments_numpy(k), o.moments())
+        assert max(e) <= TOL, (k, d, e)
+        check_diagnostics(batch.diagnostics(k), o.diagnostics(), int(np.prod(d)), field_err=max(e),
+                          tau=dens[k][2:])
+        o.close()
+    with pytest.raises(lbgb.LBError) as ex:
+        batch.set_density([1.0] * 4, [0.0] * 4, [1.0] * 4, [1.0] * 4)
+    assert ex.value.code == lbgb.LB_EINVAL
+    batch.close()
+
+
 def test_batch_call_order(lbgb):
     batch = lbgb.Batch([(16, 16, 16), (24, 8, 8)], 0.8, 0.1, 3.0, 0.01)
     phi, u = box_fields(16, 16, 16, 1)
