@@ -161,6 +161,28 @@ def measured_traffic(storage: str, n_sites: int, tile=None):
         return None
 
 
+def measured_inst_per_site(storage: str, tile=None):
+    """Warp-instructions per site of the fused kernel from the committed ncu
+    record (same conditions as measured_traffic), or None."""
+    try:
+        import hashlib
+
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for src in rec["kernel_sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        cap = rec["captures"].get(storage)
+        if h.hexdigest() != rec["kernel_sources_sha256"] or cap is None:
+            return None
+        if tile is not None and list(cap["tile"]) != list(tile):
+            return None
+        return cap.get("warp_inst_per_site")
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -477,7 +499,7 @@ def storage_errors(lbgb, storage: str, preset: str, ref) -> dict:
             "fields_max_abs_diff": fields, "laplace_dp_relerr": abs(float(np.mean(dps)) / ref["dp"] - 1)}
 
 
-def run_box(args, lbgb, torch, w, storage: str, force, rank: int, world: int, pg, barrier):
+def run_box(args, lbgb, torch, w, storage: str, force, rank: int, world: int, pg, barrier, alu=None):
     """Create, tune and initialise one box in `storage`, time args.steps steps
     on the device (CUDA events on the library's stream, the fused kernel's own
     event pairs), then the same run end to end through the C ABI with pinned host
@@ -567,6 +589,14 @@ def run_box(args, lbgb, torch, w, storage: str, force, rank: int, world: int, pg
             "kernel": "fused_step_kernel" + (" (VD)" if args.density else "") + (" (PF)" if args.phase != "lb" else "")
                       + (" (paired: two sites per thread)" if paired else ""),
             "bytes_per_site": bps, "kernel_ms_avg": kern_avg_s * 1e3, "peak_source": peak_kind}
+    ips = measured_inst_per_site(key + ("+paired" if paired else ""), [64 if paired else 32, ty, zc])
+    if ips is not None and alu:
+        # the compute side: warp-instructions issued per second against the
+        # device's measured FMA issue rate (one per scheduler and cycle)
+        ach = ips * N / kern_avg_s
+        roof["issue"] = {"warp_inst_per_site": ips, "achieved": ach, "peak": alu["warp_inst_per_s"],
+                         "unit": "warp-instructions/s", "frac": ach / alu["warp_inst_per_s"],
+                         "peak_source": "measured (lb_measure_fp32_peak)"}
     if args.phase == "lb" and not args.density and storage in SURVEY_BYTES:
         # the same kernel time against the survey's count, which adds 8 B/site for
         # writing and re-reading a stored phi (this kernel keeps phi on chip)
@@ -673,10 +703,11 @@ def main():
     else:
         force = None if droplet else lbgb.Force(kind=lbgb.LB_FORCE_LINEAR, T_relax=w.T_relax)
 
-    main_run = run_box(args, lbgb, torch, w, args.storage, force, rank, world, pg, barrier)
+    alu = lbgb.measure_fp32_peak() if rank == 0 else None  # the compute-side roofline's denominator
+    main_run = run_box(args, lbgb, torch, w, args.storage, force, rank, world, pg, barrier, alu)
     compare = None
     if hit and args.storage == "f32" and args.compare != "none" and not args.density and args.phase == "lb":
-        compare = run_box(args, lbgb, torch, w, args.compare, force, rank, world, pg, barrier)
+        compare = run_box(args, lbgb, torch, w, args.compare, force, rank, world, pg, barrier, alu)
 
     if rank == 0:
         cpu, errors = None, None
@@ -728,7 +759,8 @@ def main():
                 "config": {"workload": workload_name, "edge": n, "storage": args.storage, "tile": main_run["tile"],
                            "l2": main_run["l2"], "parallelism": f"replicas x{world}"},
                 "roofline": main_run["roofline"], "cpu_baseline": cpu, "e2e": main_run["e2e"],
-                "clocks": main_run["clocks"], "gpu_launches": main_run["gpu_launches"]}
+                "clocks": main_run["clocks"], "gpu_launches": main_run["gpu_launches"],
+                "alu_peak": alu}
         if compare is not None:
             line["storage16"] = {k: compare[k] for k in ("storage", "value", "ms_per_step", "tile", "paired", "roofline",
                                                          "e2e", "clocks", "gpu_launches", "diagnostics")}

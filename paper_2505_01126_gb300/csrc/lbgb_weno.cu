@@ -177,6 +177,22 @@ __global__ void __launch_bounds__(WNT, 4) weno_stage_kernel(const float* __restr
     make_J(z0);
     float uzc = __ldg(uz + (long long)wrap_mod(z0, nz) * plane + own);  // uz of the current plane
     float fzm = z_flux(z0 - 1, __ldg(uz + (long long)wrap_mod(z0 - 1, nz) * plane + own), uzc);
+    // the face velocities of a plane (left and right site of each x and y face)
+    // and uz above the column, loaded one plane ahead of their use so that
+    // their latency overlaps the barrier and the J planes
+    float vxl[NFL], vxr[NFL], vyl[NFL], vyr[NFL];
+    auto load_u = [&](int zq) {  // z0 <= zq < nz
+        const long long zb = (long long)zq * plane;
+#pragma unroll
+        for (int k = 0; k < NFL; ++k) {
+            vxl[k] = fx_i[k] >= 0 ? __ldg(ux + zb + fx_l[k]) : 0.f;
+            vxr[k] = fx_i[k] >= 0 ? __ldg(ux + zb + fx_r[k]) : 0.f;
+            vyl[k] = fy_i[k] >= 0 ? __ldg(uy + zb + fy_l[k]) : 0.f;
+            vyr[k] = fy_i[k] >= 0 ? __ldg(uy + zb + fy_r[k]) : 0.f;
+        }
+    };
+    load_u(z0);
+    float uzn = __ldg(uz + (long long)wrap_mod(z0 + 1, nz) * plane + own);
 
     for (int z = z0; z < z1; ++z) {
         make_J(z + 1);
@@ -193,14 +209,14 @@ __global__ void __launch_bounds__(WNT, 4) weno_stage_kernel(const float* __restr
                 float v[6];
 #pragma unroll
                 for (int j = 0; j < 6; ++j) v[j] = P0[r + WH][f + j];
-                (&s_Fx[0][0])[fx_i[k]] = face_flux(v, __ldg(ux + zb + fx_l[k]), __ldg(ux + zb + fx_r[k]));
+                (&s_Fx[0][0])[fx_i[k]] = face_flux(v, vxl[k], vxr[k]);
             }
             if (fy_i[k] >= 0) {
                 const int f = fy_i[k] / TX, c = fy_i[k] - f * TX;
                 float v[6];
 #pragma unroll
                 for (int j = 0; j < 6; ++j) v[j] = P0[f + j][c + WH];
-                (&s_Fy[0][0])[fy_i[k]] = face_flux(v, __ldg(uy + zb + fy_l[k]), __ldg(uy + zb + fy_r[k]));
+                (&s_Fy[0][0])[fy_i[k]] = face_flux(v, vyl[k], vyr[k]);
             }
         }
         // D lap(p) - kappa div(J) at (x, y, z), the 26 neighbours with weights (1, 4, 1)^3 / 216
@@ -235,7 +251,6 @@ __global__ void __launch_bounds__(WNT, 4) weno_stage_kernel(const float* __restr
                               dj);
         }
         // the upper z face of this column
-        const float uzn = __ldg(uz + (long long)wrap_mod(z + 1, nz) * plane + own);
         const float fzp = z_flux(z, uzc, uzn);
         __syncthreads();  // the plane's x and y face fluxes are in place
 
@@ -257,7 +272,11 @@ __global__ void __launch_bounds__(WNT, 4) weno_stage_kernel(const float* __restr
         }
         fzm = fzp;
         uzc = uzn;
-        if (z + 1 < z1) load_plane(z + 4);  // the next plane's; no copy may be in flight when the march ends
+        if (z + 1 < z1) {
+            load_plane(z + 4);  // the next plane's; no copy may be in flight when the march ends
+            load_u(z + 1);
+            uzn = __ldg(uz + (long long)wrap_mod(z + 2, nz) * plane + own);
+        }
     }
 }
 
