@@ -391,8 +391,10 @@ int lb_batch_diagnostics(lb_batch* batch, int box, double out[5]);
 /* Tile height ty in {4, 8} and z-chunk zc >= 1 of the work items. */
 int lb_batch_set_tile(lb_batch* batch, int ty, int zc);
 int lb_batch_get_tile(const lb_batch* batch, int* ty, int* zc);
-/* Time every tile shape on the batch's own arrays (zeroed) and keep the
- * fastest; call before lb_batch_init (LB_ESTATE otherwise). */
+/* Time every tile shape (heights 8 and 4, z-chunks 16 to 128) on the batch's
+ * own arrays (zeroed), each as the median of five windows of 2*steps steps, and
+ * keep the first shape in that order within 1% of the fastest; call before
+ * lb_batch_init (LB_ESTATE otherwise). */
 int lb_batch_tune(lb_batch* batch, int steps);
 /* Density and viscosity contrasts (Sec. 2.3, as lb_set_density) for every box,
  * each with its own rho_l, rho_g, tau_l, tau_g (count values each; tau of

@@ -554,16 +554,22 @@ int lb_batch_tune(lb_batch* B, int steps) {
     cudaEvent_t e0, e1;
     BCUDA(cudaEventCreate(&e0));
     BCUDA(cudaEventCreate(&e1));
-    const int tys[2] = {4, 8};
+    // As lb_tune: each shape the median of five windows (after one that warms
+    // up), the first shape in this order within 1% of the fastest.
+    constexpr int WINDOWS = 5;
+    constexpr float TIE = 0.01f;
+    const int tys[2] = {8, 4};
     const int zcs[4] = {16, 32, 64, 128};
-    float best = 1e30f;
-    int bty = B->ty, bzc = B->zc;
+    float med[8];
+    int cty[8], czc[8], ncand = 0;
     int rc = LB_OK;
     for (int a = 0; a < 2 && rc == LB_OK; ++a)
         for (int b = 0; b < 4 && rc == LB_OK; ++b) {
             if (lb_batch_set_tile(B, tys[a], zcs[b]) != LB_OK) continue;
-            float shape_best = 1e30f;
-            for (int rep = 0; rep < 3; ++rep) {
+            float win[WINDOWS + 1];
+            int nwin = 0;
+            bool ok = true;
+            for (int rep = 0; rep <= WINDOWS && ok; ++rep) {
                 cudaEventRecord(e0, B->stream);
                 int r2 = LB_OK;
                 for (int k = 0; k < 2 * steps && r2 == LB_OK; ++k) r2 = enqueue_batch_step(B, k & 1, B->stream);
@@ -573,16 +579,34 @@ int lb_batch_tune(lb_batch* B, int steps) {
                 cudaEventElapsedTime(&ms, e0, e1);
                 if (r2 != LB_OK) {
                     cudaGetLastError();
-                    break;
+                    ok = false;
+                } else if (rep > 0) {
+                    win[nwin++] = ms;
                 }
-                if (rep > 0 && ms < shape_best) shape_best = ms;  // the first window warms up
             }
-            if (shape_best < best) {
-                best = shape_best;
-                bty = tys[a];
-                bzc = zcs[b];
-            }
+            if (!ok || nwin == 0) continue;
+            for (int i = 1; i < nwin; ++i)
+                for (int j = i; j > 0 && win[j] < win[j - 1]; --j) {
+                    const float t = win[j];
+                    win[j] = win[j - 1];
+                    win[j - 1] = t;
+                }
+            med[ncand] = win[nwin / 2];
+            cty[ncand] = tys[a];
+            czc[ncand] = zcs[b];
+            ++ncand;
         }
+    int bty = B->ty, bzc = B->zc;
+    if (ncand > 0) {
+        float best = med[0];
+        for (int k = 1; k < ncand; ++k) best = med[k] < best ? med[k] : best;
+        for (int k = 0; k < ncand; ++k)
+            if (med[k] <= best * (1.f + TIE)) {
+                bty = cty[k];
+                bzc = czc[k];
+                break;
+            }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     B->launches = 0;
