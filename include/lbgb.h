@@ -366,8 +366,9 @@ int lb_kernel_time(lb_ctx* ctx, double* ms, long long* launches);
  * items of all boxes, plus one per-box FP64 reduction launch; runs of two or
  * more steps replay a captured CUDA graph.  Every box is computed by the same
  * per-tile code as a single box (lb_step), so its fields are bitwise those of
- * lb_step with the same tile shape and the one-site kernel (lb_set_pairing
- * off).  No external force (LB_FORCE_NONE).
+ * lb_step with the same tile shape and the same kernel (one-site, or paired
+ * for FP16/BF16; lb_batch_set_pairing, lb_set_pairing).  No external force
+ * (LB_FORCE_NONE).
  */
 typedef struct lb_batch lb_batch;
 
@@ -404,6 +405,12 @@ int lb_batch_tune(lb_batch* batch, int steps);
  * Errors: LB_EINVAL unless every rho > 0 and tau > 1/2 (finite). */
 int lb_batch_set_density(lb_batch* batch, const double* rho_l, const double* rho_g, const double* tau_l,
                          const double* tau_g);
+/* Which tile body runs the batch step of the FP16/BF16 storages: 1 (the default
+ * where it applies) the paired one of lb_set_pairing, 0 one site per thread.
+ * Applies when every box has nx % 4 == 0 and no density contrasts are set.
+ * Errors: LB_EINVAL for 1 where it does not apply. */
+int lb_batch_set_pairing(lb_batch* batch, int on);
+int lb_batch_get_pairing(const lb_batch* batch, int* on);  /* 1 when the paired body runs */
 long long lb_batch_sites(const lb_batch* batch);  /* sum of the boxes' sites */
 long long lb_batch_time(const lb_batch* batch);   /* steps taken */
 void lb_batch_destroy(lb_batch* batch);            /* NULL is ignored */

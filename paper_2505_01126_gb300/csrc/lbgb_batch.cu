@@ -101,6 +101,7 @@ struct lb_batch {
     bool mc = false;                  // moment-only storage
     std::vector<double> tau, M, W, sigma;
     bool vd = false;                  // density and viscosity contrasts (lb_batch_set_density)
+    bool pair = false;                // paired tile body preferred (16-bit storages; see batch_use_pair)
     long long total_sites = 0, max_N = 0;
     bool vec = true;                  // every box has nx % 4 == 0
 
@@ -130,6 +131,14 @@ struct lb_batch {
 
 namespace {
 
+// The paired tile body (two sites per thread, tiles 64 sites wide) runs the
+// step when it is preferred and applies: FP16/BF16 storage, every box with
+// nx % 4 == 0, no density contrasts.
+bool batch_pair_applies(const lb_batch* B) {
+    return (B->storage == LB_F16_SHIFTED || B->storage == LB_BF16_SHIFTED) && B->vec && !B->vd;
+}
+bool batch_use_pair(const lb_batch* B) { return B->pair && batch_pair_applies(B); }
+
 long long items_for(const lb_batch* B, int ty, int zc) {
     long long n = 0;
     for (const BoxDesc& d : B->boxes)
@@ -146,9 +155,10 @@ void drop_graph(lb_batch* B) {
 int build_work(lb_batch* B) {
     std::vector<int> item_box, item0(B->count), nitem(B->count);
     int item = 0;
+    const int tx = batch_use_pair(B) ? 64 : 32;
     for (int b = 0; b < B->count; ++b) {
         BoxDesc& d = B->boxes[b];
-        d.tiles_x = (d.nx + 31) / 32;
+        d.tiles_x = (d.nx + tx - 1) / tx;
         d.tiles_y = (d.ny + B->ty - 1) / B->ty;
         d.tiles_z = (d.nz + B->zc - 1) / B->zc;
         d.item0 = item;
@@ -168,7 +178,9 @@ int build_work(lb_batch* B) {
     BCUDA(cudaMemcpy(B->d_nitem, nitem.data(), (size_t)B->count * sizeof(int), cudaMemcpyHostToDevice));
     B->nitems = item;
     int per_sm = 0;
-    if (B->vd) switch (B->storage) {
+    if (batch_use_pair(B)) per_sm = B->storage == LB_F16_SHIFTED ? batch_pair_blocks_per_sm<__half>(B->ty)
+                                                                  : batch_pair_blocks_per_sm<__nv_bfloat16>(B->ty);
+    else if (B->vd) switch (B->storage) {
         case LB_F32_MOMENTS: per_sm = batch_vd_blocks_per_sm<float, true>(B->ty, B->vec); break;
         case LB_F32: per_sm = batch_vd_blocks_per_sm<float, false>(B->ty, B->vec); break;
         case LB_F16_SHIFTED: per_sm = batch_vd_blocks_per_sm<__half, false>(B->ty, B->vec); break;
@@ -253,7 +265,10 @@ int enqueue_batch_step(lb_batch* B, int par, cudaStream_t s, bool first = false)
     }
     b.partials = B->partials;
     cudaError_t e;
-    if (B->vd) {
+    if (batch_use_pair(B)) {
+        e = B->storage == LB_F16_SHIFTED ? launch_batch_pair<__half>(par, B->ty, B->grid_blocks, b, s)
+                                         : launch_batch_pair<__nv_bfloat16>(par, B->ty, B->grid_blocks, b, s);
+    } else if (B->vd) {
         switch (B->storage) {
             case LB_F32_MOMENTS: e = launch_batch_vd<float, true>(first ? 0 : 1, B->ty, B->vec, B->grid_blocks, b, s); break;
             case LB_F32: e = launch_batch_vd<float, false>(par, B->ty, B->vec, B->grid_blocks, b, s); break;
@@ -376,6 +391,7 @@ int lb_batch_create(int count, const int* dims, const double* tau, const double*
         if (nx % 4) B->vec = false;
     }
     B->initialized.assign(count, 0);
+    B->pair = batch_pair_applies(B);  // the paired body by default where it applies
     // partial records: the work list of the smallest tile, or one box's lb_init grid
     long long cap = items_for(B, 4, 1);
     for (const BoxDesc& d : B->boxes) {
@@ -558,14 +574,18 @@ int lb_batch_tune(lb_batch* B, int steps) {
     // up), the first shape in this order within 1% of the fastest.
     constexpr int WINDOWS = 5;
     constexpr float TIE = 0.01f;
-    const int tys[2] = {8, 4};
+    // with a 16-bit storage the paired body's shapes come first
+    const bool try_pair = batch_pair_applies(B);
+    const int kinds[4][2] = {{1, 8}, {1, 4}, {0, 8}, {0, 4}};  // (paired, tile height)
     const int zcs[4] = {16, 32, 64, 128};
-    float med[8];
-    int cty[8], czc[8], ncand = 0;
+    float med[16];
+    int cty[16], czc[16], cpr[16], ncand = 0;
     int rc = LB_OK;
-    for (int a = 0; a < 2 && rc == LB_OK; ++a)
+    for (int a = 0; a < 4 && rc == LB_OK; ++a)
         for (int b = 0; b < 4 && rc == LB_OK; ++b) {
-            if (lb_batch_set_tile(B, tys[a], zcs[b]) != LB_OK) continue;
+            if (kinds[a][0] && !try_pair) continue;
+            B->pair = kinds[a][0] != 0;
+            if (lb_batch_set_tile(B, kinds[a][1], zcs[b]) != LB_OK) continue;
             float win[WINDOWS + 1];
             int nwin = 0;
             bool ok = true;
@@ -592,11 +612,12 @@ int lb_batch_tune(lb_batch* B, int steps) {
                     win[j - 1] = t;
                 }
             med[ncand] = win[nwin / 2];
-            cty[ncand] = tys[a];
+            cty[ncand] = kinds[a][1];
             czc[ncand] = zcs[b];
+            cpr[ncand] = kinds[a][0];
             ++ncand;
         }
-    int bty = B->ty, bzc = B->zc;
+    int bty = B->ty, bzc = B->zc, bpr = B->pair ? 1 : 0;
     if (ncand > 0) {
         float best = med[0];
         for (int k = 1; k < ncand; ++k) best = med[k] < best ? med[k] : best;
@@ -604,13 +625,30 @@ int lb_batch_tune(lb_batch* B, int steps) {
             if (med[k] <= best * (1.f + TIE)) {
                 bty = cty[k];
                 bzc = czc[k];
+                bpr = cpr[k];
                 break;
             }
     }
+    B->pair = bpr != 0;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     B->launches = 0;
     return lb_batch_set_tile(B, bty, bzc);
+}
+
+int lb_batch_set_pairing(lb_batch* B, int on) {
+    if (!B) return bfail(LB_EINVAL, "batch is NULL");
+    if (on && !batch_pair_applies(B))
+        return bfail(LB_EINVAL, "the paired tile body needs FP16 or BF16 storage, nx %% 4 == 0 in every box and no "
+                                "density contrasts");
+    B->pair = on != 0;
+    return build_work(B);
+}
+
+int lb_batch_get_pairing(const lb_batch* B, int* on) {
+    if (!B || !on) return bfail(LB_EINVAL, "NULL argument");
+    *on = batch_use_pair(B) ? 1 : 0;
+    return LB_OK;
 }
 
 int lb_batch_set_density(lb_batch* B, const double* rho_l, const double* rho_g, const double* tau_l,

@@ -654,9 +654,10 @@ struct BoxTileArgs {
 // Persistent kernel: the grid strides over the work list of all boxes.  With
 // MC_ (moment-only storage, FT float) PAR = 0 evaluates each site's own
 // coefficients (the step from t = 0) and PAR = 1 pulls.  VD_: every box with
-// its own density and viscosity contrasts (Sec. 2.3).
-template <class FT, int TY, int PAR, bool VEC, bool MC_ = false, bool VD_ = false>
-__global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 512 / (32 * TY)))
+// its own density and viscosity contrasts (Sec. 2.3).  PAIR_: the paired
+// tile body of the 16-bit storages (tiles 64 sites wide, two sites per thread).
+template <class FT, int TY, int PAR, bool VEC, bool MC_ = false, bool VD_ = false, bool PAIR_ = false>
+__global__ void __launch_bounds__(32 * TY, PAIR_ ? (TY == 4 ? 3 : 2) : (TY >= 16 ? 1 : 512 / (32 * TY)))
 batch_step_kernel(const __grid_constant__ BatchArgs b) {
     for (int item = blockIdx.x; item < b.nitems; item += gridDim.x) {
         const BoxDesc d = b.boxes[b.item_box[item]];
@@ -684,7 +685,7 @@ batch_step_kernel(const __grid_constant__ BatchArgs b) {
             constexpr bool MC = MC_;
             constexpr bool VD = VD_;
             constexpr bool PF = false;
-            constexpr bool PAIR = false;
+            constexpr bool PAIR = PAIR_;
 #define TILE_BX tbx
 #define TILE_BY tby
 #define TILE_BZ tbz
@@ -734,6 +735,11 @@ template <class FT>
 cudaError_t launch_fused_pair(int parity, int ty, dim3 grid, const StepArgs& a, cudaStream_t st);
 template <class FT>
 int fused_pair_blocks_per_sm(int ty);
+// The batch kernel with the paired tile body (16-bit storages; every box nx % 4 == 0).
+template <class FT>
+cudaError_t launch_batch_pair(int parity, int ty, int blocks, const BatchArgs& b, cudaStream_t st);
+template <class FT>
+int batch_pair_blocks_per_sm(int ty);
 
 // The batch kernel with density and viscosity contrasts (every box its own),
 // for the AA storage FT (MC = false) or the moment-only storage (FT float,

@@ -40,4 +40,37 @@ int fused_pair_blocks_per_sm<LBGB_FT>(int ty) {
     return n;
 }
 
+template <class FT, int TY>
+static void launch_batch_pair_ty(int parity, int blocks, const BatchArgs& b, cudaStream_t st) {
+    if (parity == 0) batch_step_kernel<FT, TY, 0, true, false, false, true><<<blocks, 32 * TY, 0, st>>>(b);
+    else batch_step_kernel<FT, TY, 1, true, false, false, true><<<blocks, 32 * TY, 0, st>>>(b);
+}
+
+template <>
+cudaError_t launch_batch_pair<LBGB_FT>(int parity, int ty, int blocks, const BatchArgs& b, cudaStream_t st) {
+    switch (ty) {
+        case 4: launch_batch_pair_ty<LBGB_FT, 4>(parity, blocks, b, st); break;
+        case 8: launch_batch_pair_ty<LBGB_FT, 8>(parity, blocks, b, st); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <>
+int batch_pair_blocks_per_sm<LBGB_FT>(int ty) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (ty == 4)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LBGB_FT, 4, 1, true, false, false, true>,
+                                                          128, 0);
+    else if (ty == 8)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LBGB_FT, 8, 1, true, false, false, true>,
+                                                          256, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
 }  // namespace lbgb

@@ -42,7 +42,8 @@ EXPORTS = ["lb_create", "lb_set_stream", "lb_init", "lb_step", "lb_moments", "lb
            "lb_batch_step", "lb_batch_moments", "lb_batch_diagnostics", "lb_batch_set_tile", "lb_batch_get_tile",
            "lb_batch_tune", "lb_batch_sites", "lb_batch_time", "lb_batch_destroy", "lb_velocity_statistics",
            "lb_spectrum", "lb_state_bytes", "lb_save", "lb_load", "lb_set_density", "lb_set_gravity",
-           "lb_set_phase_solver", "lb_measure_fp32_peak", "lb_set_pairing", "lb_get_pairing", "lb_batch_set_density"]
+           "lb_set_phase_solver", "lb_measure_fp32_peak", "lb_set_pairing", "lb_get_pairing", "lb_batch_set_density",
+           "lb_batch_set_pairing", "lb_batch_get_pairing"]
 
 
 def _load():
@@ -103,6 +104,8 @@ def _load():
     lib.lb_load.argtypes = [vp, vp, ctypes.c_size_t]
     lib.lb_measure_fp32_peak.argtypes = [vp, dp_]
     lib.lb_batch_set_density.argtypes = [vp, dp_, dp_, dp_, dp_]
+    lib.lb_batch_set_pairing.argtypes = [vp, i]
+    lib.lb_batch_get_pairing.argtypes = [vp, ctypes.POINTER(i)]
     lib.lb_set_pairing.argtypes = [vp, i]
     lib.lb_get_pairing.argtypes = [vp, ctypes.POINTER(i)]
     return lib
@@ -399,6 +402,16 @@ class Batch:
             return (ctypes.c_double * n)(*[float(v) for v in x])
 
         _check(_lib.lb_batch_set_density(self._h, arr(rho_l), arr(rho_g), arr(tau_l), arr(tau_g)))
+
+    def set_pairing(self, on: bool):
+        """The paired tile body for FP16/BF16 storage (lb_batch_set_pairing)."""
+        _check(_lib.lb_batch_set_pairing(self._h, 1 if on else 0))
+
+    @property
+    def paired(self) -> bool:
+        v = ctypes.c_int()
+        _check(_lib.lb_batch_get_pairing(self._h, ctypes.byref(v)))
+        return bool(v.value)
 
     def init(self, box, phi, u):
         p, _a = _ptr(phi, self._N(box))

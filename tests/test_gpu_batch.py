@@ -54,6 +54,12 @@ def test_batch_boxes_equal_single_boxes(lbgb, dims, storage):
     sigma = [0.01, 0.005, 0.02, 0.015, 0.01][: len(dims)]
     fields = [box_fields(*d, seed=k) for k, d in enumerate(dims)]
     batch = lbgb.Batch(dims, tau, 0.1, 3.0, sigma, storage=storage)
+    # FP16 with every nx % 4 == 0 runs the paired body by default
+    paired = storage == "f16" and all(d[0] % 4 == 0 for d in dims)
+    assert batch.paired == paired
+    if storage == "f16" and not paired:
+        with pytest.raises(lbgb.LBError):
+            batch.set_pairing(True)
     batch.set_tile(4, 16)
     for k, (phi, u) in enumerate(fields):
         batch.init(k, phi, u)
@@ -61,7 +67,8 @@ def test_batch_boxes_equal_single_boxes(lbgb, dims, storage):
     assert batch.time == 7
     for k, (d, (phi, u)) in enumerate(zip(dims, fields)):
         box = lbgb.Box(*d, tau[k], 0.1, 3.0, sigma[k], storage=storage)
-        box.set_pairing(False)  # the batch runs the one-site tile body
+        if storage in ("f16", "bf16"):
+            box.set_pairing(paired)  # the same tile body as the batch
         box.set_tile(4, 16)
         box.init(phi, u)
         box.step(7)
@@ -139,6 +146,44 @@ def test_batch_with_density_contrasts_matches_the_oracle(lbgb, orc, storage):
     batch.close()
 
 
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_batch_paired_matches_the_oracle(lbgb, orc, storage):
+    """16-bit storages run the paired tile body (two sites per thread, tiles 64
+    sites wide) in the persistent batch kernel: five boxes with nx % 4 == 0, one
+    a single x tile of 8, one ragged at 36 and one two tiles wide at 100, 50 steps,
+    each against its own FP64 oracle within the 16-bit storage's bound (2e-4 FP16,
+    5e-3 BF16, as the single-box kernels), and within that bound of the one-site
+    body's fields."""
+    from test_gpu_pair import BOUND
+    from test_gpu_parity import max_err
+
+    dims = [(32, 24, 20), (8, 8, 8), (36, 12, 16), (100, 9, 7), (64, 16, 12)]
+    tau = [0.8, 1.0, 0.6, 0.9, 0.7]
+    sigma = [0.01, 0.005, 0.02, 0.015, 0.01]
+    fields = [box_fields(*d, seed=60 + k) for k, d in enumerate(dims)]
+    got = {}
+    for pair in (True, False):
+        batch = lbgb.Batch(dims, tau, 0.1, 3.0, sigma, storage=storage)
+        batch.set_pairing(pair)
+        batch.set_tile(4 if pair else 8, 16)
+        assert batch.paired == pair
+        for k, (phi, u) in enumerate(fields):
+            batch.init(k, phi, u)
+        batch.step(49)
+        batch.step(1)
+        got[pair] = [batch.moments_numpy(k) for k in range(len(dims))]
+        batch.close()
+    for k, (d, (phi, u)) in enumerate(zip(dims, fields)):
+        o = orc.Oracle(*d, tau[k], 0.1, 3.0, sigma[k])
+        o.init(phi.astype(np.float64), u.astype(np.float64))
+        o.step(50)
+        ep, es = max_err(got[True][k], o.moments()), max_err(got[False][k], o.moments())
+        assert max(ep) <= BOUND[storage], (k, d, ep, es)
+        dd = max_err(got[True][k], [x.astype(np.float64) for x in got[False][k]])
+        assert max(dd) <= BOUND[storage], (k, d, dd)
+        o.close()
+
+
 def test_batch_call_order(lbgb):
     batch = lbgb.Batch([(16, 16, 16), (24, 8, 8)], 0.8, 0.1, 3.0, 0.01)
     phi, u = box_fields(16, 16, 16, 1)
@@ -157,11 +202,13 @@ def test_batch_call_order(lbgb):
     assert e.value.code == lbgb.LB_ESTATE
 
 
-def test_batch_tune_then_run(lbgb):
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_batch_tune_then_run(lbgb, storage):
     dims = [(24, 24, 24), (32, 32, 32), (48, 48, 48)]
-    batch = lbgb.Batch(dims, 1.0, 0.1, 3.0, 0.01)
+    batch = lbgb.Batch(dims, 1.0, 0.1, 3.0, 0.01, storage=storage)
     ty, zc = batch.tune(2)
     assert ty in (4, 8) and zc >= 1
+    assert storage == "f16" or not batch.paired
     for k, d in enumerate(dims):
         batch.init(k, *box_fields(*d, seed=10 + k))
     batch.step(4)
