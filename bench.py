@@ -18,7 +18,7 @@ reached by the fused kernel.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                        [--preset hit256|hit512|hit768|hit1024]
-                       [--storage f32|f16|bf16|moments] [--compare f16|bf16|none]
+                       [--storage f32|f16|bf16|moments|f16g|bf16g] [--compare f16|bf16|f16g|bf16g|none]
                        [--workload hit|ensemble|droplet|abc] [--edge E]
                        [--density RHO_L RHO_G TAU_L TAU_G] [--gravity GX,GY,GZ]
                        [--phase lb|weno5]
@@ -64,7 +64,7 @@ SURR_EDGE, SURR_STEPS, SURR_EVERY = 64, 500, 50
 LAP_EDGE, LAP_R, LAP_SAMPLES = 32, 8.0, list(range(220, 401, 20))
 # bytes per site of the survey's roofline table, which also counts writing and
 # re-reading a stored phi field (8 B/site)
-SURVEY_BYTES = {"f32": 280.0, "f16": 172.0, "bf16": 172.0}
+SURVEY_BYTES = {"f32": 280.0, "f16": 172.0, "bf16": 172.0, "f16g": 144.0, "bf16g": 144.0}
 
 
 # Presets of the bubbly forced HIT workload: edge, bubbles, radius, tau, seed.
@@ -624,9 +624,10 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300")
-    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "moments"],
-                    help="population storage: FP32/FP16/BF16 AA populations, or the moment-only coefficients")
-    ap.add_argument("--compare", default="f16", choices=["f16", "bf16", "none"],
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "moments", "f16g", "bf16g"],
+                    help="population storage: FP32/FP16/BF16 AA populations, the moment-only coefficients, or "
+                         "FP16/BF16 AA populations with 16-bit D3Q7 populations (f16g, bf16g)")
+    ap.add_argument("--compare", default="f16", choices=["f16", "bf16", "f16g", "bf16g", "none"],
                     help="16-bit storage run in the same invocation next to FP32 storage (bubbly HIT only), "
                          "with its errors against the oracle")
     ap.add_argument("--edge", type=int, default=None, help="box edge of the droplet and ABC workloads")

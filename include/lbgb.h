@@ -64,12 +64,20 @@ extern "C" {
  * the reconstruction from macroscopic fields of the thread-safe scheme,
  * Sec. 3), in two buffers; a step rebuilds f_i(x) from the coefficients of the
  * neighbour x - c_i.  It computes the same FP32 numbers as LB_F32 and moves
- * 136 instead of 272 bytes per site and step.  In all four the arithmetic is
- * FP32 and the D3Q7 populations g are FP32. */
+ * 136 instead of 272 bytes per site and step.  In these four the D3Q7
+ * populations g are FP32.  The last two store g in 16 bits as well, shifted so
+ * that both bulk phases are near zero: gamma_q = g_q/w_q - phi~, phi~ the
+ * phase field of the step before at the site that reads g_q (the D3Q7
+ * population of Eq. 4 streamed into it), rounded to the same 16-bit type and
+ * kept as an eighth plane; 140 bytes per site and step.  They need nx % 4 == 0
+ * and exclude density contrasts and the WENO-5 phase field.  In all six the
+ * arithmetic is FP32. */
 #define LB_F32 0          /* delta_i stored as FP32 */
 #define LB_F16_SHIFTED 1  /* delta_i stored as FP16 */
 #define LB_BF16_SHIFTED 2 /* delta_i stored as BF16 */
 #define LB_F32_MOMENTS 3  /* post-collision coefficients, FP32 */
+#define LB_F16_SHIFTED_G16 4  /* delta_i and gamma_q (and phi~) stored as FP16 */
+#define LB_BF16_SHIFTED_G16 5 /* delta_i and gamma_q (and phi~) stored as BF16 */
 
 /* ------------------------------------------------------------ forcing */
 #define LB_FORCE_NONE 0
@@ -96,7 +104,8 @@ typedef struct lb_ctx lb_ctx;
  *          sharpening flux off (then sigma must be 0)
  *   sigma  surface tension, >= 0
  *   force  NULL for no external force
- *   storage  LB_F32, LB_F16_SHIFTED, LB_BF16_SHIFTED or LB_F32_MOMENTS
+ *   storage  LB_F32, LB_F16_SHIFTED, LB_BF16_SHIFTED, LB_F32_MOMENTS,
+ *            LB_F16_SHIFTED_G16 or LB_BF16_SHIFTED_G16
  * The context owns the populations (f: 27 planes, in place with the AA access
  * pattern, or two buffers of 10 coefficient planes; g: two buffers of 7
  * planes), the reduction scratch and the device state.  Sizes: 1 <= nx, ny, nz and nx*ny*nz < 2^31 - 1 (1024^3 fits).

@@ -149,12 +149,18 @@ dim3 grid_for(const lb_ctx* c, int ty, int zc, int tx = 32) {
 }
 
 bool is_mc(const lb_ctx* c) { return c->storage == LB_F32_MOMENTS; }
+// 16-bit D3Q7 populations as well as 16-bit f (the G16 kernels)
+bool is_g16(const lb_ctx* c) { return c->storage == LB_F16_SHIFTED_G16 || c->storage == LB_BF16_SHIFTED_G16; }
+// f stored as FP16 (LB_F16_SHIFTED, LB_F16_SHIFTED_G16)
+bool is_f16(const lb_ctx* c) { return c->storage == LB_F16_SHIFTED || c->storage == LB_F16_SHIFTED_G16; }
+// bytes of one D3Q7 buffer: 7 FP32 planes, or (G16) 7 planes of gamma and one of phi~ in 16 bits
+size_t g_buf_bytes(const lb_ctx* c) { return (size_t)c->N * (is_g16(c) ? 8 * 2 : 7 * sizeof(float)); }
 
 // The paired step kernel (two x-adjacent sites per thread, packed two-lane FP32
 // arithmetic) runs the step when it is preferred and applies: a 16-bit AA
 // storage, nx a multiple of 4, the D3Q7 phase field, no density contrasts.
 bool pair_applies(const lb_ctx* c) {
-    return (c->storage == LB_F16_SHIFTED || c->storage == LB_BF16_SHIFTED) && c->nx % 4 == 0 && !c->vd && !c->fd;
+    return (c->fsize == 2 && !is_mc(c)) && c->nx % 4 == 0 && !c->vd && !c->fd;
 }
 bool use_pair(const lb_ctx* c) { return c->pair && pair_applies(c); }
 
@@ -196,6 +202,17 @@ StepArgs base_args(const lb_ctx* c) {
 float* g_plane(const lb_ctx* c, int buf, int q) { return c->g[buf] + (size_t)q * (size_t)c->N; }
 
 void set_g(StepArgs& a, const lb_ctx* c, int par, bool init = false) {
+    if (is_g16(c)) {  // planes of 2-byte values: gamma_0..6, then phi~
+        const char* gi = reinterpret_cast<const char*>(c->g[par]);
+        char* go = reinterpret_cast<char*>(c->g[par ^ 1]);
+        for (int q = 0; q < 7; ++q) {
+            a.gin[q] = reinterpret_cast<const float*>(gi + (size_t)q * (size_t)c->N * 2);
+            a.gout[q] = reinterpret_cast<float*>(go + (size_t)q * (size_t)c->N * 2);
+        }
+        a.gphi_in = gi + (size_t)7 * (size_t)c->N * 2;
+        a.gphi_out = go + (size_t)7 * (size_t)c->N * 2;
+        return;
+    }
     if (c->fd) {
         for (int q = 0; q < 7; ++q) {
             a.gin[q] = g_plane(c, 0, 0);
@@ -222,6 +239,9 @@ cudaError_t launch_any(const lb_ctx* c, int mode, int parity, int ty, dim3 grid,
                        cudaStream_t s) {
     // float4 phase-A loads need 16-byte aligned rows: nx % 4 == 0 (planes then start aligned too)
     const bool vec = (c->nx % 4) == 0;
+    if (is_g16(c))
+        return is_f16(c) ? launch_fused_g16<__half>(mode, parity, ty, grid, a, s)
+                         : launch_fused_g16<__nv_bfloat16>(mode, parity, ty, grid, a, s);
     if (c->fd || (c->vd && mode != MODE_INIT)) {
         const bool vd = c->vd && mode != MODE_INIT;
 #define LBGB_X(FT, MC)                                                                              \
@@ -283,8 +303,12 @@ int enqueue_step(lb_ctx* c, int par, cudaStream_t s, bool first = false) {
         LB_CUDA(cudaEventRecord(c->ev_start[c->ev_used], s));
     }
     if (use_pair(c)) {
-        LB_CUDA(c->storage == LB_F16_SHIFTED ? launch_fused_pair<__half>(par, c->ty, grid, a, s)
-                                             : launch_fused_pair<__nv_bfloat16>(par, c->ty, grid, a, s));
+        if (is_g16(c))
+            LB_CUDA(is_f16(c) ? launch_fused_pair_g16<__half>(par, c->ty, grid, a, s)
+                              : launch_fused_pair_g16<__nv_bfloat16>(par, c->ty, grid, a, s));
+        else
+            LB_CUDA(is_f16(c) ? launch_fused_pair<__half>(par, c->ty, grid, a, s)
+                              : launch_fused_pair<__nv_bfloat16>(par, c->ty, grid, a, s));
     } else {
         LB_CUDA(launch_any(c, MODE_STEP, is_mc(c) ? (first ? 0 : 1) : par, c->ty, grid, a, s));
     }
@@ -383,9 +407,13 @@ int tune_chunks(const lb_ctx* c, int ty, int zcs[6]) {
         case LB_F32_MOMENTS: per_sm = x ? LBGB_XO(float, true) : fused_mc_blocks_per_sm(ty, vec); break;
     }
 #undef LBGB_XO
-    if (use_pair(c))
-        per_sm = c->storage == LB_F16_SHIFTED ? fused_pair_blocks_per_sm<__half>(ty)
-                                              : fused_pair_blocks_per_sm<__nv_bfloat16>(ty);
+    if (is_g16(c))
+        per_sm = use_pair(c) ? (is_f16(c) ? fused_pair_g16_blocks_per_sm<__half>(ty)
+                                          : fused_pair_g16_blocks_per_sm<__nv_bfloat16>(ty))
+                             : (is_f16(c) ? fused_g16_blocks_per_sm<__half>(ty)
+                                          : fused_g16_blocks_per_sm<__nv_bfloat16>(ty));
+    else if (use_pair(c))
+        per_sm = is_f16(c) ? fused_pair_blocks_per_sm<__half>(ty) : fused_pair_blocks_per_sm<__nv_bfloat16>(ty);
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
         cudaGetLastError();
@@ -464,8 +492,11 @@ int lb_create(int nx, int ny, int nz, double tau, double M, double W, double sig
     if (!(W > 0)) return fail(LB_EINVAL, "W = %g must be > 0 (or +inf)", W);
     if (!(sigma >= 0) || !isfinite(sigma)) return fail(LB_EINVAL, "sigma = %g must be >= 0", sigma);
     if (isinf(W) && sigma > 0) return fail(LB_EINVAL, "sigma > 0 needs a finite W");
-    if (storage != LB_F32 && storage != LB_F16_SHIFTED && storage != LB_BF16_SHIFTED && storage != LB_F32_MOMENTS)
+    if (storage != LB_F32 && storage != LB_F16_SHIFTED && storage != LB_BF16_SHIFTED && storage != LB_F32_MOMENTS &&
+        storage != LB_F16_SHIFTED_G16 && storage != LB_BF16_SHIFTED_G16)
         return fail(LB_EINVAL, "unknown storage %d", storage);
+    if ((storage == LB_F16_SHIFTED_G16 || storage == LB_BF16_SHIFTED_G16) && nx % 4 != 0)
+        return fail(LB_EINVAL, "16-bit D3Q7 storage needs nx %% 4 == 0 (got nx = %d)", nx);
     lb_force fz;
     memset(&fz, 0, sizeof(fz));
     if (force) fz = *force;
@@ -496,8 +527,8 @@ int lb_create(int nx, int ny, int nz, double tau, double M, double W, double sig
         }
     };
     alloc(&c->f, f_bytes(c));
-    alloc((void**)&c->g[0], (size_t)c->N * 7 * sizeof(float));
-    alloc((void**)&c->g[1], (size_t)c->N * 7 * sizeof(float));
+    alloc((void**)&c->g[0], g_buf_bytes(c));
+    alloc((void**)&c->g[1], g_buf_bytes(c));
     c->npart_cap = max_blocks(c);
     alloc((void**)&c->partials, (size_t)c->npart_cap * NPART * sizeof(double));
     alloc((void**)&c->st, sizeof(DevState));
@@ -657,6 +688,7 @@ int lb_set_density(lb_ctx* c, double rho_l, double rho_g, double tau_l, double t
         !isfinite(tau_l) || !isfinite(tau_g))
         return fail(LB_EINVAL, "lb_set_density: need rho > 0 and tau > 1/2, got rho %g, %g, tau %g, %g", rho_l, rho_g,
                     tau_l, tau_g);
+    if (is_g16(c)) return fail(LB_EINVAL, "lb_set_density: density contrasts need FP32 D3Q7 populations");
     c->vd = true;
     c->rho_l = rho_l; c->rho_g = rho_g; c->tau_l = tau_l; c->tau_g = tau_g;
     drop_graph(c);  // the captured launches carry the old kernel and arguments
@@ -666,6 +698,8 @@ int lb_set_density(lb_ctx* c, double rho_l, double rho_g, double tau_l, double t
 int lb_set_phase_solver(lb_ctx* c, int solver) {
     if (!c) return fail(LB_EINVAL, "ctx is NULL");
     if (solver != LB_PHASE_LB && solver != LB_PHASE_WENO5) return fail(LB_EINVAL, "unknown phase solver %d", solver);
+    if (solver == LB_PHASE_WENO5 && is_g16(c))
+        return fail(LB_EINVAL, "the WENO-5 phase field holds no D3Q7 populations: use LB_F16_SHIFTED or LB_BF16_SHIFTED");
     if (c->initialized && (solver == LB_PHASE_WENO5) != c->fd)
         return fail(LB_ESTATE, "lb_set_phase_solver after lb_init (the state is held differently)");
     c->fd = solver == LB_PHASE_WENO5;
@@ -758,6 +792,7 @@ static size_t ckpt_f_bytes(const lb_ctx* c) {
 // The D3Q7 buffer of time t, or (finite-difference phase field) the buffer
 // whose plane 0 holds phi.
 static float* g_state(const lb_ctx* c) { return c->fd ? c->g[0] : c->g[c->t & 1]; }
+static size_t ckpt_g_bytes(const lb_ctx* c) { return g_buf_bytes(c); }
 
 static char* ckpt_f_ptr(const lb_ctx* c) {
     if (!is_mc(c)) return static_cast<char*>(c->f);
@@ -766,7 +801,7 @@ static char* ckpt_f_ptr(const lb_ctx* c) {
 
 size_t lb_state_bytes(const lb_ctx* c) {
     if (!c) return 0;
-    return sizeof(CkptHeader) + sizeof(DevState) + ckpt_f_bytes(c) + (size_t)c->N * 7 * sizeof(float);
+    return sizeof(CkptHeader) + sizeof(DevState) + ckpt_f_bytes(c) + ckpt_g_bytes(c);
 }
 
 int lb_save(lb_ctx* c, void* buf, size_t bytes) {
@@ -786,7 +821,7 @@ int lb_save(lb_ctx* c, void* buf, size_t bytes) {
     }
     h.t = c->t;
     h.f_bytes = (long long)ckpt_f_bytes(c);
-    h.g_bytes = (long long)c->N * 7 * (long long)sizeof(float);
+    h.g_bytes = (long long)ckpt_g_bytes(c);
     char* p = static_cast<char*>(buf);
     memcpy(p, &h, sizeof(h));
     p += sizeof(h);
@@ -823,7 +858,7 @@ int lb_load(lb_ctx* c, const void* buf, size_t bytes) {
         return fail(LB_EINVAL, "lb_load: checkpoint of a %dx%dx%d box in storage %d, context is %dx%dx%d in %d", h.nx,
                     h.ny, h.nz, h.storage, c->nx, c->ny, c->nz, c->storage);
     if (h.t < 0 || bytes < lb_state_bytes(c) || h.f_bytes != (long long)ckpt_f_bytes(c) ||
-        h.g_bytes != (long long)c->N * 7 * (long long)sizeof(float))
+        h.g_bytes != (long long)ckpt_g_bytes(c))
         return fail(LB_EINVAL, "lb_load: truncated or inconsistent checkpoint");
     c->t = h.t;  // selects the buffers the state goes to
     const char* p = static_cast<const char*>(buf) + sizeof(h);
@@ -840,7 +875,8 @@ int lb_load(lb_ctx* c, const void* buf, size_t bytes) {
 double lb_bytes_per_site(const lb_ctx* c) {
     if (!c) return 0.0;
     // phase part: D3Q7 read + write, or (finite-difference phase field) phi read + u written
-    const double ph = c->fd ? 4.0 + 3.0 * 4.0 : 7.0 * 2.0 * 4.0;
+    // (G16: gamma_0..6 and phi~, 2 bytes each, read + write)
+    const double ph = c->fd ? 4.0 + 3.0 * 4.0 : is_g16(c) ? 8.0 * 2.0 * 2.0 : 7.0 * 2.0 * 4.0;
     if (is_mc(c)) return 10.0 * 2.0 * 4.0 + ph;
     return 27.0 * 2.0 * (double)c->fsize + ph;
 }
@@ -887,8 +923,8 @@ int lb_tune(lb_ctx* c, int steps) {
     if (in_place) {
         s = c;
         LB_CUDA(cudaMemsetAsync(c->f, 0, f_bytes(c), c->stream));
-        LB_CUDA(cudaMemsetAsync(c->g[0], 0, (size_t)c->N * 7 * sizeof(float), c->stream));
-        LB_CUDA(cudaMemsetAsync(c->g[1], 0, (size_t)c->N * 7 * sizeof(float), c->stream));
+        LB_CUDA(cudaMemsetAsync(c->g[0], 0, g_buf_bytes(c), c->stream));
+        LB_CUDA(cudaMemsetAsync(c->g[1], 0, g_buf_bytes(c), c->stream));
         LB_CUDA(cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
         c->initialized = true;
         c->t = 0;

@@ -350,6 +350,8 @@ int lb_batch_create(int count, const int* dims, const double* tau, const double*
     if (!out) return bfail(LB_EINVAL, "out is NULL");
     *out = nullptr;
     if (count < 1 || !dims || !tau || !M || !W || !sigma) return bfail(LB_EINVAL, "lb_batch_create: bad arguments");
+    if (storage == LB_F16_SHIFTED_G16 || storage == LB_BF16_SHIFTED_G16)
+        return bfail(LB_EINVAL, "the 16-bit D3Q7 storage runs single boxes only (lb_create)");
     if (storage != LB_F32 && storage != LB_F16_SHIFTED && storage != LB_BF16_SHIFTED && storage != LB_F32_MOMENTS)
         return bfail(LB_EINVAL, "unknown storage %d", storage);
     lb_batch* B = new lb_batch();

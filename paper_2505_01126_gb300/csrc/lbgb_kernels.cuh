@@ -90,6 +90,12 @@ struct StepArgs {
     // (rho - rho_ref) gb (gb = 0 without gravity)
     float rho_g, drho, tau_g, dtau;
     float gb0, gb1, gb2, rho_ref;
+    // 16-bit D3Q7 storage (kernels with G16): gin/gout then point at planes of
+    // the storage type holding gamma_q = g_q/w_q - phi~, and these at the
+    // plane of phi~, each site's phase field of the previous step rounded to
+    // the storage type (read at t, written at t+1)
+    const void* gphi_in;
+    void* gphi_out;
 };
 
 // ---------------------------------------------------------- storage codecs
@@ -119,6 +125,34 @@ struct Codec<float> {
     static __device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
 };
 
+// Bit-pattern views of the 16-bit types (the 16-bit D3Q7 storage keeps phi~
+// and staged values as raw bits in shared memory): dec2u widens the pair held
+// in a 32-bit word (first value in the low half), enc2u rounds a pair into
+// one, decu / encu do the same for one value.
+template <class T, class R2>
+struct Bits16 {
+    static __device__ __forceinline__ float2 dec2u(unsigned u) {
+        union { unsigned u; R2 r; } c;
+        c.u = u;
+        return Codec<T>::dec2(c.r);
+    }
+    static __device__ __forceinline__ unsigned enc2u(float2 v) {
+        union { unsigned u; R2 r; } c;
+        c.r = Codec<T>::enc2(v);
+        return c.u;
+    }
+    static __device__ __forceinline__ float decu(unsigned short h) {
+        union { unsigned short u; T r; } c;
+        c.u = h;
+        return Codec<T>::dec(c.r);
+    }
+    static __device__ __forceinline__ unsigned short encu(float v) {
+        union { unsigned short u; T r; } c;
+        c.r = Codec<T>::enc(v);
+        return c.u;
+    }
+};
+
 template <>
 struct Codec<__half> {
     using raw = __half;
@@ -133,6 +167,10 @@ struct Codec<__half> {
     static __device__ __forceinline__ void st2(__half* p, float2 v) {
         *reinterpret_cast<__half2*>(p) = __float22half2_rn(v);
     }
+    static __device__ __forceinline__ raw enc(float v) { return __float2half_rn(v); }
+    static __device__ __forceinline__ raw2 enc2(float2 v) { return __float22half2_rn(v); }
+    static __device__ __forceinline__ raw lo(raw2 r) { return __low2half(r); }
+    static __device__ __forceinline__ raw hi(raw2 r) { return __high2half(r); }
 };
 
 template <>
@@ -151,6 +189,24 @@ struct Codec<__nv_bfloat16> {
     static __device__ __forceinline__ void st2(__nv_bfloat16* p, float2 v) {
         *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v);
     }
+    static __device__ __forceinline__ raw enc(float v) { return __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ raw2 enc2(float2 v) { return __float22bfloat162_rn(v); }
+    static __device__ __forceinline__ raw lo(raw2 r) { return __low2bfloat16(r); }
+    static __device__ __forceinline__ raw hi(raw2 r) { return __high2bfloat16(r); }
+};
+
+template <class T>
+struct Bits;
+template <>
+struct Bits<__half> : Bits16<__half, __half2> {};
+template <>
+struct Bits<__nv_bfloat16> : Bits16<__nv_bfloat16, __nv_bfloat162> {};
+template <>
+struct Bits<float> {  // never used with FP32 storage; present so that the tile body compiles
+    static __device__ __forceinline__ float2 dec2u(unsigned) { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ unsigned enc2u(float2) { return 0u; }
+    static __device__ __forceinline__ float decu(unsigned short) { return 0.f; }
+    static __device__ __forceinline__ unsigned short encu(float) { return 0; }
 };
 
 __device__ __forceinline__ int wrap_mod(int v, int n) {
@@ -162,6 +218,11 @@ __device__ __forceinline__ int wrap_mod(int v, int n) {
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+// 8-byte asynchronous global -> shared copy (both addresses 8-byte aligned).
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 // 4-byte asynchronous global -> shared copy (any 4-byte aligned address).
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
@@ -583,8 +644,10 @@ __device__ __forceinline__ void pull_column(LD ld, float& vm, float& v0, float& 
 // two sites each; nx a multiple of 4).  Blocks per SM that fit in registers
 // and shared memory: three of TY = 4 (168 registers, none spilled), two of
 // TY = 8.
+// G16: the D3Q7 populations in the 16-bit storage type as well (see the tile
+// body), for the AA storages FT = __half or __nv_bfloat16, nx a multiple of 4.
 template <class FT, int TY, int MODE, int PAR, bool VEC, bool MC = false, bool VD = false, bool PF = false,
-          bool PAIR = false>
+          bool PAIR = false, bool G16 = false>
 __global__ void __launch_bounds__(32 * TY, PAIR ? (TY == 4 ? 3 : 2) : (TY >= 16 ? 1 : 512 / (32 * TY)))
 fused_step_kernel(const StepArgs a) {
 #define TILE_BX blockIdx.x
@@ -649,6 +712,8 @@ struct BoxTileArgs {
     PlaneSet<float> cout;
     float rho_g, drho, tau_g, dtau;  // density and viscosity contrasts (VD); no buoyancy in a batch
     float gb0, gb1, gb2, rho_ref;
+    const void* gphi_in;             // 16-bit D3Q7 storage: not in a batch (null)
+    void* gphi_out;
 };
 
 // Persistent kernel: the grid strides over the work list of all boxes.  With
@@ -676,6 +741,8 @@ batch_step_kernel(const __grid_constant__ BatchArgs b) {
         t.cout = PlaneSet<float>{MC_ ? b.c_out + d.c_off : nullptr, (long long)d.N};
         t.rho_g = d.rho_g; t.drho = d.drho; t.tau_g = d.tau_g; t.dtau = d.dtau;
         t.gb0 = t.gb1 = t.gb2 = t.rho_ref = 0.f;
+        t.gphi_in = nullptr;
+        t.gphi_out = nullptr;
         const int local = item - d.item0;
         const int tbx = local % d.tiles_x, rest = local / d.tiles_x;
         const int tby = rest % d.tiles_y, tbz = rest / d.tiles_y;
@@ -686,6 +753,7 @@ batch_step_kernel(const __grid_constant__ BatchArgs b) {
             constexpr bool VD = VD_;
             constexpr bool PF = false;
             constexpr bool PAIR = PAIR_;
+            constexpr bool G16 = false;
 #define TILE_BX tbx
 #define TILE_BY tby
 #define TILE_BZ tbz
@@ -735,6 +803,18 @@ template <class FT>
 cudaError_t launch_fused_pair(int parity, int ty, dim3 grid, const StepArgs& a, cudaStream_t st);
 template <class FT>
 int fused_pair_blocks_per_sm(int ty);
+// The kernels of the 16-bit D3Q7 storage (G16; FT __half or __nv_bfloat16,
+// nx % 4 == 0): one-site kernels for MODE_INIT (ty 8), MODE_MOMENTS (ty 8) and
+// MODE_STEP (ty 4 or 8), defined in lbgb_step_g16_*.cu; the paired step kernel
+// (64 x ty tiles, ty 4 or 8), defined in lbgb_step_pair_g16_*.cu.
+template <class FT>
+cudaError_t launch_fused_g16(int mode, int parity, int ty, dim3 grid, const StepArgs& a, cudaStream_t st);
+template <class FT>
+int fused_g16_blocks_per_sm(int ty);
+template <class FT>
+cudaError_t launch_fused_pair_g16(int parity, int ty, dim3 grid, const StepArgs& a, cudaStream_t st);
+template <class FT>
+int fused_pair_g16_blocks_per_sm(int ty);
 // The batch kernel with the paired tile body (16-bit storages; every box nx % 4 == 0).
 template <class FT>
 cudaError_t launch_batch_pair(int parity, int ty, int blocks, const BatchArgs& b, cudaStream_t st);

@@ -19,9 +19,11 @@ LIB_PATH = os.path.join(_HERE, "csrc", "liblbgb.so")
 
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENONFINITE, LB_ESTATE = 0, -1, -2, -3, -4, -5
 LB_F32, LB_F16_SHIFTED, LB_BF16_SHIFTED, LB_F32_MOMENTS = 0, 1, 2, 3
+LB_F16_SHIFTED_G16, LB_BF16_SHIFTED_G16 = 4, 5
 LB_FORCE_NONE, LB_FORCE_CONST, LB_FORCE_ABC, LB_FORCE_LINEAR = 0, 1, 2, 3
 
-STORAGE = {"f32": LB_F32, "f16": LB_F16_SHIFTED, "bf16": LB_BF16_SHIFTED, "moments": LB_F32_MOMENTS}
+STORAGE = {"f32": LB_F32, "f16": LB_F16_SHIFTED, "bf16": LB_BF16_SHIFTED, "moments": LB_F32_MOMENTS,
+           "f16g": LB_F16_SHIFTED_G16, "bf16g": LB_BF16_SHIFTED_G16}
 
 
 class LBError(RuntimeError):

@@ -32,7 +32,7 @@ def make(lbgb, w, storage):
                     storage=storage)
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16", "moments"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "moments", "f16g"])
 @pytest.mark.parametrize("split", [0, 25, 26])
 def test_interrupted_run_equals_uninterrupted(lbgb, storage, split):
     w = inputs.bubbly_hit(32, 1, 8.0, seed=5)

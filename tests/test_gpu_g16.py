@@ -1,0 +1,158 @@
+"""16-bit D3Q7 storage (LB_F16_SHIFTED_G16, LB_BF16_SHIFTED_G16): f and the
+phase-field populations g both in 16 bits, FP32 arithmetic.
+
+g_q is stored as gamma_q = g_q/w_q - phi~, phi~ the phase field of the step
+before at the site that reads the value, rounded to the storage type and kept
+as an eighth plane; the writer subtracts the reader's phi~, which phase A has
+computed on the tile's halo.  Each step rounds the seven D3Q7 values to 11
+(FP16) or 8 (BF16) significant bits: |gamma| stays below about 0.3 (the
+interface jump of phi over one lattice link plus the flux j), so one rounding
+moves g_q by at most w_q 0.3 2^-12 = 9e-6 (FP16), and phi by a few times that
+per step; over 50 steps, with the diffusion of Eq. 4 spreading it, the fields
+stay within 5e-4 of the oracle (FP16; measured up to 3.0e-4 on sharp 50-step
+boxes) and 5e-3 (BF16; measured up to 2.0e-3).  The rounding errors of the six
+moving values are taken out of the resting one before it is rounded, so the
+phase mass a site sends on changes only by the rounding of gamma_0.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2505_01126_gb300 import inputs
+from test_gpu_parity import max_err, smooth_fields
+
+pytestmark = pytest.mark.gpu
+
+BOUND = {"f16g": 5e-4, "bf16g": 5e-3}
+SHAPES = [((6, 5, 4), (8, 3)), ((9, 13, 8), (4, 4)), ((11, 17, 36), (8, 5)), ((7, 9, 100), (8, 32)),
+          ((40, 12, 64), (4, 16))]
+
+
+@pytest.fixture(scope="module")
+def lbgb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_01126_gb300 import build
+
+    build.build()
+    from paper_2505_01126_gb300 import lbgb as mod
+
+    return mod
+
+
+_REF = {}
+
+
+def oracle_fields(orc, shape, phi, u, steps=50, tau=0.7, sigma=0.02, **force):
+    key = (shape, steps, tau, sigma, tuple(sorted(force.items())))
+    if key not in _REF:
+        nz, ny, nx = shape
+        o = orc.Oracle(nx, ny, nz, tau, 0.1, 3.0, sigma, **force)
+        o.init(phi.astype(np.float64), u.astype(np.float64))
+        o.step(steps)
+        _REF[key] = (o.moments(), o.diagnostics())
+        o.close()
+    return _REF[key]
+
+
+def run(lbgb, shape, storage, steps, phi, u, pair, tile=None, force=None, tau=0.7, sigma=0.02):
+    nz, ny, nx = shape
+    b = lbgb.Box(nx, ny, nz, tau, 0.1, 3.0, sigma, force=force, storage=storage)
+    b.set_pairing(pair)
+    assert b.paired == pair
+    if tile:
+        b.set_tile(*tile)
+    b.init(phi, u)
+    b.step(steps)
+    out = b.moments_numpy(), b.diagnostics()
+    b.close()
+    return out
+
+
+@pytest.mark.parametrize("storage", ["f16g", "bf16g"])
+@pytest.mark.parametrize("shape,tile", SHAPES)
+def test_g16_against_oracle_paired_and_one_site(lbgb, orc, storage, shape, tile):
+    """Both AA parities, x wrap-around on both sites of a pair (nx = 4, 8), ragged
+    last tiles in x (36, 100) and y, both tile heights: 50 steps in the paired and
+    the one-site kernel, each against the oracle and against each other."""
+    phi, u = smooth_fields(shape, sum(shape) + 1)
+    want, dw = oracle_fields(orc, shape, phi, u)
+    (gp, dp) = run(lbgb, shape, storage, 50, phi, u, True, tile)
+    (gs, ds) = run(lbgb, shape, storage, 50, phi, u, False, tile)
+    ep, es = max_err(gp, want), max_err(gs, want)
+    assert max(ep) <= BOUND[storage] and max(es) <= BOUND[storage], (ep, es)
+    d = max_err(gp, [x.astype(np.float64) for x in gs])
+    assert max(d) <= BOUND[storage], d
+    assert np.isfinite(dp).all() and np.isfinite(ds).all()
+
+
+@pytest.mark.parametrize("kind", ["const", "abc", "linear"])
+def test_g16_forcing_kinds(lbgb, orc, kind):
+    shape = (12, 20, 36)
+    phi, u = smooth_fields(shape, 3)
+    f = {"const": dict(force_kind=1, g=(1e-5, -2e-5, 5e-6)),
+         "abc": dict(force_kind=2, A_abc=2e-5, kf=2 * math.pi / 12),
+         "linear": dict(force_kind=3, T_relax=20.0)}[kind]
+    want, do = oracle_fields(orc, shape, phi, u, tau=0.6, sigma=0.01, **f)
+    fk = lbgb.Force(kind=f["force_kind"], g=f.get("g", (0, 0, 0)), A=f.get("A_abc", 0.0), kf=f.get("kf", 0.0),
+                    T_relax=f.get("T_relax", 100.0))
+    (got, dg) = run(lbgb, shape, "f16g", 50, phi, u, True, (8, 5), force=fk, tau=0.6, sigma=0.01)
+    assert max(max_err(got, want)) <= BOUND["f16g"]
+    if kind == "linear":
+        assert abs(dg[4] - do[4]) <= 0.02 * abs(do[4])
+
+
+def test_g16_hit_64_against_oracle(lbgb, orc):
+    """64^3 bubbly forced HIT (two bubbles R = 10, tau 0.51, linear forcing), 50
+    steps in the tuned kernel and launch shape (measured: 5.1e-5 FP16, 4.6e-4 BF16)."""
+    w = inputs.bubbly_hit(64, 2, 10.0, seed=2)
+    o = orc.Oracle(64, 64, 64, w.tau, w.M, w.W, w.sigma, force_kind=3, T_relax=w.T_relax)
+    o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
+    o.step(50)
+    want = o.moments()
+    o.close()
+    for st, bound in (("f16g", 2e-4), ("bf16g", 2e-3)):
+        b = lbgb.Box(64, 64, 64, w.tau, w.M, w.W, w.sigma, force=lbgb.Force(kind=3, T_relax=w.T_relax),
+                     storage=st)
+        b.tune(2)
+        b.init(w.phi, w.u)
+        b.step(50)
+        got = b.moments_numpy()
+        b.close()
+        assert max(max_err(got, want)) <= bound, st
+
+
+def test_g16_moments_and_reductions_agree(lbgb):
+    """lb_moments decodes phi like the step: its sum equals the step's FP64 phase
+    mass (the step's sum is over the phi it used, one step earlier)."""
+    w = inputs.bubbly_hit(32, 1, 8.0, seed=7)
+    b = lbgb.Box(32, 32, 32, w.tau, w.M, w.W, w.sigma, storage="f16g")
+    b.init(w.phi, w.u)
+    b.step(9)
+    phi9 = b.moments_numpy()[2].astype(np.float64).sum()
+    b.step(1)
+    assert abs(b.diagnostics()[0] - phi9) <= 1e-6 * phi9
+    b.close()
+
+
+def test_g16_interface(lbgb):
+    """Where the 16-bit D3Q7 storage applies, and its byte count."""
+    b = lbgb.Box(8, 8, 8, 0.8, 0.1, 3.0, 0.01, storage="f16g")
+    assert b.paired and b.bytes_per_site == 27 * 2 * 2 + 8 * 2 * 2
+    b.set_pairing(False)  # the one-site kernel runs it too
+    assert not b.paired
+    for call in (lambda: b.set_density(10.0, 1.0, 0.8, 0.8), lambda: b.set_phase_solver("weno5")):
+        with pytest.raises(lbgb.LBError) as e:
+            call()
+        assert e.value.code == lbgb.LB_EINVAL
+    b.close()
+    for nx in (6, 10):
+        with pytest.raises(lbgb.LBError) as e:
+            lbgb.Box(nx, 4, 4, 0.8, 0.1, 3.0, 0.01, storage="bf16g")
+        assert e.value.code == lbgb.LB_EINVAL
+    with pytest.raises(lbgb.LBError) as e:
+        lbgb.Batch([(8, 8, 8)], 0.8, 0.1, 3.0, 0.01, storage="f16g")
+    assert e.value.code == lbgb.LB_EINVAL
