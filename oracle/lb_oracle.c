@@ -856,6 +856,21 @@ void orc_set_populations(orc_state* s, const double* f, const double* g) {
     if (g) memcpy(s->g, g, (size_t)(7 * s->N) * sizeof(double));
 }
 
+/* The stored phase field of the finite-difference solver (the state when
+ * orc_set_phase_solver selected WENO-5); -1 when that solver is not selected.
+ * Test access only: the tests round the state to FP32 storage between steps. */
+int orc_get_phase(const orc_state* s, double* phi) {
+    if (!s->fd) return -1;
+    memcpy(phi, s->phs, (size_t)s->N * sizeof(double));
+    return 0;
+}
+
+int orc_set_phase(orc_state* s, const double* phi) {
+    if (!s->fd) return -1;
+    memcpy(s->phs, phi, (size_t)s->N * sizeof(double));
+    return 0;
+}
+
 void orc_last_force(const orc_state* s, double* F) {
     memcpy(F, s->F, (size_t)(3 * s->N) * sizeof(double));
 }

@@ -68,6 +68,8 @@ double orc_weno5_face(const double v[5]);
 /* Raw populations: f is 27N in the oracle's own direction order (see
  * orc_lattice27), g is 7N in the order of orc_lattice7. */
 void orc_get_populations(const orc_state* s, double* f, double* g);
+int orc_get_phase(const orc_state* s, double* phi);
+int orc_set_phase(orc_state* s, const double* phi);
 void orc_set_populations(orc_state* s, const double* f, const double* g);
 /* Body force F of the last step (3N). */
 void orc_last_force(const orc_state* s, double* F);

@@ -61,6 +61,8 @@ def _load():
             lib.orc_time.restype = ctypes.c_longlong
             lib.orc_get_populations.argtypes = [ctypes.c_void_p, _dp, _dp]
             lib.orc_set_populations.argtypes = [ctypes.c_void_p, _dp, _dp]
+            lib.orc_get_phase.argtypes = [ctypes.c_void_p, _dp]
+            lib.orc_set_phase.argtypes = [ctypes.c_void_p, _dp]
             lib.orc_last_force.argtypes = [ctypes.c_void_p, _dp]
             lib.orc_lattice27.argtypes = [ctypes.POINTER(ctypes.c_int), _dp]
             lib.orc_lattice7.argtypes = [ctypes.POINTER(ctypes.c_int), _dp]
@@ -245,7 +247,20 @@ class Oracle:
         return f, g
 
     def set_populations(self, f, g):
-        self._lib.orc_set_populations(self._h, _ptr(_f64(f)), _ptr(_f64(g)))
+        """f (27 planes) and g (7 planes); either may be None to keep it."""
+        self._lib.orc_set_populations(self._h, None if f is None else _ptr(_f64(f)),
+                                      None if g is None else _ptr(_f64(g)))
+
+    def phase_field(self) -> np.ndarray:
+        """The stored phi of the WENO-5 phase solver (the state that solver steps)."""
+        phi = np.zeros(self.shape)
+        if self._lib.orc_get_phase(self._h, _ptr(phi)) != 0:
+            raise RuntimeError("phase_field: the WENO-5 phase solver is not selected")
+        return phi
+
+    def set_phase_field(self, phi):
+        if self._lib.orc_set_phase(self._h, _ptr(_f64(phi))) != 0:
+            raise RuntimeError("set_phase_field: the WENO-5 phase solver is not selected")
 
     def last_force(self) -> np.ndarray:
         F = np.zeros((3,) + self.shape)

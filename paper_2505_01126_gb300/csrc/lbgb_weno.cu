@@ -25,21 +25,36 @@ namespace lbgb {
 namespace {
 
 // A block takes a 32 x 8 column tile and marches over a z-chunk: phi planes
-// (with a halo of 3 in x and y) in a ring of 8, J planes (halo 1) in a ring
-// of 4.  Per plane z: J of plane z + 1; barrier; the x- and y-face fluxes of
-// plane z, each once, spread over the block (264 + 288 faces), and per thread
-// D lap - kappa div J and the flux through its column's upper z face (the
-// lower one carried from the plane below); barrier; the stage combination,
-// then the asynchronous copy of plane z + 4.
+// (with a halo of 3 in x and y) in a ring of 8.  The lattice stencils are
+// separable, so each plane's in-plane parts are formed once and combined
+// across planes:
+//   - on the halo-1 ring of the tile, per plane: Gx2 = sum_b w_b dx phi,
+//     Gy2 = sum_a w_a dy phi (central differences, weights (1, 4, 1) across)
+//     and S2 = sum_ab w_a w_b (phi - phi_c), phi_c the site's own value, in a
+//     ring of five planes in shared memory; then
+//       grad_x = (1/72) sum_c w_c Gx2(z + c),  likewise y,
+//       grad_z = (1/72) (S2(z+1) - S2(z-1) + 36 (phi_c(z+1) - phi_c(z-1))),
+//       lap    = sum_c w_c (S2(z + c) + 36 (phi_c(z + c) - phi_c(z))),
+//     every term a difference, so that nearly uniform phi keeps its FP32
+//     accuracy;
+//   - J = max(phi (1 - phi), 0) n on the halo-1 plane (one plane at a time),
+//     and for the thread's own site the in-plane parts of div J:
+//     A(z) = sum_b w_b dx J_x + sum_a w_a dy J_y and B(z) = sum_ab w_a w_b J_z,
+//     carried in registers: div J = sum_c w_c A(z + c) + B(z + 1) - B(z - 1).
+// Per plane z: J of plane z + 1; barrier; the x- and y-face fluxes of plane z,
+// each once, spread over the block (264 + 288 faces), the partials of plane
+// z + 3, A and B of plane z + 1, D lap - kappa div J and the flux through the
+// column's upper z face (the lower one carried from the plane below);
+// barrier; the stage combination, then the asynchronous copy of plane z + 4.
 constexpr int TX = 32, TY = 8, WH = 3;
 constexpr int PX = TX + 2 * WH, PY = TY + 2 * WH, NP = PX * PY;  // 38 x 14
 constexpr int QX = TX + 2, QY = TY + 2, NQ = QX * QY;            // 34 x 10
 constexpr int WNT = TX * TY;                                       // 256 threads
 constexpr int NPL = (NP + WNT - 1) / WNT;                          // phi elements per thread
-constexpr int NJL = (NQ + WNT - 1) / WNT;                          // J elements per thread
+constexpr int NJL = (NQ + WNT - 1) / WNT;                          // halo-1 sites per thread
 constexpr int NFX = TY * (TX + 1), NFY = (TY + 1) * TX;            // faces per plane
 constexpr int NFL = (NFY + WNT - 1) / WNT;                         // faces per thread (>= x's)
-constexpr int PR = 8, JR = 4;                                      // ring sizes (powers of 2)
+constexpr int PR = 8, GR = 5;                                      // phi ring, partials ring
 static_assert(NFX <= NFL * WNT, "x faces fit the per-thread face slots");
 
 __device__ __forceinline__ float weno5(float vm2, float vm1, float v0, float v1, float v2) {
@@ -71,12 +86,15 @@ __device__ __forceinline__ float face_flux(const float (&v)[6], float ul, float 
     return uf * weno5(up ? v[0] : v[5], up ? v[1] : v[4], up ? v[2] : v[3], up ? v[3] : v[2], up ? v[4] : v[1]);
 }
 
+__device__ __forceinline__ int g5(int p) { return (p + 10) % GR; }  // partials ring slot, planes p >= -10
+
 __global__ void __launch_bounds__(WNT, 4) weno_stage_kernel(const float* __restrict__ pin, const float* phin,
                                                          const float* __restrict__ ux, const float* __restrict__ uy,
                                                          const float* __restrict__ uz, float* out, int nx, int ny,
                                                          int nz, int zc, float D, float kap, int stage) {
     __shared__ float s_p[PR][PY][PX];
-    __shared__ float s_J[JR][3][QY][QX];
+    __shared__ float s_G[GR][3][NQ];  // Gx2, Gy2, S2 of a plane on the halo-1 ring
+    __shared__ float s_J[3][QY][QX];  // J of one plane on the halo-1 ring
     __shared__ float s_Fx[TY][TX + 1];
     __shared__ float s_Fy[TY + 1][TX];
     const int tid = threadIdx.x;
@@ -85,8 +103,8 @@ __global__ void __launch_bounds__(WNT, 4) weno_stage_kernel(const float* __restr
     const int z1 = min(z0 + zc, nz);
     const long long plane = (long long)nx * ny;
 
-    // fixed in-plane offsets: this thread's phi-plane elements, J elements,
-    // faces (left/right site of each), and its own column
+    // fixed in-plane offsets: this thread's phi-plane elements, faces (left and
+    // right site of each) and its own column
     int p_off[NPL], p_dst[NPL];
 #pragma unroll
     for (int k = 0; k < NPL; ++k) {
@@ -123,8 +141,31 @@ __global__ void __launch_bounds__(WNT, 4) weno_stage_kernel(const float* __restr
             if (p_dst[k] >= 0) cp_async4(dst + p_dst[k], src + p_off[k]);
         cp_async_commit();
     };
-    // J of plane zp on the halo-1 ring, from phi planes zp - 1 .. zp + 1
+    // in-plane partials of plane zp on the halo-1 ring (from phi plane zp)
+    auto partials = [&](int zp) {
+        const float(*P)[PX] = s_p[zp & (PR - 1)];
+        float* G = &s_G[g5(zp)][0][0];
+#pragma unroll
+        for (int k = 0; k < NJL; ++k) {
+            const int i = tid + k * WNT;
+            if (i >= NQ) continue;
+            const int qy = i / QX, qx = i - (i / QX) * QX;
+            const int cy = qy + 2, cx = qx + 2;
+            const float pc = P[cy][cx];
+            const float mm = P[cy - 1][cx - 1], m0 = P[cy - 1][cx], mp = P[cy - 1][cx + 1];
+            const float om = P[cy][cx - 1], op = P[cy][cx + 1];
+            const float pm = P[cy + 1][cx - 1], p0 = P[cy + 1][cx], pp = P[cy + 1][cx + 1];
+            G[i] = fmaf(4.f, op - om, (mp - mm) + (pp - pm));           // Gx2
+            G[NQ + i] = fmaf(4.f, p0 - m0, (pm - mm) + (pp - mp));      // Gy2
+            G[2 * NQ + i] = fmaf(4.f, (m0 - pc) + (p0 - pc) + (om - pc) + (op - pc),
+                                 ((mm - pc) + (mp - pc)) + ((pm - pc) + (pp - pc)));  // S2
+        }
+    };
+    // J of plane zp on the halo-1 ring, from the partials of planes zp - 1 .. zp + 1
     auto make_J = [&](int zp) {
+        const float* Gm = &s_G[g5(zp - 1)][0][0];
+        const float* G0 = &s_G[g5(zp)][0][0];
+        const float* Gp = &s_G[g5(zp + 1)][0][0];
         const float(*Pm)[PX] = s_p[(zp - 1) & (PR - 1)];
         const float(*P0)[PX] = s_p[zp & (PR - 1)];
         const float(*Pp)[PX] = s_p[(zp + 1) & (PR - 1)];
@@ -134,34 +175,34 @@ __global__ void __launch_bounds__(WNT, 4) weno_stage_kernel(const float* __restr
             if (i >= NQ) continue;
             const int qy = i / QX, qx = i - (i / QX) * QX;
             const int cy = qy + 2, cx = qx + 2;
-            float gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-            for (int b = -1; b <= 1; ++b) {
-                const float wb = b == 0 ? 4.f : 1.f;
-                // along x and y: transverse (y or x, z) weights, z from the three planes
-                gx = fmaf(wb, (Pm[cy + b][cx + 1] - Pm[cy + b][cx - 1]) + (Pp[cy + b][cx + 1] - Pp[cy + b][cx - 1]),
-                          gx);
-                gx = fmaf(4.f * wb, P0[cy + b][cx + 1] - P0[cy + b][cx - 1], gx);
-                gy = fmaf(wb, (Pm[cy + 1][cx + b] - Pm[cy - 1][cx + b]) + (Pp[cy + 1][cx + b] - Pp[cy - 1][cx + b]),
-                          gy);
-                gy = fmaf(4.f * wb, P0[cy + 1][cx + b] - P0[cy - 1][cx + b], gy);
-#pragma unroll
-                for (int a = -1; a <= 1; ++a)
-                    gz = fmaf(wb * (a == 0 ? 4.f : 1.f), Pp[cy + b][cx + a] - Pm[cy + b][cx + a], gz);
-            }
-            gx *= 1.f / 72.f;
-            gy *= 1.f / 72.f;
-            gz *= 1.f / 72.f;
+            const float gx = fmaf(4.f, G0[i], Gm[i] + Gp[i]) * (1.f / 72.f);
+            const float gy = fmaf(4.f, G0[NQ + i], Gm[NQ + i] + Gp[NQ + i]) * (1.f / 72.f);
+            const float gz = fmaf(36.f, Pp[cy][cx] - Pm[cy][cx], Gp[2 * NQ + i] - Gm[2 * NQ + i]) * (1.f / 72.f);
             const float m = sqrtf(gx * gx + gy * gy + gz * gz);
             const float p = P0[cy][cx];
             const float w = __fdividef(fmaxf(p * (1.f - p), 0.f), fmaxf(m, 1e-10f));
-            s_J[zp & (JR - 1)][0][qy][qx] = w * gx;
-            s_J[zp & (JR - 1)][1][qy][qx] = w * gy;
-            s_J[zp & (JR - 1)][2][qy][qx] = w * gz;
+            s_J[0][qy][qx] = w * gx;
+            s_J[1][qy][qx] = w * gy;
+            s_J[2][qy][qx] = w * gz;
         }
+    };
+    // the in-plane parts of div J at this thread's site, from the J plane in place
+    const int jy = ly + 1, jx = lx + 1;
+    auto divJ_parts = [&](float& A, float& B) {
+        const float(*J0)[QX] = s_J[0];
+        const float(*J1)[QX] = s_J[1];
+        const float(*J2)[QX] = s_J[2];
+        A = fmaf(4.f, J0[jy][jx + 1] - J0[jy][jx - 1],
+                 (J0[jy - 1][jx + 1] - J0[jy - 1][jx - 1]) + (J0[jy + 1][jx + 1] - J0[jy + 1][jx - 1]));
+        A += fmaf(4.f, J1[jy + 1][jx] - J1[jy - 1][jx],
+                  (J1[jy + 1][jx - 1] - J1[jy - 1][jx - 1]) + (J1[jy + 1][jx + 1] - J1[jy - 1][jx + 1]));
+        B = fmaf(4.f, fmaf(4.f, J2[jy][jx], J2[jy][jx - 1] + J2[jy][jx + 1]),
+                 (fmaf(4.f, J2[jy - 1][jx], J2[jy - 1][jx - 1] + J2[jy - 1][jx + 1]) +
+                  fmaf(4.f, J2[jy + 1][jx], J2[jy + 1][jx - 1] + J2[jy + 1][jx + 1])));
     };
     // flux through the z face zf + 1/2 of this thread's column
     const int pcy = ly + WH, pcx = lx + WH;
+    const int gq = (ly + 1) * QX + (lx + 1);  // own site on the halo-1 ring
     auto z_flux = [&](int zf, float ul, float ur) {
         float v[6];
 #pragma unroll
@@ -169,12 +210,21 @@ __global__ void __launch_bounds__(WNT, 4) weno_stage_kernel(const float* __restr
         return face_flux(v, ul, ur);
     };
 
-    // prologue: phi planes z0 - 3 .. z0 + 3, J of z0 - 1 and z0, the z face below z0
+    // prologue: phi planes z0 - 3 .. z0 + 3, partials of z0 - 2 .. z0 + 2, J and
+    // the div J parts of z0 - 1 and z0, the z face below z0
     for (int zp = z0 - WH; zp <= z0 + WH; ++zp) load_plane(zp);
     cp_async_wait<0>();
     __syncthreads();
+    for (int zp = z0 - 2; zp <= z0 + 2; ++zp) partials(zp);
+    __syncthreads();
+    float Am, Bm, A0, B0;  // div J parts of the planes below and at the current one
     make_J(z0 - 1);
+    __syncthreads();
+    divJ_parts(Am, Bm);
+    __syncthreads();
     make_J(z0);
+    __syncthreads();
+    divJ_parts(A0, B0);
     float uzc = __ldg(uz + (long long)wrap_mod(z0, nz) * plane + own);  // uz of the current plane
     float fzm = z_flux(z0 - 1, __ldg(uz + (long long)wrap_mod(z0 - 1, nz) * plane + own), uzc);
     // the face velocities of a plane (left and right site of each x and y face)
@@ -193,6 +243,7 @@ __global__ void __launch_bounds__(WNT, 4) weno_stage_kernel(const float* __restr
     };
     load_u(z0);
     float uzn = __ldg(uz + (long long)wrap_mod(z0 + 1, nz) * plane + own);
+    __syncthreads();  // the J plane is rewritten below
 
     for (int z = z0; z < z1; ++z) {
         make_J(z + 1);
@@ -219,37 +270,19 @@ __global__ void __launch_bounds__(WNT, 4) weno_stage_kernel(const float* __restr
                 (&s_Fy[0][0])[fy_i[k]] = face_flux(v, vyl[k], vyr[k]);
             }
         }
-        // D lap(p) - kappa div(J) at (x, y, z), the 26 neighbours with weights (1, 4, 1)^3 / 216
-        float lap = 0.f, dj = 0.f;
+        if (z + 3 <= z1 + 1) partials(z + 3);  // make_J(z + 2) of the next plane reads it
+        float Ap, Bp;
+        divJ_parts(Ap, Bp);
+        // D lap(p) - kappa div(J) at (x, y, z) with weights (1, 4, 1)^3
+        float lap;
         {
-            const float p0 = P0[pcy][pcx];
-            const int jy = ly + 1, jx = lx + 1;
-#pragma unroll
-            for (int c = -1; c <= 1; ++c) {
-                const float(*P)[PX] = s_p[(z + c) & (PR - 1)];
-                const float(*J0)[QX] = s_J[(z + c) & (JR - 1)][0];
-                const float(*J1)[QX] = s_J[(z + c) & (JR - 1)][1];
-#pragma unroll
-                for (int b = -1; b <= 1; ++b) {
-                    const float wbc = (b == 0 ? 4.f : 1.f) * (c == 0 ? 4.f : 1.f);
-#pragma unroll
-                    for (int a = -1; a <= 1; ++a) {
-                        if (a == 0 && b == 0 && c == 0) continue;
-                        lap = fmaf(wbc * (a == 0 ? 4.f : 1.f), P[pcy + b][pcx + a] - p0, lap);
-                    }
-                    dj = fmaf(wbc, J0[jy + b][jx + 1] - J0[jy + b][jx - 1], dj);
-                    dj = fmaf(wbc, J1[jy + 1][jx + b] - J1[jy - 1][jx + b], dj);
-                }
-            }
-            const float(*J2m)[QX] = s_J[(z - 1) & (JR - 1)][2];
-            const float(*J2p)[QX] = s_J[(z + 1) & (JR - 1)][2];
-#pragma unroll
-            for (int b = -1; b <= 1; ++b)
-#pragma unroll
-                for (int a = -1; a <= 1; ++a)
-                    dj = fmaf((b == 0 ? 4.f : 1.f) * (a == 0 ? 4.f : 1.f), J2p[jy + b][jx + a] - J2m[jy + b][jx + a],
-                              dj);
+            const float pz = P0[pcy][pcx];
+            const float pm = s_p[(z - 1) & (PR - 1)][pcy][pcx], pp = s_p[(z + 1) & (PR - 1)][pcy][pcx];
+            const float Sm = s_G[g5(z - 1)][2][gq], S0 = s_G[g5(z)][2][gq], Sp = s_G[g5(z + 1)][2][gq];
+            lap = fmaf(4.f, S0, fmaf(36.f, pm - pz, Sm) + fmaf(36.f, pp - pz, Sp));
         }
+        const float dj = fmaf(4.f, A0, Am + Ap) + (Bp - Bm);
+        Am = A0; Bm = B0; A0 = Ap; B0 = Bp;
         // the upper z face of this column
         const float fzp = z_flux(z, uzc, uzn);
         __syncthreads();  // the plane's x and y face fluxes are in place

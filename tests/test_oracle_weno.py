@@ -252,3 +252,22 @@ def test_fd_phase_does_not_depend_on_the_d3q7_relaxation(orc):
         res.append(o.moments()[2])
         o.close()
     assert np.array_equal(res[0], res[1])
+
+
+def test_phase_field_access_is_the_state(orc):
+    """The stored phi of the WENO-5 solver reads back as lb_init gave it, and a
+    phi written back is what the next step advances (a uniform phi stays put)."""
+    o = orc.Oracle(6, 5, 4, 0.8, 0.1, 3.0, 0.0)
+    o.set_phase_solver("weno5")
+    rng = np.random.default_rng(1)
+    phi = rng.uniform(0.0, 1.0, (4, 5, 6))
+    o.init(phi, np.zeros((3, 4, 5, 6)))
+    assert np.array_equal(o.phase_field(), phi)
+    o.set_phase_field(np.full((4, 5, 6), 0.25))
+    o.step(3)
+    assert np.abs(o.phase_field() - 0.25).max() < 1e-15
+    o.close()
+    d3q7 = orc.Oracle(4, 4, 4, 0.8, 0.1, 3.0, 0.0)
+    with pytest.raises(RuntimeError):
+        d3q7.phase_field()
+    d3q7.close()
