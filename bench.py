@@ -397,7 +397,7 @@ def run_ensemble(args):
                                    + (", density and viscosity contrasts rho_l, rho_g, tau_l, tau_g = "
                                       + ", ".join(f"{v:g}" for v in args.density) if args.density else ""),
                        "boxes": len(specs), "sites": sites, "storage": args.storage,
-                       "tile": [64 if batch.paired else 32, ty, zc], "paired": batch.paired,
+                       "tile": [batch.pair_width or 32, ty, zc], "paired": batch.paired,
                        "l2": "populations larger than L2, no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "batch_step_kernel (step time incl. "

@@ -414,12 +414,16 @@ int lb_batch_tune(lb_batch* batch, int steps);
  * Errors: LB_EINVAL unless every rho > 0 and tau > 1/2 (finite). */
 int lb_batch_set_density(lb_batch* batch, const double* rho_l, const double* rho_g, const double* tau_l,
                          const double* tau_g);
-/* Which tile body runs the batch step of the FP16/BF16 storages: 1 (the default
- * where it applies) the paired one of lb_set_pairing, 0 one site per thread.
- * Applies when every box has nx % 4 == 0 and no density contrasts are set.
- * Errors: LB_EINVAL for 1 where it does not apply. */
+/* Which tile body runs the batch step of the FP16/BF16 storages: the paired
+ * one of lb_set_pairing on tiles 64 (on = 64 or 1, the default where it
+ * applies) or 32 sites wide (on = 32, which idles fewer columns on boxes of 24
+ * or 48 sites), or one site per thread (on = 0).  The paired body applies when
+ * every box has nx % 4 == 0 and no density contrasts are set.  lb_batch_tune
+ * times all three.  Errors: LB_EINVAL for another value, or a paired body
+ * where it does not apply. */
 int lb_batch_set_pairing(lb_batch* batch, int on);
-int lb_batch_get_pairing(const lb_batch* batch, int* on);  /* 1 when the paired body runs */
+/* *on = the paired tile's width (64 or 32) when the paired body runs, else 0 */
+int lb_batch_get_pairing(const lb_batch* batch, int* on);
 long long lb_batch_sites(const lb_batch* batch);  /* sum of the boxes' sites */
 long long lb_batch_time(const lb_batch* batch);   /* steps taken */
 void lb_batch_destroy(lb_batch* batch);            /* NULL is ignored */

@@ -101,7 +101,8 @@ struct lb_batch {
     bool mc = false;                  // moment-only storage
     std::vector<double> tau, M, W, sigma;
     bool vd = false;                  // density and viscosity contrasts (lb_batch_set_density)
-    bool pair = false;                // paired tile body preferred (16-bit storages; see batch_use_pair)
+    int pair = 0;                     // paired tile body preferred, tiles this wide (64 or 32; 0: one
+                                      // site per thread; 16-bit storages, see batch_use_pair)
     long long total_sites = 0, max_N = 0;
     bool vec = true;                  // every box has nx % 4 == 0
 
@@ -137,7 +138,7 @@ namespace {
 bool batch_pair_applies(const lb_batch* B) {
     return (B->storage == LB_F16_SHIFTED || B->storage == LB_BF16_SHIFTED) && B->vec && !B->vd;
 }
-bool batch_use_pair(const lb_batch* B) { return B->pair && batch_pair_applies(B); }
+bool batch_use_pair(const lb_batch* B) { return B->pair != 0 && batch_pair_applies(B); }
 
 long long items_for(const lb_batch* B, int ty, int zc) {
     long long n = 0;
@@ -155,7 +156,7 @@ void drop_graph(lb_batch* B) {
 int build_work(lb_batch* B) {
     std::vector<int> item_box, item0(B->count), nitem(B->count);
     int item = 0;
-    const int tx = batch_use_pair(B) ? 64 : 32;
+    const int tx = batch_use_pair(B) ? B->pair : 32;
     for (int b = 0; b < B->count; ++b) {
         BoxDesc& d = B->boxes[b];
         d.tiles_x = (d.nx + tx - 1) / tx;
@@ -178,8 +179,8 @@ int build_work(lb_batch* B) {
     BCUDA(cudaMemcpy(B->d_nitem, nitem.data(), (size_t)B->count * sizeof(int), cudaMemcpyHostToDevice));
     B->nitems = item;
     int per_sm = 0;
-    if (batch_use_pair(B)) per_sm = B->storage == LB_F16_SHIFTED ? batch_pair_blocks_per_sm<__half>(B->ty)
-                                                                  : batch_pair_blocks_per_sm<__nv_bfloat16>(B->ty);
+    if (batch_use_pair(B)) per_sm = B->storage == LB_F16_SHIFTED ? batch_pair_blocks_per_sm<__half>(B->ty, B->pair)
+                                                                  : batch_pair_blocks_per_sm<__nv_bfloat16>(B->ty, B->pair);
     else if (B->vd) switch (B->storage) {
         case LB_F32_MOMENTS: per_sm = batch_vd_blocks_per_sm<float, true>(B->ty, B->vec); break;
         case LB_F32: per_sm = batch_vd_blocks_per_sm<float, false>(B->ty, B->vec); break;
@@ -266,8 +267,8 @@ int enqueue_batch_step(lb_batch* B, int par, cudaStream_t s, bool first = false)
     b.partials = B->partials;
     cudaError_t e;
     if (batch_use_pair(B)) {
-        e = B->storage == LB_F16_SHIFTED ? launch_batch_pair<__half>(par, B->ty, B->grid_blocks, b, s)
-                                         : launch_batch_pair<__nv_bfloat16>(par, B->ty, B->grid_blocks, b, s);
+        e = B->storage == LB_F16_SHIFTED ? launch_batch_pair<__half>(par, B->ty, B->pair, B->grid_blocks, b, s)
+                                         : launch_batch_pair<__nv_bfloat16>(par, B->ty, B->pair, B->grid_blocks, b, s);
     } else if (B->vd) {
         switch (B->storage) {
             case LB_F32_MOMENTS: e = launch_batch_vd<float, true>(first ? 0 : 1, B->ty, B->vec, B->grid_blocks, b, s); break;
@@ -393,7 +394,7 @@ int lb_batch_create(int count, const int* dims, const double* tau, const double*
         if (nx % 4) B->vec = false;
     }
     B->initialized.assign(count, 0);
-    B->pair = batch_pair_applies(B);  // the paired body by default where it applies
+    B->pair = batch_pair_applies(B) ? 64 : 0;  // the paired body by default where it applies
     // partial records: the work list of the smallest tile, or one box's lb_init grid
     long long cap = items_for(B, 4, 1);
     for (const BoxDesc& d : B->boxes) {
@@ -576,17 +577,17 @@ int lb_batch_tune(lb_batch* B, int steps) {
     // up), the first shape in this order within 1% of the fastest.
     constexpr int WINDOWS = 5;
     constexpr float TIE = 0.01f;
-    // with a 16-bit storage the paired body's shapes come first
+    // with a 16-bit storage the paired body's shapes come first (64 sites wide, then 32)
     const bool try_pair = batch_pair_applies(B);
-    const int kinds[4][2] = {{1, 8}, {1, 4}, {0, 8}, {0, 4}};  // (paired, tile height)
+    const int kinds[6][2] = {{64, 8}, {64, 4}, {32, 8}, {32, 4}, {0, 8}, {0, 4}};  // (paired width, tile height)
     const int zcs[4] = {16, 32, 64, 128};
-    float med[16];
-    int cty[16], czc[16], cpr[16], ncand = 0;
+    float med[24];
+    int cty[24], czc[24], cpr[24], ncand = 0;
     int rc = LB_OK;
-    for (int a = 0; a < 4 && rc == LB_OK; ++a)
+    for (int a = 0; a < 6 && rc == LB_OK; ++a)
         for (int b = 0; b < 4 && rc == LB_OK; ++b) {
             if (kinds[a][0] && !try_pair) continue;
-            B->pair = kinds[a][0] != 0;
+            B->pair = kinds[a][0];
             if (lb_batch_set_tile(B, kinds[a][1], zcs[b]) != LB_OK) continue;
             float win[WINDOWS + 1];
             int nwin = 0;
@@ -619,7 +620,7 @@ int lb_batch_tune(lb_batch* B, int steps) {
             cpr[ncand] = kinds[a][0];
             ++ncand;
         }
-    int bty = B->ty, bzc = B->zc, bpr = B->pair ? 1 : 0;
+    int bty = B->ty, bzc = B->zc, bpr = B->pair;
     if (ncand > 0) {
         float best = med[0];
         for (int k = 1; k < ncand; ++k) best = med[k] < best ? med[k] : best;
@@ -631,7 +632,7 @@ int lb_batch_tune(lb_batch* B, int steps) {
                 break;
             }
     }
-    B->pair = bpr != 0;
+    B->pair = bpr;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     B->launches = 0;
@@ -640,16 +641,18 @@ int lb_batch_tune(lb_batch* B, int steps) {
 
 int lb_batch_set_pairing(lb_batch* B, int on) {
     if (!B) return bfail(LB_EINVAL, "batch is NULL");
+    if (on != 0 && on != 1 && on != 32 && on != 64)
+        return bfail(LB_EINVAL, "lb_batch_set_pairing: %d is none of 0, 1, 32, 64", on);
     if (on && !batch_pair_applies(B))
         return bfail(LB_EINVAL, "the paired tile body needs FP16 or BF16 storage, nx %% 4 == 0 in every box and no "
                                 "density contrasts");
-    B->pair = on != 0;
+    B->pair = on == 1 ? 64 : on;
     return build_work(B);
 }
 
 int lb_batch_get_pairing(const lb_batch* B, int* on) {
     if (!B || !on) return bfail(LB_EINVAL, "NULL argument");
-    *on = batch_use_pair(B) ? 1 : 0;
+    *on = batch_use_pair(B) ? B->pair : 0;
     return LB_OK;
 }
 

@@ -650,6 +650,7 @@ template <class FT, int TY, int MODE, int PAR, bool VEC, bool MC = false, bool V
           bool PAIR = false, bool G16 = false>
 __global__ void __launch_bounds__(32 * TY, PAIR ? (TY == 4 ? 3 : 2) : (TY >= 16 ? 1 : 512 / (32 * TY)))
 fused_step_kernel(const StepArgs a) {
+    constexpr int PTX = 64;
 #define TILE_BX blockIdx.x
 #define TILE_BY blockIdx.y
 #define TILE_BZ blockIdx.z
@@ -720,9 +721,14 @@ struct BoxTileArgs {
 // MC_ (moment-only storage, FT float) PAR = 0 evaluates each site's own
 // coefficients (the step from t = 0) and PAR = 1 pulls.  VD_: every box with
 // its own density and viscosity contrasts (Sec. 2.3).  PAIR_: the paired
-// tile body of the 16-bit storages (tiles 64 sites wide, two sites per thread).
-template <class FT, int TY, int PAR, bool VEC, bool MC_ = false, bool VD_ = false, bool PAIR_ = false>
-__global__ void __launch_bounds__(32 * TY, PAIR_ ? (TY == 4 ? 3 : 2) : (TY >= 16 ? 1 : 512 / (32 * TY)))
+// tile body of the 16-bit storages (tiles PW_ = 64 or 32 sites wide, two sites
+// per thread, PW_/2 * TY threads).
+template <int PW, int TY>
+constexpr int pair_threads() { return PW / 2 * TY; }
+template <class FT, int TY, int PAR, bool VEC, bool MC_ = false, bool VD_ = false, bool PAIR_ = false, int PW_ = 64>
+__global__ void __launch_bounds__(PAIR_ ? pair_threads<PW_, TY>() : 32 * TY,
+                                  PAIR_ ? (pair_threads<PW_, TY>() == 64 ? 6 : pair_threads<PW_, TY>() == 128 ? 3 : 2)
+                                        : (TY >= 16 ? 1 : 512 / (32 * TY)))
 batch_step_kernel(const __grid_constant__ BatchArgs b) {
     for (int item = blockIdx.x; item < b.nitems; item += gridDim.x) {
         const BoxDesc d = b.boxes[b.item_box[item]];
@@ -754,6 +760,7 @@ batch_step_kernel(const __grid_constant__ BatchArgs b) {
             constexpr bool PF = false;
             constexpr bool PAIR = PAIR_;
             constexpr bool G16 = false;
+            constexpr int PTX = PW_;
 #define TILE_BX tbx
 #define TILE_BY tby
 #define TILE_BZ tbz
@@ -815,11 +822,12 @@ template <class FT>
 cudaError_t launch_fused_pair_g16(int parity, int ty, dim3 grid, const StepArgs& a, cudaStream_t st);
 template <class FT>
 int fused_pair_g16_blocks_per_sm(int ty);
-// The batch kernel with the paired tile body (16-bit storages; every box nx % 4 == 0).
+// The batch kernel with the paired tile body (16-bit storages; every box nx % 4 == 0),
+// tiles pw = 64 or 32 sites wide and ty = 4 or 8 rows (pw/2 * ty threads).
 template <class FT>
-cudaError_t launch_batch_pair(int parity, int ty, int blocks, const BatchArgs& b, cudaStream_t st);
+cudaError_t launch_batch_pair(int parity, int ty, int pw, int blocks, const BatchArgs& b, cudaStream_t st);
 template <class FT>
-int batch_pair_blocks_per_sm(int ty);
+int batch_pair_blocks_per_sm(int ty, int pw);
 
 // The batch kernel with density and viscosity contrasts (every box its own),
 // for the AA storage FT (MC = false) or the moment-only storage (FT float,

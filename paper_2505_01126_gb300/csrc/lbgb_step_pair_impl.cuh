@@ -40,37 +40,39 @@ int fused_pair_blocks_per_sm<LBGB_FT>(int ty) {
     return n;
 }
 
-template <class FT, int TY>
+template <class FT, int TY, int PW>
 static void launch_batch_pair_ty(int parity, int blocks, const BatchArgs& b, cudaStream_t st) {
-    if (parity == 0) batch_step_kernel<FT, TY, 0, true, false, false, true><<<blocks, 32 * TY, 0, st>>>(b);
-    else batch_step_kernel<FT, TY, 1, true, false, false, true><<<blocks, 32 * TY, 0, st>>>(b);
+    constexpr int threads = PW / 2 * TY;
+    if (parity == 0) batch_step_kernel<FT, TY, 0, true, false, false, true, PW><<<blocks, threads, 0, st>>>(b);
+    else batch_step_kernel<FT, TY, 1, true, false, false, true, PW><<<blocks, threads, 0, st>>>(b);
 }
 
 template <>
-cudaError_t launch_batch_pair<LBGB_FT>(int parity, int ty, int blocks, const BatchArgs& b, cudaStream_t st) {
-    switch (ty) {
-        case 4: launch_batch_pair_ty<LBGB_FT, 4>(parity, blocks, b, st); break;
-        case 8: launch_batch_pair_ty<LBGB_FT, 8>(parity, blocks, b, st); break;
-        default: return cudaErrorInvalidValue;
-    }
+cudaError_t launch_batch_pair<LBGB_FT>(int parity, int ty, int pw, int blocks, const BatchArgs& b, cudaStream_t st) {
+    if (pw == 64 && ty == 4) launch_batch_pair_ty<LBGB_FT, 4, 64>(parity, blocks, b, st);
+    else if (pw == 64 && ty == 8) launch_batch_pair_ty<LBGB_FT, 8, 64>(parity, blocks, b, st);
+    else if (pw == 32 && ty == 4) launch_batch_pair_ty<LBGB_FT, 4, 32>(parity, blocks, b, st);
+    else if (pw == 32 && ty == 8) launch_batch_pair_ty<LBGB_FT, 8, 32>(parity, blocks, b, st);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
-template <>
-int batch_pair_blocks_per_sm<LBGB_FT>(int ty) {
+template <class FT, int TY, int PW>
+static int batch_pair_occupancy() {
     int n = 0;
-    cudaError_t e = cudaErrorInvalidValue;
-    if (ty == 4)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LBGB_FT, 4, 1, true, false, false, true>,
-                                                          128, 0);
-    else if (ty == 8)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<LBGB_FT, 8, 1, true, false, false, true>,
-                                                          256, 0);
-    if (e != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<FT, TY, 1, true, false, false, true, PW>,
+                                                      PW / 2 * TY, 0) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return n;
+}
+
+template <>
+int batch_pair_blocks_per_sm<LBGB_FT>(int ty, int pw) {
+    if (pw == 64) return ty == 4 ? batch_pair_occupancy<LBGB_FT, 4, 64>() : ty == 8 ? batch_pair_occupancy<LBGB_FT, 8, 64>() : 0;
+    if (pw == 32) return ty == 4 ? batch_pair_occupancy<LBGB_FT, 4, 32>() : ty == 8 ? batch_pair_occupancy<LBGB_FT, 8, 32>() : 0;
+    return 0;
 }
 
 }  // namespace lbgb

@@ -405,15 +405,21 @@ class Batch:
 
         _check(_lib.lb_batch_set_density(self._h, arr(rho_l), arr(rho_g), arr(tau_l), arr(tau_g)))
 
-    def set_pairing(self, on: bool):
-        """The paired tile body for FP16/BF16 storage (lb_batch_set_pairing)."""
-        _check(_lib.lb_batch_set_pairing(self._h, 1 if on else 0))
+    def set_pairing(self, on):
+        """The paired tile body for FP16/BF16 storage (lb_batch_set_pairing):
+        False/0, True (64 sites wide), or the tile width 64 or 32."""
+        _check(_lib.lb_batch_set_pairing(self._h, int(on)))
+
+    @property
+    def pair_width(self) -> int:
+        """Width of the paired tiles, 0 when one site per thread runs."""
+        v = ctypes.c_int()
+        _check(_lib.lb_batch_get_pairing(self._h, ctypes.byref(v)))
+        return v.value
 
     @property
     def paired(self) -> bool:
-        v = ctypes.c_int()
-        _check(_lib.lb_batch_get_pairing(self._h, ctypes.byref(v)))
-        return bool(v.value)
+        return self.pair_width != 0
 
     def init(self, box, phi, u):
         p, _a = _ptr(phi, self._N(box))

@@ -60,6 +60,8 @@ def test_batch_boxes_equal_single_boxes(lbgb, dims, storage):
     if storage == "f16" and not paired:
         with pytest.raises(lbgb.LBError):
             batch.set_pairing(True)
+    with pytest.raises(lbgb.LBError):
+        batch.set_pairing(16)  # widths are 64 and 32
     batch.set_tile(4, 16)
     for k, (phi, u) in enumerate(fields):
         batch.init(k, phi, u)
@@ -149,11 +151,11 @@ def test_batch_with_density_contrasts_matches_the_oracle(lbgb, orc, storage):
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 def test_batch_paired_matches_the_oracle(lbgb, orc, storage):
     """16-bit storages run the paired tile body (two sites per thread, tiles 64
-    sites wide) in the persistent batch kernel: five boxes with nx % 4 == 0, one
-    a single x tile of 8, one ragged at 36 and one two tiles wide at 100, 50 steps,
-    each against its own FP64 oracle within the 16-bit storage's bound (2e-4 FP16,
-    5e-3 BF16, as the single-box kernels), and within that bound of the one-site
-    body's fields."""
+    or 32 sites wide) in the persistent batch kernel: five boxes with nx % 4 == 0,
+    one a single x tile of 8, one ragged at 36 and one two tiles wide at 100, 50
+    steps, each against its own FP64 oracle within the 16-bit storage's bound
+    (2e-4 FP16, 5e-3 BF16, as the single-box kernels), and within that bound of
+    the one-site body's fields."""
     from test_gpu_pair import BOUND
     from test_gpu_parity import max_err
 
@@ -162,11 +164,11 @@ def test_batch_paired_matches_the_oracle(lbgb, orc, storage):
     sigma = [0.01, 0.005, 0.02, 0.015, 0.01]
     fields = [box_fields(*d, seed=60 + k) for k, d in enumerate(dims)]
     got = {}
-    for pair in (True, False):
+    for pair in (64, 32, 0):
         batch = lbgb.Batch(dims, tau, 0.1, 3.0, sigma, storage=storage)
         batch.set_pairing(pair)
-        batch.set_tile(4 if pair else 8, 16)
-        assert batch.paired == pair
+        batch.set_tile(4 if pair == 64 else 8, 16)
+        assert batch.pair_width == pair
         for k, (phi, u) in enumerate(fields):
             batch.init(k, phi, u)
         batch.step(49)
@@ -177,10 +179,13 @@ def test_batch_paired_matches_the_oracle(lbgb, orc, storage):
         o = orc.Oracle(*d, tau[k], 0.1, 3.0, sigma[k])
         o.init(phi.astype(np.float64), u.astype(np.float64))
         o.step(50)
-        ep, es = max_err(got[True][k], o.moments()), max_err(got[False][k], o.moments())
-        assert max(ep) <= BOUND[storage], (k, d, ep, es)
-        dd = max_err(got[True][k], [x.astype(np.float64) for x in got[False][k]])
-        assert max(dd) <= BOUND[storage], (k, d, dd)
+        want = o.moments()
+        es = max_err(got[0][k], want)
+        for pw in (64, 32):
+            ep = max_err(got[pw][k], want)
+            assert max(ep) <= BOUND[storage], (pw, k, d, ep, es)
+            dd = max_err(got[pw][k], [x.astype(np.float64) for x in got[0][k]])
+            assert max(dd) <= BOUND[storage], (pw, k, d, dd)
         o.close()
 
 
