@@ -352,7 +352,13 @@ def run_ensemble(args):
                        [sp["sigma"] for sp in specs], storage=args.storage, stream=stream)
     if args.density:  # every box with the same contrasts: droplets of the phase at phi = 1
         batch.set_density(*args.density)
-    ty, zc = batch.tune(3)
+    if args.pair_width is not None:
+        batch.set_pairing(args.pair_width)
+    if args.tile:
+        batch.set_tile(*args.tile)
+        ty, zc = batch.tile()
+    else:
+        ty, zc = batch.tune(3)
     fields = {}
     for k, sp in enumerate(specs):
         e = sp["edge"]
@@ -523,12 +529,15 @@ def run_box(args, lbgb, torch, w, storage: str, force, rank: int, world: int, pg
             phim = 1.0 - phim  # the flipped field of the gas-bubble case
         rho_ref = args.density[1] + (args.density[0] - args.density[1]) * phim
         box.set_gravity(args.gravity, rho_ref)
+    sixteen = storage in ("f16", "bf16", "f16g", "bf16g")
     if args.tile:
+        if args.no_pair and sixteen:
+            box.set_pairing(False)
         box.set_tile(*args.tile)
     elif not args.no_tune:
-        box.tune(8)
+        box.tune(8)  # times the paired and the one-site kernel
     ty, zc = box.tile()
-    paired = box.paired if storage in ("f16", "bf16") else False
+    paired = box.paired if sixteen else False
     phi_d = w.phi if torch.is_tensor(w.phi) else torch.from_numpy(w.phi).cuda()
     if args.density and not droplet:
         phi_d = 1.0 - phi_d  # gas bubbles: phi = 0 inside
@@ -627,9 +636,15 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "moments", "f16g", "bf16g"],
                     help="population storage: FP32/FP16/BF16 AA populations, the moment-only coefficients, or "
                          "FP16/BF16 AA populations with 16-bit D3Q7 populations (f16g, bf16g)")
-    ap.add_argument("--compare", default="f16", choices=["f16", "bf16", "f16g", "bf16g", "none"],
-                    help="16-bit storage run in the same invocation next to FP32 storage (bubbly HIT only), "
-                         "with its errors against the oracle")
+    ap.add_argument("--compare", default="f16,f16g",
+                    help="16-bit storages (comma list of f16, bf16, f16g, bf16g, or none) run in the same invocation "
+                         "next to FP32 storage (bubbly HIT only), each with its errors against the oracle; the first "
+                         "is the line's storage16 object, the others follow under compare")
+    ap.add_argument("--no-pair", action="store_true",
+                    help="one site per thread for the 16-bit storages (the paired kernel is the default)")
+    ap.add_argument("--pair-width", type=int, choices=[0, 32, 64], default=None,
+                    help="ensemble: paired tile width of the 16-bit storages (0: one site per thread); with --tile "
+                         "it skips the tuner")
     ap.add_argument("--edge", type=int, default=None, help="box edge of the droplet and ABC workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
@@ -708,8 +723,14 @@ def main():
     alu = lbgb.measure_fp32_peak() if rank == 0 else None  # the compute-side roofline's denominator
     main_run = run_box(args, lbgb, torch, w, args.storage, force, rank, world, pg, barrier, alu)
     compare = None
-    if hit and args.storage == "f32" and args.compare != "none" and not args.density and args.phase == "lb":
-        compare = run_box(args, lbgb, torch, w, args.compare, force, rank, world, pg, barrier, alu)
+    compare_list = [] if args.compare == "none" else args.compare.split(",")
+    for st in compare_list:
+        if st not in ("f16", "bf16", "f16g", "bf16g"):
+            raise SystemExit(f"--compare: unknown storage {st}")
+    compares = []
+    if hit and args.storage == "f32" and compare_list and not args.density and args.phase == "lb":
+        compares = [run_box(args, lbgb, torch, w, st, force, rank, world, pg, barrier, alu) for st in compare_list]
+        compare = compares[0]
 
     if rank == 0:
         cpu, errors = None, None
@@ -725,7 +746,7 @@ def main():
                                      f"bubble R={PRESETS[args.preset][2]:g}, linear forcing) for {SURR_STEPS} FP64 "
                                      f"oracle steps, and the {LAP_EDGE}^3 static droplet R={LAP_R:g} for "
                                      f"{LAP_SAMPLES[-1]} steps; {ref['time_s']:.1f} s of stepping"}
-                    errors = {st: storage_errors(lbgb, st, args.preset, ref) for st in ("f32", args.compare)}
+                    errors = {st: storage_errors(lbgb, st, args.preset, ref) for st in ["f32"] + compare_list}
                     errors["how"] = (f"each storage on the GPU against the FP64 oracle: K = 1/2 sum |u|^2 every "
                                      f"{SURR_EVERY} steps for {SURR_STEPS} steps of the {SURR_EDGE}^3 surrogate "
                                      f"(largest relative error), phase mass sum(phi) drift and max|delta| of p*, u, "
@@ -750,8 +771,11 @@ def main():
                           f"solenoidal start from modes 1 <= |k| <= 4 with u_rms=0.02, linear forcing holding K"
                           + (", gas bubbles (phi = 0) with rho_l, rho_g, tau_l, tau_g = "
                              + ", ".join(f"{v:g}" for v in args.density) if args.density else "")
-                          + (f"; run with FP32 population storage (value) and {args.compare.upper()} shifted "
-                             f"storage (storage16), FP32 arithmetic, FP64 reductions" if compare else "")))
+                          + (f"; run with FP32 population storage (value) and {compare_list[0].upper()} shifted "
+                             f"storage (storage16)"
+                             + "".join(f", {st.upper()}" for st in compare_list[1:])
+                             + (" (compare)" if compare_list[1:] else "")
+                             + ", FP32 arithmetic, FP64 reductions" if compare else "")))
         workload_name += ((f", buoyancy g = ({', '.join(f'{v:g}' for v in args.gravity)}), "
                            f"rho_ref = {rho_ref:.6g} (mean density)" if args.gravity else "")
                           + (", phase field by WENO-5 finite differences (SSP-RK3)" if args.phase != "lb" else ""))
@@ -767,8 +791,15 @@ def main():
             line["storage16"] = {k: compare[k] for k in ("storage", "value", "ms_per_step", "tile", "paired", "roofline",
                                                          "e2e", "clocks", "gpu_launches", "diagnostics")}
             line["storage16"]["speedup_vs_f32"] = compare["value"] / main_run["value"]
-            line["storage16"]["errors"] = errors[args.compare] if errors else None
+            line["storage16"]["errors"] = errors[compare_list[0]] if errors else None
             line["gpu_launches"] += compare["gpu_launches"]
+            for st, c in zip(compare_list[1:], compares[1:]):
+                o = {k: c[k] for k in ("storage", "value", "ms_per_step", "tile", "paired", "roofline", "e2e",
+                                       "clocks", "gpu_launches", "diagnostics")}
+                o["speedup_vs_f32"] = c["value"] / main_run["value"]
+                o["errors"] = errors[st] if errors else None
+                line.setdefault("compare", {})[st] = o
+                line["gpu_launches"] += c["gpu_launches"]
             line["errors"] = errors
         if droplet:
             line["paper_context"] = {"value": 105480.0 / 64, "unit": "MLUPS per GPU",
