@@ -62,9 +62,9 @@ REF_EDGE = 64
 # (Laplace pressure jump averaged over steps 220-400)
 SURR_EDGE, SURR_STEPS, SURR_EVERY = 64, 500, 50
 LAP_EDGE, LAP_R, LAP_SAMPLES = 32, 8.0, list(range(220, 401, 20))
-# bytes per site of the survey's roofline table, which also counts writing and
-# re-reading a stored phi field (8 B/site)
-SURVEY_BYTES = {"f32": 280.0, "f16": 172.0, "bf16": 172.0, "f16g": 144.0, "bf16g": 144.0}
+# bytes per site and step when a stored FP32 phi field is also written and
+# re-read (8 B/site); the f16g/bf16g kernels keep a 16-bit phi~ (4 B/site) of their own
+PHI_STORED_BYTES = {"f32": 280.0, "f16": 172.0, "bf16": 172.0, "f16g": 144.0, "bf16g": 144.0}
 
 
 # Presets of the bubbly forced HIT workload: edge, bubbles, radius, tau, seed.
@@ -607,11 +607,11 @@ def run_box(args, lbgb, torch, w, storage: str, force, rank: int, world: int, pg
         roof["issue"] = {"warp_inst_per_site": ips, "achieved": ach, "peak": alu["warp_inst_per_s"],
                          "unit": "warp-instructions/s", "frac": ach / alu["warp_inst_per_s"],
                          "peak_source": "measured (lb_measure_fp32_peak)"}
-    if args.phase == "lb" and not args.density and storage in SURVEY_BYTES:
-        # the same kernel time against the survey's count, which adds 8 B/site for
-        # writing and re-reading a stored phi (this kernel keeps phi on chip)
-        roof["bytes_per_site_with_phi"] = SURVEY_BYTES[storage]
-        roof["frac_with_phi"] = SURVEY_BYTES[storage] * N / kern_avg_s / 1e9 / peak
+    if args.phase == "lb" and not args.density and storage in PHI_STORED_BYTES:
+        # the same kernel time against the count with a stored FP32 phi (written
+        # and re-read; this kernel rebuilds phi on chip)
+        roof["bytes_per_site_with_phi"] = PHI_STORED_BYTES[storage]
+        roof["frac_with_phi"] = PHI_STORED_BYTES[storage] * N / kern_avg_s / 1e9 / peak
     if args.phase != "lb":
         # the three finite-difference stage kernels and the reduction, per step
         roof["other_kernels_ms_per_step"] = t_max / args.steps - kern_avg_s * 1e3

@@ -186,14 +186,15 @@ def test_tile_shapes_give_identical_fields(lbgb, tile, nx):
         assert np.array_equal(x, y)
 
 
-def test_graph_replay_equals_single_steps(lbgb):
+@pytest.mark.parametrize("storage", ["f32", "f16", "f16g"])
+def test_graph_replay_equals_single_steps(lbgb, storage):
     shape = (16, 16, 40)
     phi, u = smooth_fields(shape, 5)
     nz, ny, nx = shape
-    a = lbgb.Box(nx, ny, nz, 0.8, 0.1, 3.0, 0.01, force=lbgb.Force(kind=3, T_relax=30.0))
+    a = lbgb.Box(nx, ny, nz, 0.8, 0.1, 3.0, 0.01, force=lbgb.Force(kind=3, T_relax=30.0), storage=storage)
     a.init(phi, u)
     a.step(9)  # graph for pairs + one single step
-    b = lbgb.Box(nx, ny, nz, 0.8, 0.1, 3.0, 0.01, force=lbgb.Force(kind=3, T_relax=30.0))
+    b = lbgb.Box(nx, ny, nz, 0.8, 0.1, 3.0, 0.01, force=lbgb.Force(kind=3, T_relax=30.0), storage=storage)
     b.init(phi, u)
     for _ in range(9):
         b.step(1)
