@@ -277,7 +277,8 @@ int lb_load(lb_ctx* ctx, const void* buf, size_t bytes);
 
 /* Algorithmic bytes moved per site per step by the fused kernel (population
  * reads and writes): 27*2*sizeof(f) + 7*2*sizeof(g), or 10*2*4 + 7*2*4 for
- * LB_F32_MOMENTS; with LB_PHASE_WENO5 the 7*2*4 of g become 4 + 3*4 (phi read,
+ * LB_F32_MOMENTS, or 27*2*2 + 8*2*2 = 140 for the 16-bit D3Q7 storages (gamma
+ * and phi~); with LB_PHASE_WENO5 the 7*2*4 of g become 4 + 3*4 (phi read,
  * u written; the three stage kernels move 3*(4 + 3*4 + 4) + 2*4 = 68 more). */
 double lb_bytes_per_site(const lb_ctx* ctx);
 
