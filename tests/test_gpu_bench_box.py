@@ -1,5 +1,7 @@
 """The benchmark's own box: 512^3 bubble-laden forced HIT (256 bubbles R = 12,
-seed 3, tau 0.51), FP32 storage, in the launch shape the tuner picks for it.
+seed 3, tau 0.51), in each storage the benchmark line runs (FP32; FP16 and
+FP16 f and g in their paired kernels) and the launch shape the tuner picks for
+it.
 
 The oracle cannot run this box for many steps, so parity is checked on
 sampled outputs the oracle can compute one by one.  Without the linear
@@ -10,7 +12,9 @@ streaming hop of the populations of sites whose curvature reads phi at
 radius 2), and the moments at t = 2 read phi at radius 2 for the curvature in
 the forced velocity.  A periodic 24^3 window of the inputs centred on a site
 keeps its seam 12 sites away, so the oracle on that window gives the site's
-exact fields.  Two steps cover both AA parities.  Over 50 steps with the
+exact fields.  Two steps cover both AA parities.  FP32 meets 1e-5 there; the
+16-bit storages meet their 50-step bounds (2e-4 FP16 f, 5e-4 FP16 f and g).
+Over 50 steps with the
 forcing on, the box is checked by properties: finite fields and reductions,
 the phase mass conserved to FP32 rounding, and the controller holding the
 kinetic energy.
@@ -54,9 +58,12 @@ def workload():
     return w, phi, u
 
 
-def tuned_box(lbgb, w, n, force):
+BOUND = {"f32": TOL, "f16": 2e-4, "f16g": 5e-4}
+
+
+def tuned_box(lbgb, w, n, force, storage="f32"):
     os.environ.setdefault("LBGB_TUNE_CACHE", os.path.join(bench.ROOT, "paper_2505_01126_gb300", "tune_cache.txt"))
-    b = lbgb.Box(n, n, n, w.tau, w.M, w.W, w.sigma, force=force, storage="f32")
+    b = lbgb.Box(n, n, n, w.tau, w.M, w.W, w.sigma, force=force, storage=storage)
     b.tune(8)
     return b
 
@@ -66,7 +73,7 @@ def sample_sites(n, zc, count, seed):
     rng = np.random.default_rng(seed)
     pts = [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(count)]
     for z in (0, zc - 1, zc, n - 1):
-        for x, y in ((0, 0), (31, 7), (32, 8), (n - 1, n - 1), (n // 2, 3)):
+        for x, y in ((0, 0), (31, 7), (32, 8), (63, 3), (64, 4), (n - 1, n - 1), (n // 2, 3)):
             pts.append((x % n, y % n, z % n))
     return pts
 
@@ -78,11 +85,13 @@ def window(a, x, y, z, n):
     return a[..., iz[:, None, None], iy[None, :, None], ix[None, None, :]]
 
 
-def test_bench_box_two_steps_against_windowed_oracle(lbgb, orc, workload):
+@pytest.mark.parametrize("storage", ["f32", "f16", "f16g"])
+def test_bench_box_two_steps_against_windowed_oracle(lbgb, orc, workload, storage):
     w, phi, u = workload
     n = phi.shape[0]
-    b = tuned_box(lbgb, w, n, None)
+    b = tuned_box(lbgb, w, n, None, storage)
     ty, zc = b.tile()
+    paired = b.paired if storage != "f32" else False
     b.init(phi, u)
     b.step(2)
     got = b.moments_numpy()
@@ -98,7 +107,7 @@ def test_bench_box_two_steps_against_windowed_oracle(lbgb, orc, workload):
         diffs = [abs(float(got[0][z, y, x]) - rho_o[c, c, c]), abs(float(got[2][z, y, x]) - phi_o[c, c, c])]
         diffs += [abs(float(got[1][a, z, y, x]) - u_o[a, c, c, c]) for a in range(3)]
         worst = max(worst, max(diffs))
-        assert max(diffs) <= TOL, ((x, y, z), diffs, (ty, zc))
+        assert max(diffs) <= BOUND[storage], ((x, y, z), diffs, (ty, zc, paired))
     assert worst > 0.0  # the check compares something
 
 

@@ -298,25 +298,36 @@ def test_full_size_256_fifty_steps(lbgb, orc):
     """The 256^3 workload (forced HIT, 64 bubbles R = 10, tau = 0.51) in its tuned
     launch shape: 50 steps (both AA parities, the linear-forcing controller
     running), every site compared with the oracle (about 90 s of oracle time on
-    16 cores, 13 GB of host memory)."""
+    16 cores, 13 GB of host memory).  The 16-bit storages run the same box in
+    their tuned (paired) kernels against the same oracle run, within their
+    bounds: 2e-4 for FP16 f, 5e-4 for FP16 f and g (tests/test_gpu_pair.py,
+    tests/test_gpu_g16.py)."""
     w = inputs.bubbly_hit(256, 64, 10.0, seed=2)
     n = 256
-    b = lbgb.Box(n, n, n, w.tau, w.M, w.W, w.sigma, force=lbgb.Force(kind=3, T_relax=w.T_relax))
-    b.tune(2)
-    b.init(w.phi, w.u)
-    b.step(50)
-    got = b.moments_numpy()
-    dg = b.diagnostics()
-    b.close()
+    runs = {}
+    for storage in ("f32", "f16", "f16g"):
+        b = lbgb.Box(n, n, n, w.tau, w.M, w.W, w.sigma, force=lbgb.Force(kind=3, T_relax=w.T_relax),
+                     storage=storage)
+        b.tune(2)
+        b.init(w.phi, w.u)
+        b.step(50)
+        runs[storage] = (b.moments_numpy(), b.diagnostics())
+        b.close()
     o = orc.Oracle(n, n, n, w.tau, w.M, w.W, w.sigma, force_kind=3, T_relax=w.T_relax)
     o.init(w.phi.astype(np.float64), w.u.astype(np.float64))
     o.step(50)
     want = o.moments()
     do = o.diagnostics()
     o.close()
+    got, dg = runs["f32"]
     e = max_err(got, want)
     assert max(e) <= TOL, e
     check_diagnostics(dg, do, n ** 3, field_err=max(e), tau=w.tau, T_relax=w.T_relax)
+    for storage, bound in (("f16", 2e-4), ("f16g", 5e-4)):
+        got, dg = runs[storage]
+        e = max_err(got, want)
+        assert max(e) <= bound, (storage, e)
+        assert abs(dg[0] / do[0] - 1) < 1e-5, (storage, dg[0], do[0])  # phase mass
 
 
 def test_single_phase_abc_hit(lbgb, orc):
