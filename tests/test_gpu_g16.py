@@ -26,7 +26,7 @@ pytestmark = pytest.mark.gpu
 
 BOUND = {"f16g": 5e-4, "bf16g": 5e-3}
 SHAPES = [((6, 5, 4), (8, 3)), ((9, 13, 8), (4, 4)), ((11, 17, 36), (8, 5)), ((7, 9, 100), (8, 32)),
-          ((40, 12, 64), (4, 16))]
+          ((40, 12, 64), (4, 16)), ((1, 3, 4), (4, 1)), ((2, 1, 8), (8, 2))]  # the last two: nz = 1, ny = 1
 
 
 @pytest.fixture(scope="module")
@@ -76,8 +76,10 @@ def run(lbgb, shape, storage, steps, phi, u, pair, tile=None, force=None, tau=0.
 @pytest.mark.parametrize("shape,tile", SHAPES)
 def test_g16_against_oracle_paired_and_one_site(lbgb, orc, storage, shape, tile):
     """Both AA parities, x wrap-around on both sites of a pair (nx = 4, 8), ragged
-    last tiles in x (36, 100) and y, both tile heights: 50 steps in the paired and
-    the one-site kernel, each against the oracle and against each other."""
+    last tiles in x (36, 100) and y, both tile heights, boxes one plane or one row
+    thick (every z or y neighbour, and so every shift, is the site's own plane or
+    row): 50 steps in the paired and the one-site kernel, each against the oracle
+    and against each other."""
     phi, u = smooth_fields(shape, sum(shape) + 1)
     want, dw = oracle_fields(orc, shape, phi, u)
     (gp, dp) = run(lbgb, shape, storage, 50, phi, u, True, tile)
