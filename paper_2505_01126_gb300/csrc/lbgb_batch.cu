@@ -16,6 +16,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "lbgb.h"
@@ -113,6 +114,7 @@ struct lb_batch {
     BoxDesc* d_boxes = nullptr;
     int* d_item_box = nullptr;
     int* d_item0 = nullptr;
+    int* d_next = nullptr;            // the work queue's next item (zeroed before each step)
     int* d_nitem = nullptr;
     double* d_epsw = nullptr;         // eps per unit of the summed a2:a2 partials, per box
     DevState* d_st = nullptr;
@@ -157,7 +159,15 @@ int build_work(lb_batch* B) {
     std::vector<int> item_box, item0(B->count), nitem(B->count);
     int item = 0;
     const int tx = batch_use_pair(B) ? B->pair : 32;
-    for (int b = 0; b < B->count; ++b) {
+    // Blocks take items from a queue in list order, so the list holds the
+    // largest boxes first: their full-height chunks start early and the small
+    // boxes' short items fill the end of the step.
+    std::vector<int> order(B->count);
+    for (int b = 0; b < B->count; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return (long long)B->boxes[a].N > (long long)B->boxes[c].N;
+    });
+    for (int b : order) {
         BoxDesc& d = B->boxes[b];
         d.tiles_x = (d.nx + tx - 1) / tx;
         d.tiles_y = (d.ny + B->ty - 1) / B->ty;
@@ -265,6 +275,8 @@ int enqueue_batch_step(lb_batch* B, int par, cudaStream_t s, bool first = false)
         b.c_out = C + buf * (size_t)(par ^ 1);
     }
     b.partials = B->partials;
+    b.next = B->d_next;
+    BCUDA(cudaMemsetAsync(B->d_next, 0, sizeof(int), s));
     cudaError_t e;
     if (batch_use_pair(B)) {
         e = B->storage == LB_F16_SHIFTED ? launch_batch_pair<__half>(par, B->ty, B->pair, B->grid_blocks, b, s)
@@ -339,6 +351,7 @@ void lb_batch_destroy(lb_batch* B) {
     cudaFree(B->d_item_box);
     cudaFree(B->d_item0);
     cudaFree(B->d_nitem);
+    cudaFree(B->d_next);
     cudaFree(B->d_epsw);
     cudaFree(B->d_st);
     cudaFree(B->stage);
@@ -419,6 +432,7 @@ int lb_batch_create(int count, const int* dims, const double* tau, const double*
     alloc((void**)&B->d_boxes, (size_t)count * sizeof(BoxDesc));
     alloc((void**)&B->d_item0, (size_t)count * sizeof(int));
     alloc((void**)&B->d_nitem, (size_t)count * sizeof(int));
+    alloc((void**)&B->d_next, sizeof(int));
     alloc((void**)&B->d_epsw, (size_t)count * sizeof(double));
     alloc((void**)&B->d_st, (size_t)count * sizeof(DevState));
     if (rc == LB_OK) {

@@ -665,7 +665,8 @@ fused_step_kernel(const StepArgs a) {
 // ------------------------------------------------------ batched ensemble
 // Many independent periodic boxes in one array set: box b's f planes start at
 // element f_off and are N_b apart; its g planes likewise at g_off in each of
-// the two g buffers.  The work list enumerates (box, tile, z-chunk) items.
+// the two g buffers.  The work list enumerates (box, tile, z-chunk) items;
+// a persistent grid takes them from a queue.
 struct BoxDesc {
     int nx, ny, nz, N;
     long long f_off, g_off;                 // element offsets into the batch arrays
@@ -685,6 +686,7 @@ struct BatchArgs {
     const float* c_in;     // moment-only storage: coefficient buffers at t and t+1
     float* c_out;
     double* partials;      // NPART per work item
+    int* next;             // work queue: the next item to take (zero at the step's start)
 };
 
 // Plane q of a plane set stored q * stride elements apart.
@@ -730,7 +732,14 @@ __global__ void __launch_bounds__(PAIR_ ? pair_threads<PW_, TY>() : 32 * TY,
                                   PAIR_ ? (pair_threads<PW_, TY>() == 64 ? 6 : pair_threads<PW_, TY>() == 128 ? 3 : 2)
                                         : (TY >= 16 ? 1 : 512 / (32 * TY)))
 batch_step_kernel(const __grid_constant__ BatchArgs b) {
-    for (int item = blockIdx.x; item < b.nitems; item += gridDim.x) {
+    __shared__ int s_item;
+    for (;;) {
+        // each block takes the next item of the queue (items of unequal cost:
+        // boxes and z-chunks of different heights)
+        if (threadIdx.x == 0) s_item = atomicAdd(b.next, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= b.nitems) break;
         const BoxDesc d = b.boxes[b.item_box[item]];
         BoxTileArgs<FT> t;
         t.nx = d.nx; t.ny = d.ny; t.nz = d.nz; t.zc = b.zc; t.N = d.N;
