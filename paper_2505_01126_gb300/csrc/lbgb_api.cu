@@ -158,9 +158,10 @@ size_t g_buf_bytes(const lb_ctx* c) { return (size_t)c->N * (is_g16(c) ? 8 * 2 :
 
 // The paired step kernel (two x-adjacent sites per thread, packed two-lane FP32
 // arithmetic) runs the step when it is preferred and applies: a 16-bit AA
-// storage, nx a multiple of 4, the D3Q7 phase field, no density contrasts.
+// storage, nx a multiple of 4, the D3Q7 phase field (with or without density
+// contrasts).
 bool pair_applies(const lb_ctx* c) {
-    return (c->fsize == 2 && !is_mc(c)) && c->nx % 4 == 0 && !c->vd && !c->fd;
+    return (c->fsize == 2 && !is_mc(c)) && c->nx % 4 == 0 && !c->fd;
 }
 bool use_pair(const lb_ctx* c) { return c->pair && pair_applies(c); }
 
@@ -306,6 +307,9 @@ int enqueue_step(lb_ctx* c, int par, cudaStream_t s, bool first = false) {
         if (is_g16(c))
             LB_CUDA(is_f16(c) ? launch_fused_pair_g16<__half>(par, c->ty, grid, a, s)
                               : launch_fused_pair_g16<__nv_bfloat16>(par, c->ty, grid, a, s));
+        else if (c->vd)
+            LB_CUDA(is_f16(c) ? launch_fused_pair_vd<__half>(par, c->ty, grid, a, s)
+                              : launch_fused_pair_vd<__nv_bfloat16>(par, c->ty, grid, a, s));
         else
             LB_CUDA(is_f16(c) ? launch_fused_pair<__half>(par, c->ty, grid, a, s)
                               : launch_fused_pair<__nv_bfloat16>(par, c->ty, grid, a, s));
@@ -412,6 +416,8 @@ int tune_chunks(const lb_ctx* c, int ty, int zcs[6]) {
                                           : fused_pair_g16_blocks_per_sm<__nv_bfloat16>(ty))
                              : (is_f16(c) ? fused_g16_blocks_per_sm<__half>(ty)
                                           : fused_g16_blocks_per_sm<__nv_bfloat16>(ty));
+    else if (use_pair(c) && c->vd)
+        per_sm = is_f16(c) ? fused_pair_vd_blocks_per_sm<__half>(ty) : fused_pair_vd_blocks_per_sm<__nv_bfloat16>(ty);
     else if (use_pair(c))
         per_sm = is_f16(c) ? fused_pair_blocks_per_sm<__half>(ty) : fused_pair_blocks_per_sm<__nv_bfloat16>(ty);
     int sms = 0;
@@ -751,8 +757,8 @@ int lb_set_tile(lb_ctx* c, int ty, int zc) {
 int lb_set_pairing(lb_ctx* c, int on) {
     if (!c) return fail(LB_EINVAL, "ctx is NULL");
     if (on && !pair_applies(c))
-        return fail(LB_EINVAL, "the paired step kernel needs FP16 or BF16 storage, nx %% 4 == 0, the D3Q7 phase "
-                               "field and no density contrasts");
+        return fail(LB_EINVAL, "the paired step kernel needs FP16 or BF16 storage, nx %% 4 == 0 and the D3Q7 phase "
+                               "field");
     c->pair = on != 0;
     return LB_OK;
 }

@@ -502,11 +502,11 @@ __device__ __forceinline__ void quad_poly27_2(float2 e0, const float2 (&Pp)[3], 
     v[IDX(-1, -1, -1)] = add2(emm, add2(Pm[2], Vpp));
 }
 
-// collide_site for a pair of sites: steps 8-10 (inv = 1/(1 - A/2) and the
-// relaxation rate are the same for both).
+// collide_site for a pair of sites: steps 8-10 (inv = 1/(1 - A/2) is the same
+// for both; the relaxation rates may differ, with density contrasts).
 __device__ __forceinline__ void collide_pair(float2 pp, float2 m0, float2 m1, float2 m2, float2 P00, float2 P11,
                                              float2 P22, float2 P01, float2 P02, float2 P12, float2 Fe0, float2 Fe1,
-                                             float2 Fe2, float A_lin, float inv_s, float omega, float2& u0,
+                                             float2 Fe2, float A_lin, float inv_s, float2 omega, float2& u0,
                                              float2& u1, float2& u2, float2& aa, float2 (&v)[27]) {
     const float2 half = f2(0.5f), inv = f2(inv_s), A = f2(A_lin);
     u0 = mul2(fma2(half, Fe0, m0), inv);
@@ -523,7 +523,7 @@ __device__ __forceinline__ void collide_pair(float2 pp, float2 m0, float2 m1, fl
     const float2 a12 = fma2(half, fma2(u1, F2, mul2(F1, u2)), fma2(mul2(u1, f2(-1.f)), u2, P12));
     const float2 offd = fma2(a01, a01, fma2(a02, a02, mul2(a12, a12)));
     aa = fma2(f2(2.f), offd, fma2(a00, a00, fma2(a11, a11, mul2(a22, a22))));
-    const float2 om1 = f2(1.f - omega);
+    const float2 om1 = sub2(f2(1.f), omega);
     const float2 B00 = fma2(om1, a00, mul2(u0, u0)), B11 = fma2(om1, a11, mul2(u1, u1));
     const float2 B22 = fma2(om1, a22, mul2(u2, u2)), B01 = fma2(om1, a01, mul2(u0, u1));
     const float2 B02 = fma2(om1, a02, mul2(u0, u2)), B12 = fma2(om1, a12, mul2(u1, u2));
@@ -578,6 +578,36 @@ __host__ __device__ __forceinline__ void vd_force(float phi, float gp0, float gp
     F1 = fmaf(c, fmaf(n01, q0, fmaf(n11, q1, n12 * q2)), G1) * irho;
     F2 = fmaf(c, fmaf(n02, q0, fmaf(n12, q1, n22 * q2)), G2) * irho;
     aa_w = 1.5f * (1.f - 0.5f * omega) * omega;
+}
+
+// vd_force for a pair of sites (the same formulas, two lanes per instruction;
+// grad phi given as |grad phi| n, as the paired kernel keeps it).
+__device__ __forceinline__ void vd_force2(float2 phi, float2 gp0, float2 gp1, float2 gp2, float2 pp, float2 m0,
+                                          float2 m1, float2 m2, float2 P00, float2 P11, float2 P22, float2 P01,
+                                          float2 P02, float2 P12, float A_lin, float rho_g, float drho, float tau_g,
+                                          float dtau, float gb0, float gb1, float gb2, float rho_ref, float2& F0,
+                                          float2& F1, float2& F2, float2& omega, float2& aa_w) {
+    const float2 rho = fma2(phi, f2(drho), f2(rho_g));
+    const float2 irho = make_float2(1.f / rho.x, 1.f / rho.y);
+    const float2 tau = fma2(phi, f2(dtau), f2(tau_g));
+    omega = make_float2(1.f / tau.x, 1.f / tau.y);
+    const float2 q0 = mul2(f2(drho), gp0), q1 = mul2(f2(drho), gp1), q2 = mul2(f2(drho), gp2);  // grad rho
+    const float2 br = sub2(rho, f2(rho_ref));
+    const float2 fp = mul2(pp, f2(-1.f / 3.f));
+    const float2 G0 = fma2(fp, q0, fma2(br, f2(gb0), F0)), G1 = fma2(fp, q1, fma2(br, f2(gb1), F1));
+    const float2 G2 = fma2(fp, q2, fma2(br, f2(gb2), F2));
+    const float2 h = mul2(f2(0.5f), irho), inv = f2(1.f / (1.f - 0.5f * A_lin));
+    const float2 v0 = mul2(fma2(h, G0, m0), inv), v1 = mul2(fma2(h, G1, m1), inv), v2 = mul2(fma2(h, G2, m2), inv);
+    const float2 p3 = mul2(pp, f2(1.f / 3.f));
+    const float2 mv0 = mul2(v0, f2(-1.f)), mv1 = mul2(v1, f2(-1.f));
+    const float2 n00 = fma2(mv0, v0, sub2(P00, p3)), n11 = fma2(mv1, v1, sub2(P11, p3));
+    const float2 n22 = fma2(mul2(v2, f2(-1.f)), v2, sub2(P22, p3));
+    const float2 n01 = fma2(mv0, v1, P01), n02 = fma2(mv0, v2, P02), n12 = fma2(mv1, v2, P12);
+    const float2 c = fma2(f2(0.5f), omega, f2(-1.f));  // -nu omega / cs^2
+    F0 = mul2(fma2(c, fma2(n00, q0, fma2(n01, q1, mul2(n02, q2))), G0), irho);
+    F1 = mul2(fma2(c, fma2(n01, q0, fma2(n11, q1, mul2(n12, q2))), G1), irho);
+    F2 = mul2(fma2(c, fma2(n02, q0, fma2(n12, q1, mul2(n22, q2))), G2), irho);
+    aa_w = mul2(mul2(f2(1.5f), fma2(f2(-0.5f), omega, f2(1.f))), omega);
 }
 
 // One pulled column of the moment-only storage: the three directions
@@ -819,6 +849,11 @@ template <class FT>
 cudaError_t launch_fused_pair(int parity, int ty, dim3 grid, const StepArgs& a, cudaStream_t st);
 template <class FT>
 int fused_pair_blocks_per_sm(int ty);
+// The same with density and viscosity contrasts (VD); lbgb_step_pair_vd_*.cu.
+template <class FT>
+cudaError_t launch_fused_pair_vd(int parity, int ty, dim3 grid, const StepArgs& a, cudaStream_t st);
+template <class FT>
+int fused_pair_vd_blocks_per_sm(int ty);
 // The kernels of the 16-bit D3Q7 storage (G16; FT __half or __nv_bfloat16,
 // nx % 4 == 0): one-site kernels for MODE_INIT (ty 8), MODE_MOMENTS (ty 8) and
 // MODE_STEP (ty 4 or 8), defined in lbgb_step_g16_*.cu; the paired step kernel

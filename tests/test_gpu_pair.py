@@ -111,12 +111,52 @@ def test_paired_hit_64_against_oracle(lbgb, orc):
     o.close()
 
 
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("dens", [(10.0, 1.0, 0.6, 0.8), (1.0, 10.0, 0.8, 0.6)])
+def test_paired_with_density_contrasts(lbgb, orc, storage, dens):
+    """Density and viscosity contrasts (Sec. 2.3) in the paired kernel: heavy and
+    light droplets at ratio 10 with their own tau, buoyancy on, 50 steps, against
+    the oracle with the same contrasts within the 16-bit bounds, and within them
+    of the one-site contrast kernel's fields."""
+    shape = (12, 20, 36)
+    phi, u = smooth_fields(shape, 9)
+    nz, ny, nx = shape
+    rho_ref = dens[1] + (dens[0] - dens[1]) * float(phi.astype(np.float64).mean())
+    o = orc.Oracle(nx, ny, nz, 0.7, 0.1, 3.0, 0.01)
+    o.set_density(*dens)
+    o.set_gravity((0.0, 0.0, -2e-6), rho_ref)
+    o.init(phi.astype(np.float64), u.astype(np.float64))
+    o.step(50)
+    want = o.moments()
+    o.close()
+    got = {}
+    for pair in (True, False):
+        b = lbgb.Box(nx, ny, nz, 0.7, 0.1, 3.0, 0.01, storage=storage)
+        b.set_density(*dens)
+        b.set_gravity((0.0, 0.0, -2e-6), rho_ref)
+        b.set_pairing(pair)
+        b.set_tile(8, 5)
+        assert b.paired == pair
+        b.init(phi, u)
+        b.step(50)
+        got[pair] = b.moments_numpy()
+        b.close()
+    ep, es = max_err(got[True], want), max_err(got[False], want)
+    assert max(ep) <= BOUND[storage], (ep, es)
+    d = max_err(got[True], [x.astype(np.float64) for x in got[False]])
+    assert max(d) <= BOUND[storage], (d, ep, es)
+
+
 def test_pairing_applies_where_it_can(lbgb):
     b = lbgb.Box(8, 8, 8, 0.8, 0.1, 3.0, 0.01, storage="f16")
     assert b.paired  # the default for FP16 with nx % 4 == 0
     b.set_tile(4, 8)
-    b.set_density(10.0, 1.0, 0.8, 0.8)  # the contrast kernels are one site per thread
-    assert not b.paired and b.tile() == (4, 8)
+    b.set_density(10.0, 1.0, 0.8, 0.8)  # the contrast step is paired as well
+    assert b.paired and b.tile() == (4, 8)
+    b.close()
+    b = lbgb.Box(8, 8, 8, 0.8, 0.1, 3.0, 0.01, storage="f16")
+    b.set_phase_solver("weno5")  # the finite-difference phase field is one site per thread
+    assert not b.paired
     with pytest.raises(lbgb.LBError) as e:
         b.set_pairing(True)
     assert e.value.code == lbgb.LB_EINVAL
