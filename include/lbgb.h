@@ -419,7 +419,7 @@ int lb_batch_set_density(lb_batch* batch, const double* rho_l, const double* rho
  * one of lb_set_pairing on tiles 64 (on = 64 or 1, the default where it
  * applies) or 32 sites wide (on = 32, which idles fewer columns on boxes of 24
  * or 48 sites), or one site per thread (on = 0).  The paired body applies when
- * every box has nx % 4 == 0 and no density contrasts are set.  lb_batch_tune
+ * every box has nx % 4 == 0, with or without density contrasts.  lb_batch_tune
  * times all three.  Errors: LB_EINVAL for another value, or a paired body
  * where it does not apply. */
 int lb_batch_set_pairing(lb_batch* batch, int on);

@@ -24,6 +24,14 @@
 
 using namespace lbgb;
 
+namespace lbgb {
+// The batch kernel with the paired tile body and density contrasts (lbgb_batch_pair_vd_*.cu).
+template <class FT>
+cudaError_t launch_batch_pair_vd(int parity, int ty, int pw, int blocks, const BatchArgs& b, cudaStream_t st);
+template <class FT>
+int batch_pair_vd_blocks_per_sm(int ty, int pw);
+}  // namespace lbgb
+
 namespace {
 
 int bfail(int code, const char* fmt, ...) {
@@ -134,11 +142,11 @@ struct lb_batch {
 
 namespace {
 
-// The paired tile body (two sites per thread, tiles 64 sites wide) runs the
-// step when it is preferred and applies: FP16/BF16 storage, every box with
-// nx % 4 == 0, no density contrasts.
+// The paired tile body (two sites per thread, tiles 64 or 32 sites wide) runs
+// the step when it is preferred and applies: FP16/BF16 storage, every box with
+// nx % 4 == 0 (with or without density contrasts).
 bool batch_pair_applies(const lb_batch* B) {
-    return (B->storage == LB_F16_SHIFTED || B->storage == LB_BF16_SHIFTED) && B->vec && !B->vd;
+    return (B->storage == LB_F16_SHIFTED || B->storage == LB_BF16_SHIFTED) && B->vec;
 }
 bool batch_use_pair(const lb_batch* B) { return B->pair != 0 && batch_pair_applies(B); }
 
@@ -189,7 +197,10 @@ int build_work(lb_batch* B) {
     BCUDA(cudaMemcpy(B->d_nitem, nitem.data(), (size_t)B->count * sizeof(int), cudaMemcpyHostToDevice));
     B->nitems = item;
     int per_sm = 0;
-    if (batch_use_pair(B)) per_sm = B->storage == LB_F16_SHIFTED ? batch_pair_blocks_per_sm<__half>(B->ty, B->pair)
+    if (batch_use_pair(B) && B->vd)
+        per_sm = B->storage == LB_F16_SHIFTED ? batch_pair_vd_blocks_per_sm<__half>(B->ty, B->pair)
+                                              : batch_pair_vd_blocks_per_sm<__nv_bfloat16>(B->ty, B->pair);
+    else if (batch_use_pair(B)) per_sm = B->storage == LB_F16_SHIFTED ? batch_pair_blocks_per_sm<__half>(B->ty, B->pair)
                                                                   : batch_pair_blocks_per_sm<__nv_bfloat16>(B->ty, B->pair);
     else if (B->vd) switch (B->storage) {
         case LB_F32_MOMENTS: per_sm = batch_vd_blocks_per_sm<float, true>(B->ty, B->vec); break;
@@ -278,7 +289,10 @@ int enqueue_batch_step(lb_batch* B, int par, cudaStream_t s, bool first = false)
     b.next = B->d_next;
     BCUDA(cudaMemsetAsync(B->d_next, 0, sizeof(int), s));
     cudaError_t e;
-    if (batch_use_pair(B)) {
+    if (batch_use_pair(B) && B->vd) {
+        e = B->storage == LB_F16_SHIFTED ? launch_batch_pair_vd<__half>(par, B->ty, B->pair, B->grid_blocks, b, s)
+                                         : launch_batch_pair_vd<__nv_bfloat16>(par, B->ty, B->pair, B->grid_blocks, b, s);
+    } else if (batch_use_pair(B)) {
         e = B->storage == LB_F16_SHIFTED ? launch_batch_pair<__half>(par, B->ty, B->pair, B->grid_blocks, b, s)
                                          : launch_batch_pair<__nv_bfloat16>(par, B->ty, B->pair, B->grid_blocks, b, s);
     } else if (B->vd) {
@@ -658,8 +672,7 @@ int lb_batch_set_pairing(lb_batch* B, int on) {
     if (on != 0 && on != 1 && on != 32 && on != 64)
         return bfail(LB_EINVAL, "lb_batch_set_pairing: %d is none of 0, 1, 32, 64", on);
     if (on && !batch_pair_applies(B))
-        return bfail(LB_EINVAL, "the paired tile body needs FP16 or BF16 storage, nx %% 4 == 0 in every box and no "
-                                "density contrasts");
+        return bfail(LB_EINVAL, "the paired tile body needs FP16 or BF16 storage and nx %% 4 == 0 in every box");
     B->pair = on == 1 ? 64 : on;
     return build_work(B);
 }
