@@ -385,8 +385,10 @@ typedef struct lb_batch lb_batch;
 /* count boxes; dims = count triples (nx, ny, nz); tau, M, W, sigma = count
  * values each, with the meaning and limits of lb_create.  The batch owns one
  * population array for all boxes (same storage), two D3Q7 arrays and the
- * reduction scratch.  storage is any LB_* storage.
- * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA. */
+ * reduction scratch.  storage is LB_F32, LB_F16_SHIFTED, LB_BF16_SHIFTED or
+ * LB_F32_MOMENTS (the 16-bit D3Q7 storages run single boxes only).
+ * Errors: LB_EINVAL (also for LB_F16_SHIFTED_G16 / LB_BF16_SHIFTED_G16),
+ * LB_ENOMEM, LB_ECUDA. */
 int lb_batch_create(int count, const int* dims, const double* tau, const double* M, const double* W,
                     const double* sigma, int storage, lb_batch** out);
 int lb_batch_set_stream(lb_batch* batch, void* stream);
