@@ -227,9 +227,10 @@ int lb_get_tile(const lb_ctx* ctx, int* ty, int* zc);
  * bound by instruction issue, which this halves for the arithmetic.  on = 0:
  * one site per thread, as for every other storage.  The two compute the same
  * formulas in FP32; their results agree to FP32 rounding, not bit for bit.
- * The paired kernel applies to FP16/BF16 storage with nx % 4 == 0 and the
- * D3Q7 phase field, with or without density contrasts (lb_set_density);
- * lb_set_phase_solver(LB_PHASE_WENO5) switches back to the one-site kernel.
+ * The paired kernel applies to FP16/BF16 storage with nx % 4 == 0: with the
+ * D3Q7 phase field, with or without density contrasts (lb_set_density), and
+ * with the WENO-5 phase field (lb_set_phase_solver) without them; the two
+ * together run the one-site kernel.
  * lb_get_pairing reports whether the paired kernel runs the step.
  * Errors: LB_EINVAL for on = 1 where the paired kernel does not apply.
  */

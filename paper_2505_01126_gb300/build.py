@@ -20,7 +20,7 @@ SOURCES = ["lbgb_api.cu", "lbgb_step_f32.cu", "lbgb_step_f16.cu", "lbgb_step_bf1
            "lbgb_static.cu", "lbgb_batch.cu", "lbgb_stats.cu", "lbgb_weno.cu", "lbgb_peak.cu", "lbgb_step_pair_f16.cu",
            "lbgb_step_pair_bf16.cu", "lbgb_step_g16_f16.cu", "lbgb_step_g16_bf16.cu", "lbgb_step_pair_g16_f16.cu",
            "lbgb_step_pair_g16_bf16.cu", "lbgb_step_pair_vd_f16.cu", "lbgb_step_pair_vd_bf16.cu", "lbgb_batch_pair_vd_f16.cu",
-           "lbgb_batch_pair_vd_bf16.cu"] + [
+           "lbgb_batch_pair_vd_bf16.cu", "lbgb_step_pair_pf_f16.cu", "lbgb_step_pair_pf_bf16.cu"] + [
            f"lbgb_step_{v}_{st}.cu" for v in ("vd", "fd", "fdvd") for st in ("f32", "f16", "bf16", "mc")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -158,10 +158,10 @@ size_t g_buf_bytes(const lb_ctx* c) { return (size_t)c->N * (is_g16(c) ? 8 * 2 :
 
 // The paired step kernel (two x-adjacent sites per thread, packed two-lane FP32
 // arithmetic) runs the step when it is preferred and applies: a 16-bit AA
-// storage, nx a multiple of 4, the D3Q7 phase field (with or without density
-// contrasts).
+// storage, nx a multiple of 4; the D3Q7 phase field with or without density
+// contrasts, or the finite-difference phase field without them.
 bool pair_applies(const lb_ctx* c) {
-    return (c->fsize == 2 && !is_mc(c)) && c->nx % 4 == 0 && !c->fd;
+    return (c->fsize == 2 && !is_mc(c)) && c->nx % 4 == 0 && !(c->fd && c->vd);
 }
 bool use_pair(const lb_ctx* c) { return c->pair && pair_applies(c); }
 
@@ -310,6 +310,9 @@ int enqueue_step(lb_ctx* c, int par, cudaStream_t s, bool first = false) {
         else if (c->vd)
             LB_CUDA(is_f16(c) ? launch_fused_pair_vd<__half>(par, c->ty, grid, a, s)
                               : launch_fused_pair_vd<__nv_bfloat16>(par, c->ty, grid, a, s));
+        else if (c->fd)
+            LB_CUDA(is_f16(c) ? launch_fused_pair_pf<__half>(par, c->ty, grid, a, s)
+                              : launch_fused_pair_pf<__nv_bfloat16>(par, c->ty, grid, a, s));
         else
             LB_CUDA(is_f16(c) ? launch_fused_pair<__half>(par, c->ty, grid, a, s)
                               : launch_fused_pair<__nv_bfloat16>(par, c->ty, grid, a, s));
@@ -416,6 +419,8 @@ int tune_chunks(const lb_ctx* c, int ty, int zcs[6]) {
                                           : fused_pair_g16_blocks_per_sm<__nv_bfloat16>(ty))
                              : (is_f16(c) ? fused_g16_blocks_per_sm<__half>(ty)
                                           : fused_g16_blocks_per_sm<__nv_bfloat16>(ty));
+    else if (use_pair(c) && c->fd)
+        per_sm = is_f16(c) ? fused_pair_pf_blocks_per_sm<__half>(ty) : fused_pair_pf_blocks_per_sm<__nv_bfloat16>(ty);
     else if (use_pair(c) && c->vd)
         per_sm = is_f16(c) ? fused_pair_vd_blocks_per_sm<__half>(ty) : fused_pair_vd_blocks_per_sm<__nv_bfloat16>(ty);
     else if (use_pair(c))
@@ -757,8 +762,8 @@ int lb_set_tile(lb_ctx* c, int ty, int zc) {
 int lb_set_pairing(lb_ctx* c, int on) {
     if (!c) return fail(LB_EINVAL, "ctx is NULL");
     if (on && !pair_applies(c))
-        return fail(LB_EINVAL, "the paired step kernel needs FP16 or BF16 storage, nx %% 4 == 0 and the D3Q7 phase "
-                               "field");
+        return fail(LB_EINVAL, "the paired step kernel needs FP16 or BF16 storage and nx %% 4 == 0 (and not density "
+                               "contrasts together with the finite-difference phase field)");
     c->pair = on != 0;
     return LB_OK;
 }

@@ -849,6 +849,11 @@ template <class FT>
 cudaError_t launch_fused_pair(int parity, int ty, dim3 grid, const StepArgs& a, cudaStream_t st);
 template <class FT>
 int fused_pair_blocks_per_sm(int ty);
+// The same with the finite-difference phase field (PF); lbgb_step_pair_pf_*.cu.
+template <class FT>
+cudaError_t launch_fused_pair_pf(int parity, int ty, dim3 grid, const StepArgs& a, cudaStream_t st);
+template <class FT>
+int fused_pair_pf_blocks_per_sm(int ty);
 // The same with density and viscosity contrasts (VD); lbgb_step_pair_vd_*.cu.
 template <class FT>
 cudaError_t launch_fused_pair_vd(int parity, int ty, dim3 grid, const StepArgs& a, cudaStream_t st);

@@ -2,13 +2,49 @@
 // x-adjacent sites per thread, packed two-lane FP32 arithmetic) for one 16-bit
 // storage type.  Included by lbgb_step_pair_{f16,bf16}.cu and, with
 // LBGB_PAIR_VD defined (the density-contrast instances), by
-// lbgb_step_pair_vd_{f16,bf16}.cu, which compile in parallel.
+// lbgb_step_pair_vd_{f16,bf16}.cu, and with LBGB_PAIR_PF (the finite-difference
+// phase field) by lbgb_step_pair_pf_{f16,bf16}.cu, which compile in parallel.
 #pragma once
 #include "lbgb_kernels.cuh"
 
 namespace lbgb {
 
-#ifdef LBGB_PAIR_VD
+#if defined(LBGB_PAIR_PF)
+// The paired step kernel with the finite-difference phase field (PF: phi read
+// from its stored plane, u written for the stage kernels).
+template <class FT, int TY>
+static void launch_pair_pf_ty(int parity, dim3 grid, const StepArgs& a, cudaStream_t st) {
+    if (parity == 0) fused_step_kernel<FT, TY, MODE_STEP, 0, true, false, false, true, true><<<grid, 32 * TY, 0, st>>>(a);
+    else fused_step_kernel<FT, TY, MODE_STEP, 1, true, false, false, true, true><<<grid, 32 * TY, 0, st>>>(a);
+}
+
+template <>
+cudaError_t launch_fused_pair_pf<LBGB_FT>(int parity, int ty, dim3 grid, const StepArgs& a, cudaStream_t st) {
+    switch (ty) {
+        case 4: launch_pair_pf_ty<LBGB_FT, 4>(parity, grid, a, st); break;
+        case 8: launch_pair_pf_ty<LBGB_FT, 8>(parity, grid, a, st); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <>
+int fused_pair_pf_blocks_per_sm<LBGB_FT>(int ty) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (ty == 4)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &n, fused_step_kernel<LBGB_FT, 4, MODE_STEP, 1, true, false, false, true, true>, 128, 0);
+    else if (ty == 8)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &n, fused_step_kernel<LBGB_FT, 8, MODE_STEP, 1, true, false, false, true, true>, 256, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+#elif defined(LBGB_PAIR_VD)
 // The paired step kernel with density and viscosity contrasts (VD).
 template <class FT, int TY>
 static void launch_pair_vd_ty(int parity, dim3 grid, const StepArgs& a, cudaStream_t st) {

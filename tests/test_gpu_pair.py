@@ -147,6 +147,38 @@ def test_paired_with_density_contrasts(lbgb, orc, storage, dens):
     assert max(d) <= BOUND[storage], (d, ep, es)
 
 
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_paired_with_the_finite_difference_phase_field(lbgb, orc, storage):
+    """The WENO-5 phase field (Sec. 2.1.1) with the paired step kernel (phi read
+    from its stored plane, u written for the stage kernels): 50 steps against
+    the oracle within the 16-bit bounds, and within them of the one-site
+    kernel's fields."""
+    shape = (12, 20, 36)
+    phi, u = smooth_fields(shape, 13)
+    nz, ny, nx = shape
+    o = orc.Oracle(nx, ny, nz, 0.7, 0.1, 3.0, 0.01)
+    o.set_phase_solver("weno5")
+    o.init(phi.astype(np.float64), u.astype(np.float64))
+    o.step(50)
+    want = o.moments()
+    o.close()
+    got = {}
+    for pair in (True, False):
+        b = lbgb.Box(nx, ny, nz, 0.7, 0.1, 3.0, 0.01, storage=storage)
+        b.set_phase_solver("weno5")
+        b.set_pairing(pair)
+        b.set_tile(8, 5)
+        assert b.paired == pair
+        b.init(phi, u)
+        b.step(50)
+        got[pair] = b.moments_numpy()
+        b.close()
+    ep, es = max_err(got[True], want), max_err(got[False], want)
+    assert max(ep) <= BOUND[storage], (ep, es)
+    d = max_err(got[True], [x.astype(np.float64) for x in got[False]])
+    assert max(d) <= BOUND[storage], (d, ep, es)
+
+
 def test_pairing_applies_where_it_can(lbgb):
     b = lbgb.Box(8, 8, 8, 0.8, 0.1, 3.0, 0.01, storage="f16")
     assert b.paired  # the default for FP16 with nx % 4 == 0
@@ -155,7 +187,9 @@ def test_pairing_applies_where_it_can(lbgb):
     assert b.paired and b.tile() == (4, 8)
     b.close()
     b = lbgb.Box(8, 8, 8, 0.8, 0.1, 3.0, 0.01, storage="f16")
-    b.set_phase_solver("weno5")  # the finite-difference phase field is one site per thread
+    b.set_phase_solver("weno5")  # the finite-difference phase field is paired too
+    assert b.paired
+    b.set_density(10.0, 1.0, 0.8, 0.8)  # but not together with contrasts
     assert not b.paired
     with pytest.raises(lbgb.LBError) as e:
         b.set_pairing(True)
